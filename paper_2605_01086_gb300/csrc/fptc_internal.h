@@ -1,0 +1,133 @@
+// Internal layout shared by the host plan and the CUDA kernels of libfptc.
+// Nothing here is part of the C ABI.
+#pragma once
+
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+namespace fptc {
+
+// Index work unit: the symlen array of a segment is cut into chunks of this many
+// words; the symbol offsets of the SymLen words (Sec. 4.2.1) are an exclusive
+// scan over chunks, then over words inside a chunk.
+constexpr uint32_t kChunkWords = 2048;
+constexpr uint32_t kIndexThreads = 256;  // kChunkWords / kIndexThreads = 8 words per thread
+constexpr uint32_t kMaxLmax = 16;
+constexpr uint32_t kChunkBad = 0xFFFFFFFFu;  // chunk sum sentinel: a symlen > 64 was seen
+
+// Device status flags (mirror FPTC_FLAG_* in fptc.h).
+constexpr unsigned int kFlagSymlenRange = 1u;
+constexpr unsigned int kFlagBitOverrun = 2u;
+constexpr unsigned int kFlagInvalidCode = 4u;
+constexpr unsigned int kFlagSymbolCount = 8u;
+
+// Per-domain tables in device memory (copied to shared memory by the kernels).
+struct DomainDev {
+  uint32_t N, E, B1, B2;
+  uint32_t lmax;
+  uint32_t tile_windows;   // windows per tile
+  uint32_t lut_offset;     // first entry of this domain's decode table
+  uint32_t basis_offset;   // first float of this domain's E x N inverse-transform basis
+  float scale[3];          // the plan's A_0, A_1, A_2 rounded to float
+  uint32_t pad;
+  float unit[2][256];      // reconstruction at A_z = 1 for zones 0 and 1 (FP64 -> FP32)
+};
+
+// One segment, in tile-queue order (segments sorted by domain).
+struct SegDev {
+  uint64_t word_offset;
+  uint64_t n_words;
+  uint64_t n_samples;
+  uint64_t out_offset;
+  uint64_t level_offset;
+  uint64_t n_windows;
+  uint64_t tile_base;    // global index of the segment's first tile
+  uint64_t n_tiles;
+  uint64_t chunk_base;   // global index of the segment's first index chunk
+  uint32_t n_chunks;
+  uint32_t domain;
+  uint32_t caller_index; // position in the caller's segment array
+  uint32_t out_aligned;  // out_offset % 4 == 0: 16-byte vector stores allowed
+};
+
+struct ChunkDev {
+  uint64_t word_begin;
+  uint32_t n_words;
+  uint32_t seg;          // queue index of the owning segment
+};
+
+// Start of a tile in the SymLen stream: the word holding the tile's first symbol
+// and how many earlier symbols of that word belong to the previous tile.
+struct TileRec {
+  uint64_t first_word;
+  uint32_t skip;
+  uint32_t pad;
+};
+
+struct DevStatus {
+  unsigned int flags;
+  unsigned int pad;
+  unsigned long long first_bad;  // smallest caller index of a bad segment
+};
+
+struct IndexParams {
+  const uint8_t *symlen;
+  const SegDev *segs;
+  const DomainDev *domains;
+  const ChunkDev *chunks;
+  uint32_t *chunk_sum;
+  uint64_t *chunk_off;
+  uint32_t *seg_bad;
+  TileRec *tiles;
+  DevStatus *status;
+  uint64_t chunk_begin, chunk_end;  // chunk range of this launch
+  uint32_t seg_begin, seg_end;      // segment range of this launch
+};
+
+struct DecodeParams {
+  const uint64_t *words;
+  const uint8_t *symlen;
+  float *out;
+  uint8_t *levels;          // optional level output
+  const float *scale;       // optional run-time A_z [n_domains * 3]
+  const SegDev *segs;
+  const DomainDev *domains;
+  const uint16_t *luts;
+  const float *basis;
+  const TileRec *tiles;
+  const uint32_t *seg_bad;
+  DevStatus *status;
+  uint64_t tile_begin, tile_end;  // tile range of this launch
+  uint32_t seg_begin, seg_end;    // segment range covering it
+  uint32_t lut_cap;               // decode-table entries that fit the shared buffer
+  uint32_t coef_cap;              // tile_windows * E capacity of the shared tile buffers
+};
+
+struct BackwardParams {
+  DecodeParams d;              // levels/words source, segments, tables
+  const uint8_t *levels_in;    // saved levels, or null: decode again
+  const float *grad_out;
+  float *grad_coeffs;          // optional
+  double *grad_scale;          // [n_domains * 3], zeroed by the host call
+  uint32_t gx_cap;             // largest tile_windows * N of the plan
+  uint32_t basis_cap;          // largest N * E of the plan
+};
+
+// Launch wrappers (index.cu, decode.cu, backward.cu).
+cudaError_t launch_index(const IndexParams &p, cudaStream_t stream);
+// kind: 0 = generic, 1 = fixed N = 32, E = 16 (CUDA-core FP32)
+cudaError_t launch_decode(const DecodeParams &p, int kind, uint32_t threads, uint32_t grid, size_t smem,
+                          cudaStream_t stream);
+cudaError_t decode_smem_config(int kind, uint32_t threads, size_t smem);
+cudaError_t decode_occupancy(int kind, uint32_t threads, size_t smem, int *ctas_per_sm);
+size_t decode_smem_bytes(int kind, uint32_t threads, uint32_t lut_cap, uint32_t coef_cap);
+
+cudaError_t launch_backward(const BackwardParams &p, uint32_t threads, uint32_t grid, size_t smem,
+                            cudaStream_t stream);
+size_t backward_smem_bytes(uint32_t threads, uint32_t lut_cap, uint32_t coef_cap, uint32_t gx_cap,
+                           uint32_t basis_cap);
+cudaError_t backward_smem_config(uint32_t threads, size_t smem);
+cudaError_t backward_occupancy(uint32_t threads, size_t smem, int *ctas_per_sm);
+
+}  // namespace fptc

@@ -1,0 +1,795 @@
+// Host side of libfptc: plan creation (validation, decode tables,
+// reconstruction tables, tile queue), the C ABI entry points and the launch
+// sequences of the decoder (index kernels, then the fused decode kernel).
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "fptc.h"
+#include "fptc_codec.h"
+#include "fptc_internal.h"
+#include "host_util.h"
+
+using namespace fptc;
+
+struct fptc_plan {
+  int device = 0;
+  int sm_count = 0;
+  fptc_plan_options opts{};
+  std::vector<fptc_domain> domains;
+  std::vector<fptc_segment> caller_segs;
+  std::vector<uint32_t> queue;           // queue position -> caller index
+  std::vector<SegDev> segs;              // queue order
+  std::vector<DomainDev> dom_dev;
+  std::vector<ChunkDev> chunks;
+  std::vector<uint64_t> level_off;       // caller order
+  uint64_t n_tiles = 0, n_chunks = 0, n_levels = 0;
+  uint64_t words_extent = 0, out_extent = 0, n_samples = 0, n_words = 0;
+  // device memory owned by the plan
+  DomainDev *d_domains = nullptr;
+  SegDev *d_segs = nullptr;
+  ChunkDev *d_chunks = nullptr;
+  uint16_t *d_luts = nullptr;
+  float *d_basis = nullptr;
+  uint32_t *d_chunk_sum = nullptr;
+  uint64_t *d_chunk_off = nullptr;
+  uint32_t *d_seg_bad = nullptr;
+  TileRec *d_tiles = nullptr;
+  uint64_t tiles_capacity = 0;
+  DevStatus *d_status = nullptr;
+  size_t device_bytes = 0;
+  // launch settings
+  int kind = 0;
+  uint32_t threads = 256, grid = 0, ctas_per_sm = 0;
+  size_t smem = 0;
+  uint32_t lut_cap = 0, coef_cap = 0, gx_cap = 0, basis_cap = 0;
+  uint32_t b_threads = 256, b_grid = 0;
+  size_t b_smem = 0;
+  cudaStream_t aux = nullptr;
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+};
+
+namespace {
+
+struct DeviceGuard {
+  int prev = -1;
+  bool ok = true;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+fptc_status cuda_fail(cudaError_t e, const char *what) {
+  set_error("%s: %s", what, cudaGetErrorString(e));
+  return e == cudaErrorMemoryAllocation ? FPTC_ERR_OUT_OF_MEMORY : FPTC_ERR_CUDA;
+}
+
+template <typename T>
+cudaError_t upload(T **dst, const std::vector<T> &src, size_t *bytes) {
+  const size_t n = std::max<size_t>(src.size(), 1) * sizeof(T);
+  cudaError_t e = cudaMalloc(reinterpret_cast<void **>(dst), n);
+  if (e != cudaSuccess) return e;
+  *bytes += n;
+  if (!src.empty()) e = cudaMemcpy(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice);
+  return e;
+}
+
+void free_device(fptc_plan *p) {
+  cudaFree(p->d_domains);
+  cudaFree(p->d_segs);
+  cudaFree(p->d_chunks);
+  cudaFree(p->d_luts);
+  cudaFree(p->d_basis);
+  cudaFree(p->d_chunk_sum);
+  cudaFree(p->d_chunk_off);
+  cudaFree(p->d_seg_bad);
+  cudaFree(p->d_tiles);
+  cudaFree(p->d_status);
+  if (p->aux) cudaStreamDestroy(p->aux);
+  for (auto &e : p->ev)
+    if (e) cudaEventDestroy(e);
+}
+
+// Reconstruction at A_z = 1 (the inverse zone maps of Sec. 3.2), FP64 then FP32.
+void unit_tables(const fptc_domain &d, float unit[2][256]) {
+  const double mu = d.mu, a = d.alpha1, span = 1.0 - d.alpha1;
+  for (int L = 0; L < 256; ++L) {
+    double u0 = 0.0, u1 = 0.0;
+    if (L > 128) {
+      u0 = (std::pow(1.0 + mu, (L - 128) / 127.0) - 1.0) / mu;
+      u1 = a + (L - 129) / 126.0 * span;
+    } else if (L < 128) {
+      u0 = -(std::pow(1.0 + mu, (128 - L) / 128.0) - 1.0) / mu;
+      u1 = -(a + (127 - L) / 127.0 * span);
+    }
+    unit[0][L] = static_cast<float>(u0);
+    unit[1][L] = static_cast<float>(u1);
+  }
+}
+
+// Layout of the tile queue for a tile size (target samples per tile).
+void layout_tiles(fptc_plan *p, uint32_t tile_samples) {
+  p->coef_cap = 0;
+  p->gx_cap = 0;
+  for (auto &dd : p->dom_dev) {
+    dd.tile_windows = std::max<uint32_t>(1u, tile_samples / dd.N);
+    p->coef_cap = std::max(p->coef_cap, dd.tile_windows * dd.E);
+    p->gx_cap = std::max(p->gx_cap, dd.tile_windows * dd.N);
+  }
+  uint64_t t = 0;
+  for (auto &s : p->segs) {
+    const uint32_t T = p->dom_dev[s.domain].tile_windows;
+    s.tile_base = t;
+    s.n_tiles = (s.n_windows + T - 1) / T;
+    t += s.n_tiles;
+  }
+  p->n_tiles = t;
+}
+
+fptc_status configure_launch(fptc_plan *p) {
+  const uint32_t threads = p->opts.threads ? p->opts.threads : 256u;
+  if (threads != 128 && threads != 256 && threads != 512) {
+    set_error("threads must be 128, 256 or 512 (got %u)", threads);
+    return FPTC_ERR_INVALID_ARGUMENT;
+  }
+  p->threads = threads;
+  p->smem = decode_smem_bytes(p->kind, threads, p->lut_cap, p->coef_cap);
+  cudaError_t e = decode_smem_config(p->kind, threads, p->smem);
+  if (e != cudaSuccess) return cuda_fail(e, "decode shared-memory size");
+  int occ = 0;
+  e = decode_occupancy(p->kind, threads, p->smem, &occ);
+  if (e != cudaSuccess) return cuda_fail(e, "decode occupancy");
+  if (occ < 1) {
+    set_error("decode kernel does not fit an SM (%zu bytes shared memory)", p->smem);
+    return FPTC_ERR_UNSUPPORTED;
+  }
+  p->ctas_per_sm = p->opts.ctas_per_sm ? std::min<uint32_t>(p->opts.ctas_per_sm, (uint32_t)occ) : (uint32_t)occ;
+  const uint64_t full = (uint64_t)p->sm_count * p->ctas_per_sm;
+  p->grid = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(full, p->n_tiles));
+  // backward
+  p->b_threads = threads;
+  p->b_smem = backward_smem_bytes(threads, p->lut_cap, p->coef_cap, p->gx_cap, p->basis_cap);
+  e = backward_smem_config(threads, p->b_smem);
+  if (e != cudaSuccess) return cuda_fail(e, "backward shared-memory size");
+  int bocc = 0;
+  e = backward_occupancy(threads, p->b_smem, &bocc);
+  if (e != cudaSuccess) return cuda_fail(e, "backward occupancy");
+  if (bocc < 1) {
+    set_error("backward kernel does not fit an SM (%zu bytes shared memory)", p->b_smem);
+    return FPTC_ERR_UNSUPPORTED;
+  }
+  p->b_grid = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>((uint64_t)p->sm_count * bocc, p->n_tiles));
+  return FPTC_OK;
+}
+
+fptc_status upload_layout(fptc_plan *p) {
+  cudaError_t e;
+  if (p->d_segs) {
+    e = cudaMemcpy(p->d_segs, p->segs.data(), p->segs.size() * sizeof(SegDev), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e, "upload segments");
+    e = cudaMemcpy(p->d_domains, p->dom_dev.data(), p->dom_dev.size() * sizeof(DomainDev), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e, "upload domains");
+  }
+  if (p->n_tiles > p->tiles_capacity) {
+    if (p->d_tiles) {
+      cudaFree(p->d_tiles);
+      p->device_bytes -= p->tiles_capacity * sizeof(TileRec);
+      p->d_tiles = nullptr;
+    }
+    const uint64_t cap = std::max<uint64_t>(p->n_tiles, 1);
+    e = cudaMalloc(&p->d_tiles, cap * sizeof(TileRec));
+    if (e != cudaSuccess) return cuda_fail(e, "tile table");
+    p->tiles_capacity = cap;
+    p->device_bytes += cap * sizeof(TileRec);
+  }
+  return FPTC_OK;
+}
+
+IndexParams index_params(const fptc_plan *p, const uint8_t *d_symlen) {
+  IndexParams ip{};
+  ip.symlen = d_symlen;
+  ip.segs = p->d_segs;
+  ip.domains = p->d_domains;
+  ip.chunks = p->d_chunks;
+  ip.chunk_sum = p->d_chunk_sum;
+  ip.chunk_off = p->d_chunk_off;
+  ip.seg_bad = p->d_seg_bad;
+  ip.tiles = p->d_tiles;
+  ip.status = p->d_status;
+  ip.chunk_begin = 0;
+  ip.chunk_end = p->n_chunks;
+  ip.seg_begin = 0;
+  ip.seg_end = (uint32_t)p->segs.size();
+  return ip;
+}
+
+DecodeParams decode_params(const fptc_plan *p, const uint64_t *d_words, const uint8_t *d_symlen, float *d_out,
+                           uint8_t *d_levels, const float *d_scale) {
+  DecodeParams dp{};
+  dp.words = d_words;
+  dp.symlen = d_symlen;
+  dp.out = d_out;
+  dp.levels = d_levels;
+  dp.scale = d_scale;
+  dp.segs = p->d_segs;
+  dp.domains = p->d_domains;
+  dp.luts = p->d_luts;
+  dp.basis = p->d_basis;
+  dp.tiles = p->d_tiles;
+  dp.seg_bad = p->d_seg_bad;
+  dp.status = p->d_status;
+  dp.tile_begin = 0;
+  dp.tile_end = p->n_tiles;
+  dp.seg_begin = 0;
+  dp.seg_end = (uint32_t)p->segs.size();
+  dp.lut_cap = p->lut_cap;
+  dp.coef_cap = p->coef_cap;
+  return dp;
+}
+
+// Index + decode of queue segments [s0, s1) (tiles and chunks of those segments).
+cudaError_t run_range(const fptc_plan *p, const IndexParams &ip0, const DecodeParams &dp0, uint32_t s0, uint32_t s1,
+                      bool index, cudaStream_t st) {
+  if (s1 <= s0) return cudaSuccess;
+  const SegDev &a = p->segs[s0];
+  const SegDev &b = p->segs[s1 - 1];
+  if (index) {
+    IndexParams ip = ip0;
+    ip.seg_begin = s0;
+    ip.seg_end = s1;
+    ip.chunk_begin = a.chunk_base;
+    ip.chunk_end = b.chunk_base + b.n_chunks;
+    cudaError_t e = launch_index(ip, st);
+    if (e != cudaSuccess) return e;
+  }
+  DecodeParams dp = dp0;
+  dp.seg_begin = s0;
+  dp.seg_end = s1;
+  dp.tile_begin = a.tile_base;
+  dp.tile_end = b.tile_base + b.n_tiles;
+  const uint64_t tiles = dp.tile_end - dp.tile_begin;
+  const uint32_t grid = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(p->grid, tiles));
+  return launch_decode(dp, p->kind, p->threads, grid, p->smem, st);
+}
+
+fptc_status check_plan(const fptc_plan *p) {
+  if (!p) {
+    set_error("plan is NULL");
+    return FPTC_ERR_INVALID_ARGUMENT;
+  }
+  return FPTC_OK;
+}
+
+fptc_status check_ptr(const void *ptr, size_t align, bool needed, const char *name) {
+  if (needed && !ptr) {
+    set_error("%s is NULL", name);
+    return FPTC_ERR_INVALID_ARGUMENT;
+  }
+  if (ptr && (reinterpret_cast<uintptr_t>(ptr) % align) != 0) {
+    set_error("%s must be %zu-byte aligned", name, align);
+    return FPTC_ERR_INVALID_ARGUMENT;
+  }
+  return FPTC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+uint32_t fptc_abi_version(void) { return FPTC_ABI_VERSION; }
+
+uint64_t fptc_struct_size(uint32_t which) {
+  switch (which) {
+    case 0: return sizeof(fptc_domain);
+    case 1: return sizeof(fptc_segment);
+    case 2: return sizeof(fptc_plan_options);
+    case 3: return sizeof(fptc_plan_info);
+    default: return 0;
+  }
+}
+
+const char *fptc_status_string(fptc_status s) {
+  switch (s) {
+    case FPTC_OK: return "ok";
+    case FPTC_ERR_INVALID_ARGUMENT: return "invalid argument";
+    case FPTC_ERR_UNSUPPORTED: return "unsupported";
+    case FPTC_ERR_OUT_OF_MEMORY: return "out of memory";
+    case FPTC_ERR_CUDA: return "CUDA error";
+    case FPTC_ERR_CORRUPT_STREAM: return "corrupt stream";
+  }
+  return "unknown status";
+}
+
+fptc_status fptc_plan_create(fptc_plan **out, int device, const fptc_domain *domains, uint32_t n_domains,
+                             const fptc_segment *segments, uint64_t n_segments, const fptc_plan_options *opts) {
+  clear_error();
+  if (!out) {
+    set_error("plan output pointer is NULL");
+    return FPTC_ERR_INVALID_ARGUMENT;
+  }
+  *out = nullptr;
+  if (n_domains == 0 || !domains) {
+    set_error("at least one domain is required");
+    return FPTC_ERR_INVALID_ARGUMENT;
+  }
+  if (n_segments > 0 && !segments) {
+    set_error("segments is NULL");
+    return FPTC_ERR_INVALID_ARGUMENT;
+  }
+  if (n_segments > 0xFFFFFFF0ull) {
+    set_error("too many segments");
+    return FPTC_ERR_UNSUPPORTED;
+  }
+  fptc_plan_options o{};
+  o.idct = FPTC_IDCT_FP32;
+  o.schedule = FPTC_SCHEDULE_PERSISTENT;
+  if (opts) o = *opts;
+  if (o.idct > FPTC_IDCT_BF16X3 || o.schedule > FPTC_SCHEDULE_PER_SEGMENT || o.reserved[0] || o.reserved[1]) {
+    set_error("invalid plan options");
+    return FPTC_ERR_INVALID_ARGUMENT;
+  }
+  if (o.idct != FPTC_IDCT_FP32) {
+    set_error("tensor-core inverse transform is not available in this build");
+    return FPTC_ERR_UNSUPPORTED;
+  }
+  if (o.tile_samples == 0) o.tile_samples = 4096;
+  if (o.tile_samples > 65536) {
+    set_error("tile_samples must be <= 65536");
+    return FPTC_ERR_INVALID_ARGUMENT;
+  }
+  for (uint32_t d = 0; d < n_domains; ++d) {
+    fptc_status st = fptc_validate_domain(&domains[d]);
+    if (st != FPTC_OK) {
+      std::string m = fptc_last_error_message();
+      set_error("domain %u: %s", d, m.c_str());
+      return st;
+    }
+  }
+
+  fptc_plan *p = new (std::nothrow) fptc_plan();
+  if (!p) return FPTC_ERR_OUT_OF_MEMORY;
+  p->device = device;
+  p->opts = o;
+  p->domains.assign(domains, domains + n_domains);
+  p->caller_segs.assign(segments, segments + n_segments);
+
+  // ---- segment metadata checks
+  std::vector<std::pair<uint64_t, uint64_t>> out_ranges;
+  for (uint64_t i = 0; i < n_segments; ++i) {
+    const fptc_segment &s = segments[i];
+    if (s.domain >= n_domains || s.reserved != 0) {
+      set_error("segment %llu: domain %u out of range", (unsigned long long)i, s.domain);
+      delete p;
+      return FPTC_ERR_INVALID_ARGUMENT;
+    }
+    const fptc_domain &d = domains[s.domain];
+    const uint64_t W = (s.n_samples + d.N - 1) / d.N;
+    const uint64_t L = W * d.E;
+    // each word holds 1..64 codewords (Alg. 1 never closes an empty word)
+    const uint64_t min_words = (L + 63) / 64;
+    if (s.n_words < min_words || s.n_words > L) {
+      set_error("segment %llu: %llu words cannot hold %llu symbols", (unsigned long long)i,
+                (unsigned long long)s.n_words, (unsigned long long)L);
+      delete p;
+      return FPTC_ERR_INVALID_ARGUMENT;
+    }
+    if (s.word_offset + s.n_words < s.word_offset || s.out_offset + s.n_samples < s.out_offset) {
+      set_error("segment %llu: offset overflow", (unsigned long long)i);
+      delete p;
+      return FPTC_ERR_INVALID_ARGUMENT;
+    }
+    p->words_extent = std::max(p->words_extent, s.word_offset + s.n_words);
+    p->out_extent = std::max(p->out_extent, s.out_offset + s.n_samples);
+    p->n_samples += s.n_samples;
+    p->n_words += s.n_words;
+    if (s.n_samples) out_ranges.push_back({s.out_offset, s.out_offset + s.n_samples});
+  }
+  std::sort(out_ranges.begin(), out_ranges.end());
+  for (size_t i = 1; i < out_ranges.size(); ++i) {
+    if (out_ranges[i].first < out_ranges[i - 1].second) {
+      set_error("segment output ranges overlap");
+      delete p;
+      return FPTC_ERR_INVALID_ARGUMENT;
+    }
+  }
+
+  // ---- per-domain tables on the host
+  p->dom_dev.resize(n_domains);
+  std::vector<uint16_t> luts;
+  std::vector<float> basis;
+  uint32_t max_lmax = 1;
+  p->basis_cap = 0;
+  for (uint32_t d = 0; d < n_domains; ++d) {
+    const fptc_domain &dm = domains[d];
+    DomainDev &dd = p->dom_dev[d];
+    std::memset(&dd, 0, sizeof(dd));
+    dd.N = dm.N;
+    dd.E = dm.E;
+    dd.B1 = dm.B1;
+    dd.B2 = dm.B2;
+    dd.lmax = dm.lmax;
+    for (int z = 0; z < 3; ++z) dd.scale[z] = static_cast<float>(dm.scale[z]);
+    unit_tables(dm, dd.unit);
+    max_lmax = std::max(max_lmax, dm.lmax);
+    while (luts.size() % 8) luts.push_back(0);  // 16-byte aligned table starts
+    dd.lut_offset = (uint32_t)luts.size();
+    luts.resize(luts.size() + (size_t(1) << dm.lmax));
+    fptc_build_decode_table(&dm, luts.data() + dd.lut_offset);
+    while (basis.size() % 4) basis.push_back(0.f);
+    dd.basis_offset = (uint32_t)basis.size();
+    for (uint32_t k = 0; k < dm.E; ++k)
+      for (uint32_t n = 0; n < dm.N; ++n)
+        basis.push_back(k == 0 ? 0.5f
+                               : static_cast<float>(std::cos(M_PI * (2.0 * n + 1.0) * k / (2.0 * dm.N))));
+    p->basis_cap = std::max(p->basis_cap, dm.N * dm.E);
+  }
+  p->lut_cap = 1u << max_lmax;
+  bool fixed = !o.generic;
+  for (const auto &dm : p->domains) fixed = fixed && dm.N == 32 && dm.E == 16;
+  p->kind = fixed ? 1 : 0;
+
+  // ---- tile queue: segments ordered by output offset
+  p->queue.resize(n_segments);
+  std::iota(p->queue.begin(), p->queue.end(), 0u);
+  std::stable_sort(p->queue.begin(), p->queue.end(), [&](uint32_t a, uint32_t b) {
+    return segments[a].out_offset < segments[b].out_offset;
+  });
+  p->level_off.resize(n_segments);
+  uint64_t lv = 0;
+  for (uint64_t i = 0; i < n_segments; ++i) {
+    const fptc_domain &d = domains[segments[i].domain];
+    p->level_off[i] = lv;
+    lv += (segments[i].n_samples + d.N - 1) / d.N * d.E;
+  }
+  p->n_levels = lv;
+  p->segs.resize(n_segments);
+  uint64_t chunk = 0;
+  for (uint64_t qi = 0; qi < n_segments; ++qi) {
+    const uint32_t ci = p->queue[qi];
+    const fptc_segment &s = segments[ci];
+    const fptc_domain &d = domains[s.domain];
+    SegDev &sd = p->segs[qi];
+    std::memset(&sd, 0, sizeof(sd));
+    sd.word_offset = s.word_offset;
+    sd.n_words = s.n_words;
+    sd.n_samples = s.n_samples;
+    sd.out_offset = s.out_offset;
+    sd.level_offset = p->level_off[ci];
+    sd.n_windows = (s.n_samples + d.N - 1) / d.N;
+    sd.domain = s.domain;
+    sd.caller_index = ci;
+    sd.out_aligned = (s.out_offset % 4) == 0;
+    sd.chunk_base = chunk;
+    sd.n_chunks = (uint32_t)((s.n_words + kChunkWords - 1) / kChunkWords);
+    for (uint32_t c = 0; c < sd.n_chunks; ++c) {
+      ChunkDev ch;
+      ch.word_begin = s.word_offset + (uint64_t)c * kChunkWords;
+      ch.n_words = (uint32_t)std::min<uint64_t>(kChunkWords, s.n_words - (uint64_t)c * kChunkWords);
+      ch.seg = (uint32_t)qi;
+      p->chunks.push_back(ch);
+    }
+    chunk += sd.n_chunks;
+  }
+  p->n_chunks = chunk;
+  layout_tiles(p, o.tile_samples);
+
+  // ---- device
+  fptc_status st = FPTC_OK;
+  {
+    DeviceGuard g(device);
+    if (!g.ok) {
+      set_error("cannot select device %d", device);
+      delete p;
+      return FPTC_ERR_CUDA;
+    }
+    cudaError_t e = cudaDeviceGetAttribute(&p->sm_count, cudaDevAttrMultiProcessorCount, device);
+    if (e != cudaSuccess) {
+      st = cuda_fail(e, "device query");
+      delete p;
+      return st;
+    }
+    size_t b = 0;
+    if ((e = upload(&p->d_domains, p->dom_dev, &b)) != cudaSuccess ||
+        (e = upload(&p->d_segs, p->segs, &b)) != cudaSuccess ||
+        (e = upload(&p->d_chunks, p->chunks, &b)) != cudaSuccess ||
+        (e = upload(&p->d_luts, luts, &b)) != cudaSuccess || (e = upload(&p->d_basis, basis, &b)) != cudaSuccess) {
+      st = cuda_fail(e, "plan upload");
+    }
+    if (st == FPTC_OK) {
+      const size_t nc = std::max<uint64_t>(p->n_chunks, 1), ns = std::max<uint64_t>(n_segments, 1);
+      if ((e = cudaMalloc(&p->d_chunk_sum, nc * 4)) != cudaSuccess ||
+          (e = cudaMalloc(&p->d_chunk_off, nc * 8)) != cudaSuccess ||
+          (e = cudaMalloc(&p->d_seg_bad, ns * 4)) != cudaSuccess ||
+          (e = cudaMalloc(&p->d_status, sizeof(DevStatus))) != cudaSuccess) {
+        st = cuda_fail(e, "plan scratch");
+      } else {
+        b += nc * 12 + ns * 4 + sizeof(DevStatus);
+        DevStatus s0{0u, 0u, ~0ull};
+        e = cudaMemcpy(p->d_status, &s0, sizeof(s0), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemset(p->d_seg_bad, 0, ns * 4);
+        if (e != cudaSuccess) st = cuda_fail(e, "plan scratch init");
+      }
+    }
+    p->device_bytes = b;
+    if (st == FPTC_OK) st = upload_layout(p);
+    if (st == FPTC_OK) st = configure_launch(p);
+    if (st == FPTC_OK) {
+      if ((e = cudaStreamCreateWithFlags(&p->aux, cudaStreamNonBlocking)) != cudaSuccess ||
+          (e = cudaEventCreateWithFlags(&p->ev[0], cudaEventDisableTiming)) != cudaSuccess ||
+          (e = cudaEventCreateWithFlags(&p->ev[1], cudaEventDisableTiming)) != cudaSuccess)
+        st = cuda_fail(e, "plan streams");
+    }
+    if (st != FPTC_OK) {
+      free_device(p);
+      delete p;
+      return st;
+    }
+  }
+  *out = p;
+  return FPTC_OK;
+}
+
+void fptc_plan_destroy(fptc_plan *p) {
+  if (!p) return;
+  {
+    DeviceGuard g(p->device);
+    cudaDeviceSynchronize();
+    free_device(p);
+  }
+  delete p;
+}
+
+fptc_status fptc_plan_get_info(const fptc_plan *p, fptc_plan_info *info) {
+  if (check_plan(p) != FPTC_OK || !info) return FPTC_ERR_INVALID_ARGUMENT;
+  std::memset(info, 0, sizeof(*info));
+  info->n_segments = p->segs.size();
+  info->n_tiles = p->n_tiles;
+  info->n_chunks = p->n_chunks;
+  info->words_extent = p->words_extent;
+  info->out_extent = p->out_extent;
+  info->n_samples_total = p->n_samples;
+  info->n_words_total = p->n_words;
+  info->n_levels_total = p->n_levels;
+  info->device_bytes = p->device_bytes;
+  info->n_domains = (uint32_t)p->domains.size();
+  info->device = (uint32_t)p->device;
+  info->sm_count = (uint32_t)p->sm_count;
+  info->threads = p->threads;
+  info->grid = p->grid;
+  info->ctas_per_sm = p->ctas_per_sm;
+  info->idct = p->opts.idct;
+  info->schedule = p->opts.schedule;
+  info->specialized = p->kind == 1;
+  info->smem_bytes = (uint32_t)p->smem;
+  return FPTC_OK;
+}
+
+fptc_status fptc_plan_level_offsets(const fptc_plan *p, uint64_t *offsets) {
+  if (check_plan(p) != FPTC_OK) return FPTC_ERR_INVALID_ARGUMENT;
+  if (!offsets && !p->level_off.empty()) {
+    set_error("offsets is NULL");
+    return FPTC_ERR_INVALID_ARGUMENT;
+  }
+  std::copy(p->level_off.begin(), p->level_off.end(), offsets);
+  return FPTC_OK;
+}
+
+uint32_t fptc_plan_launches_per_decode(const fptc_plan *p) {
+  if (!p) return 0;
+  if (p->segs.empty()) return 0;
+  if (p->opts.schedule == FPTC_SCHEDULE_PERSISTENT) return (p->n_chunks ? 3u : 1u) + 1u;
+  uint32_t n = 0;
+  for (const auto &s : p->segs) n += (s.n_chunks ? 3u : 1u) + 1u;
+  return n;
+}
+
+fptc_status fptc_decode_batch(fptc_plan *p, const uint64_t *d_words, const uint8_t *d_symlen, float *d_out,
+                              uint8_t *d_levels, const float *d_scale, fptc_stream stream) {
+  clear_error();
+  fptc_status st = check_plan(p);
+  if (st != FPTC_OK) return st;
+  if (p->segs.empty()) return FPTC_OK;
+  if ((st = check_ptr(d_words, 8, p->words_extent > 0, "d_words")) != FPTC_OK ||
+      (st = check_ptr(d_symlen, 1, p->words_extent > 0, "d_symlen")) != FPTC_OK ||
+      (st = check_ptr(d_out, 16, p->out_extent > 0, "d_out")) != FPTC_OK ||
+      (st = check_ptr(d_scale, 4, false, "d_scale")) != FPTC_OK)
+    return st;
+  DeviceGuard g(p->device);
+  if (!g.ok) return cuda_fail(cudaGetLastError(), "set device");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const IndexParams ip = index_params(p, d_symlen);
+  const DecodeParams dp = decode_params(p, d_words, d_symlen, d_out, d_levels, d_scale);
+  cudaError_t e = cudaSuccess;
+  if (p->opts.schedule == FPTC_SCHEDULE_PERSISTENT) {
+    e = run_range(p, ip, dp, 0, (uint32_t)p->segs.size(), true, s);
+  } else {
+    for (uint32_t i = 0; i < p->segs.size() && e == cudaSuccess; ++i) e = run_range(p, ip, dp, i, i + 1, true, s);
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "decode launch");
+  return FPTC_OK;
+}
+
+fptc_status fptc_decode_backward(fptc_plan *p, const uint64_t *d_words, const uint8_t *d_symlen,
+                                 const uint8_t *d_levels, const float *d_scale, const float *d_grad_out,
+                                 float *d_grad_coeffs, double *d_grad_scale, fptc_stream stream) {
+  clear_error();
+  fptc_status st = check_plan(p);
+  if (st != FPTC_OK) return st;
+  const bool redecode = d_levels == nullptr;
+  if ((st = check_ptr(d_grad_scale, 8, true, "d_grad_scale")) != FPTC_OK ||
+      (st = check_ptr(d_words, 8, redecode && p->words_extent > 0, "d_words")) != FPTC_OK ||
+      (st = check_ptr(d_symlen, 1, redecode && p->words_extent > 0, "d_symlen")) != FPTC_OK ||
+      (st = check_ptr(d_grad_out, 4, p->out_extent > 0, "d_grad_out")) != FPTC_OK ||
+      (st = check_ptr(d_grad_coeffs, 4, false, "d_grad_coeffs")) != FPTC_OK ||
+      (st = check_ptr(d_scale, 4, false, "d_scale")) != FPTC_OK)
+    return st;
+  DeviceGuard g(p->device);
+  if (!g.ok) return cuda_fail(cudaGetLastError(), "set device");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMemsetAsync(d_grad_scale, 0, p->domains.size() * 3 * sizeof(double), s);
+  if (e != cudaSuccess) return cuda_fail(e, "zero grad_scale");
+  if (p->segs.empty()) return FPTC_OK;
+  if (redecode) {
+    e = launch_index(index_params(p, d_symlen), s);
+    if (e != cudaSuccess) return cuda_fail(e, "index launch");
+  }
+  BackwardParams bp{};
+  bp.d = decode_params(p, d_words, d_symlen, nullptr, nullptr, d_scale);
+  bp.levels_in = d_levels;
+  bp.grad_out = d_grad_out;
+  bp.grad_coeffs = d_grad_coeffs;
+  bp.grad_scale = d_grad_scale;
+  bp.gx_cap = p->gx_cap;
+  bp.basis_cap = p->basis_cap;
+  e = launch_backward(bp, p->b_threads, p->b_grid, p->b_smem, s);
+  if (e != cudaSuccess) return cuda_fail(e, "backward launch");
+  return FPTC_OK;
+}
+
+fptc_status fptc_decode_host(fptc_plan *p, const uint64_t *h_words, const uint8_t *h_symlen, float *h_out,
+                             uint64_t *d_words, uint8_t *d_symlen, float *d_out, fptc_stream stream) {
+  clear_error();
+  fptc_status st = check_plan(p);
+  if (st != FPTC_OK) return st;
+  if (p->segs.empty()) return FPTC_OK;
+  const bool any_words = p->words_extent > 0, any_out = p->out_extent > 0;
+  if ((st = check_ptr(h_words, 8, any_words, "h_words")) != FPTC_OK ||
+      (st = check_ptr(h_symlen, 1, any_words, "h_symlen")) != FPTC_OK ||
+      (st = check_ptr(h_out, 4, any_out, "h_out")) != FPTC_OK ||
+      (st = check_ptr(d_words, 8, any_words, "d_words")) != FPTC_OK ||
+      (st = check_ptr(d_symlen, 1, any_words, "d_symlen")) != FPTC_OK ||
+      (st = check_ptr(d_out, 16, any_out, "d_out")) != FPTC_OK)
+    return st;
+  DeviceGuard g(p->device);
+  if (!g.ok) return cuda_fail(cudaGetLastError(), "set device");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaSuccess;
+  if (any_words) {
+    e = cudaMemcpyAsync(d_words, h_words, p->words_extent * 8, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_symlen, h_symlen, p->words_extent, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(e, "copy to device");
+  }
+  const IndexParams ip = index_params(p, d_symlen);
+  const DecodeParams dp = decode_params(p, d_words, d_symlen, d_out, nullptr, nullptr);
+  e = launch_index(ip, s);
+  if (e != cudaSuccess) return cuda_fail(e, "index launch");
+  // decode in pieces of about equal output, copy each piece back while the next one decodes
+  const uint32_t n = (uint32_t)p->segs.size();
+  const uint32_t pieces = std::min<uint32_t>(8u, n);
+  const uint64_t per = (p->n_samples + pieces - 1) / pieces;
+  uint32_t s0 = 0;
+  int k = 0;
+  while (s0 < n && e == cudaSuccess) {
+    uint32_t s1 = s0;
+    uint64_t acc = 0;
+    while (s1 < n && (acc < per || s1 == s0)) acc += p->segs[s1++].n_samples;
+    e = run_range(p, ip, dp, s0, s1, false, s);
+    if (e != cudaSuccess) break;
+    const uint64_t o0 = p->segs[s0].out_offset;
+    uint64_t o1 = o0;
+    for (uint32_t i = s0; i < s1; ++i) o1 = std::max(o1, p->segs[i].out_offset + p->segs[i].n_samples);
+    cudaEvent_t ev = p->ev[k & 1];
+    if ((e = cudaEventRecord(ev, s)) != cudaSuccess) break;
+    if ((e = cudaStreamWaitEvent(p->aux, ev, 0)) != cudaSuccess) break;
+    if (o1 > o0) e = cudaMemcpyAsync(h_out + o0, d_out + o0, (o1 - o0) * 4, cudaMemcpyDeviceToHost, p->aux);
+    // the next piece may reuse this event only after the copy above was queued
+    s0 = s1;
+    ++k;
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(p->aux);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, "end-to-end decode");
+  return FPTC_OK;
+}
+
+fptc_status fptc_plan_device_status(fptc_plan *p, uint32_t *flags, uint64_t *first_bad) {
+  clear_error();
+  fptc_status st = check_plan(p);
+  if (st != FPTC_OK) return st;
+  DeviceGuard g(p->device);
+  cudaError_t e = cudaDeviceSynchronize();
+  DevStatus h{};
+  if (e == cudaSuccess) e = cudaMemcpy(&h, p->d_status, sizeof(h), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) {
+    DevStatus s0{0u, 0u, ~0ull};
+    e = cudaMemcpy(p->d_status, &s0, sizeof(s0), cudaMemcpyHostToDevice);
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "read device status");
+  if (flags) *flags = h.flags;
+  if (first_bad) *first_bad = h.flags ? (uint64_t)h.first_bad : UINT64_MAX;
+  if (h.flags) {
+    set_error("device found a malformed stream (flags 0x%x, first segment %llu)", h.flags,
+              (unsigned long long)h.first_bad);
+    return FPTC_ERR_CORRUPT_STREAM;
+  }
+  return FPTC_OK;
+}
+
+fptc_status fptc_plan_autotune(fptc_plan *p, const uint64_t *d_words, const uint8_t *d_symlen, float *d_out,
+                               uint32_t trials, fptc_stream stream, fptc_plan_options *best, float *best_ms) {
+  clear_error();
+  fptc_status st = check_plan(p);
+  if (st != FPTC_OK) return st;
+  if (trials == 0) trials = 3;
+  DeviceGuard g(p->device);
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const fptc_plan_options keep = p->opts;
+  const uint32_t tiles[] = {2048, 4096, 8192};
+  const uint32_t thr[] = {128, 256, 512};
+  fptc_plan_options win = keep;
+  float win_ms = 1e30f;
+  cudaEvent_t a, b;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  for (uint32_t ts : tiles) {
+    for (uint32_t th : thr) {
+      p->opts = keep;
+      p->opts.tile_samples = ts;
+      p->opts.threads = th;
+      p->opts.ctas_per_sm = 0;
+      layout_tiles(p, ts);
+      if (upload_layout(p) != FPTC_OK || configure_launch(p) != FPTC_OK) continue;
+      if (fptc_decode_batch(p, d_words, d_symlen, d_out, nullptr, nullptr, stream) != FPTC_OK) continue;
+      std::vector<float> ms;
+      for (uint32_t t = 0; t < trials; ++t) {
+        cudaEventRecord(a, s);
+        fptc_decode_batch(p, d_words, d_symlen, d_out, nullptr, nullptr, stream);
+        cudaEventRecord(b, s);
+        cudaEventSynchronize(b);
+        float m = 0;
+        cudaEventElapsedTime(&m, a, b);
+        ms.push_back(m);
+      }
+      std::sort(ms.begin(), ms.end());
+      const float med = ms[ms.size() / 2];
+      if (med < win_ms) {
+        win_ms = med;
+        win = p->opts;
+      }
+    }
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  p->opts = win;
+  layout_tiles(p, win.tile_samples);
+  st = upload_layout(p);
+  if (st == FPTC_OK) st = configure_launch(p);
+  if (st != FPTC_OK) return st;
+  if (best) *best = win;
+  if (best_ms) *best_ms = win_ms;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "autotune");
+  return FPTC_OK;
+}
+
+}  // extern "C"
