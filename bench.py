@@ -1,0 +1,422 @@
+"""Benchmark of the FPTC batch decoder on one GB300 (or N, one process per GPU).
+
+One step = one decode of the whole batch: SymLen index + fused Huffman decode,
+dequantization, inverse DCT and window reassembly of every stream, with the
+compressed streams already in GPU memory (the paper's timed region, Sec. 5.1).
+
+Workload (default): 10,000 synthetic signals with log-uniform lengths in
+[4096, 4194304] samples, 2,500 per domain (EEG-like, seismic, power-grid,
+meteorological), Table 1 parameters, encoded on the host by the library's own
+encoder with tables trained on disjoint seeds.  Prints one JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl reference]
+
+--impl reference times the FP64 CPU oracle decoder on the host cores on a
+bounded sample of the same workload (the reference arm of this build).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import siggen  # noqa: E402
+
+METRIC = "decoded GB/s (float32 out)"
+UNIT = "GB/s"
+PARAMS = dict(N=32, E=16, B1=2, B2=16, mu=50.0, alpha1=0.004, lmax=12, percentile=99.9)
+L2_BYTES = 129 * 2 ** 20
+
+
+def workload(name: str, rank: int = 0) -> siggen.Workload:
+    if name == "mixed":
+        wl = siggen.mixed_10000_logu()
+    elif name == "eeg2048":
+        wl = siggen.eeg_2048x1m()
+    elif name == "seismic":
+        wl = siggen.seismic_16384x4096()
+    elif name == "power":
+        wl = siggen.power_1024x65536()
+    elif name == "eeg1":
+        wl = siggen.eeg_1x65536()
+    elif name == "mixed_small":
+        wl = siggen.mixed_10000_logu(n=400, lo=4096, hi=262144)
+    elif name == "mixed_medium":
+        wl = siggen.mixed_10000_logu(n=2000, lo=4096, hi=524288)
+    else:
+        raise SystemExit(f"unknown workload {name}")
+    if rank:  # weak scaling: every rank decodes its own batch of the same shape, other seeds
+        wl.seeds = np.array([siggen.splitmix64(int(s) + 0x9E3779B97F4A7C15 * rank & (2 ** 64 - 1))
+                             for s in wl.seeds], dtype=np.uint64)
+    return wl
+
+
+def train_tables():
+    from paper_2605_01086_gb300 import codec
+    doms = []
+    for d in range(4):
+        ts = siggen.training_set(d)
+        flat, offs = siggen.signals(ts.domains, ts.seeds, ts.lengths)
+        p = PARAMS
+        doms.append(codec.train_domain(flat, offs, ts.lengths, p["N"], p["E"], p["B1"], p["B2"], p["mu"],
+                                       p["alpha1"], p["lmax"], p["percentile"]))
+    return doms
+
+
+def encode(wl: siggen.Workload, doms, chunk_samples: int = 1 << 29):
+    """Generate + encode in chunks of about chunk_samples samples (bounded host memory)."""
+    from paper_2605_01086_gb300 import codec
+    parts = []
+    i = 0
+    n = wl.n_streams
+    while i < n:
+        j = i
+        acc = 0
+        while j < n and (acc < chunk_samples or j == i):
+            acc += int(wl.lengths[j])
+            j += 1
+        sub = wl.subset(np.arange(i, j))
+        flat, offs = siggen.signals(sub.domains, sub.seeds, sub.lengths)
+        parts.append(codec.encode_batch(doms, flat, offs, sub.lengths, sub.domains.astype(np.uint32)))
+        del flat
+        i = j
+    words = np.concatenate([p.words for p in parts])
+    symlen = np.concatenate([p.symlen for p in parts])
+    nw = np.concatenate([p.segments["n_words"] for p in parts])
+    woff = np.zeros(n, np.uint64)
+    woff[1:] = np.cumsum(nw[:-1])
+    segs = codec.segments_array(woff, nw, wl.lengths, codec.packed_out_offsets(wl.lengths), wl.domains)
+    return codec.Batch(words, symlen, segs, doms)
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        self.proc.wait()
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) >= 9:
+                rows.append(f)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows),
+                "power_w_max": max(float(r[3]) for r in rows if r[3].replace(".", "").isdigit())
+                if any(r[3].replace(".", "").isdigit() for r in rows) else None}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            j = json.load(f)
+        return float(j["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def oracle_sample_time(batch, idx, n_threads):
+    """Times the FP64 CPU oracle decoder on the streams idx (OpenMP over streams)."""
+    import oracle
+    ods = [oracle.Domain(d.N, d.E, d.B1, d.B2, d.mu, d.alpha1, tuple(d.scale), d.lmax, d.code_len)
+           for d in batch.domains]
+    segs = batch.segments
+    ob = oracle.EncodedBatch(batch.words, batch.symlen, segs["word_offset"].copy(), segs["n_words"].copy(),
+                             segs["n_samples"].copy(), segs["domain"].astype(np.int32), ods)
+    t = time.perf_counter()
+    oracle.decode_many(ob, idx, n_threads=n_threads)
+    return time.perf_counter() - t
+
+
+def cpu_sample(batch, target_s: float, seed: int = 0):
+    """A bounded random sample of streams sized for about target_s seconds of oracle time."""
+    n_threads = os.cpu_count() or 1
+    rng = np.random.default_rng(seed)
+    order = rng.permutation(len(batch.segments))
+    S = batch.segments["n_samples"].astype(np.float64)
+    # calibrate on ~1/200 of the samples
+    k = 1
+    while k < len(order) and S[order[:k]].sum() < S.sum() / 200:
+        k += 1
+    t = oracle_sample_time(batch, order[:k], n_threads)
+    rate = S[order[:k]].sum() / max(t, 1e-6)  # samples / s
+    want = rate * target_s
+    m = int(np.searchsorted(np.cumsum(S[order]), want)) + 1
+    return order[:min(m, len(order))], n_threads
+
+
+def run_reference(args):
+    """Reference arm: the FP64 CPU oracle on the host cores, bounded sample per step."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    wl = workload(args.workload)
+    doms = train_tables()
+    batch = encode(wl, doms)
+    idx, n_threads = cpu_sample(batch, target_s=args.ref_seconds)
+    samples = int(batch.segments["n_samples"][idx].sum())
+    for _ in range(args.warmup):
+        oracle_sample_time(batch, idx[: max(1, len(idx) // 8)], n_threads)
+    ts = [oracle_sample_time(batch, idx, n_threads) for _ in range(args.steps)]
+    ms = 1000 * statistics.mean(ts)
+    value = 4.0 * samples / (ms / 1000) / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wl.name, "n_streams": wl.n_streams, "n_samples": wl.n_samples},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": n_threads, "kind": "oracle",
+                             "sample": f"{len(idx)} of {wl.n_streams} streams, {samples} samples per step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def time_steps(fn, steps, stream, torch):
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for a, b in evs:
+        a.record(stream)
+        fn()
+        b.record(stream)
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in evs]
+
+
+def run(args):
+    import torch
+
+    from paper_2605_01086_gb300 import STAGE_DECODE, STAGE_INDEX, Plan
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world != args.gpus:
+        raise SystemExit(f"--gpus {args.gpus} but WORLD_SIZE {world}")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    t_setup = time.perf_counter()
+    wl = workload(args.workload, rank)
+    doms = train_tables()
+    batch = encode(wl, doms)
+    t_encode = time.perf_counter() - t_setup
+    n_samples = batch.n_samples
+    out_bytes = 4 * n_samples
+    in_bytes = 9 * int(batch.segments["n_words"].sum())
+
+    t0 = time.perf_counter()
+    plan = Plan(doms, batch.segments, device=local)
+    t_plan = time.perf_counter() - t0
+    w, s = plan.to_device(batch.words, batch.symlen)
+    out = plan.empty_out().zero_()
+    stream = torch.cuda.Stream(dev)
+    tuned, tuned_ms = None, None
+    with torch.cuda.stream(stream):
+        if not args.no_autotune:
+            tuned, tuned_ms = plan.autotune(w, s, out, trials=3, stream=stream)
+        plan.decode(w, s, out=out, stream=stream)
+    torch.cuda.synchronize()
+    if plan.device_status()[0] != 0:
+        raise SystemExit("device reported a corrupt stream")
+
+    # one graph = one step (index + decode launches)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=stream):
+        plan.decode(w, s, out=out, stream=stream)
+    torch.cuda.synchronize()
+
+    def step():
+        graph.replay()
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        trials = time_steps(step, args.steps, stream, torch)
+        start.record(stream)
+        for _ in range(args.steps):
+            step()
+        end.record(stream)
+    torch.cuda.synchronize()
+    total_ms = start.elapsed_time(end)
+    # stage breakdown on the same stream: the fused decode kernel alone, the index alone
+    with torch.cuda.stream(stream):
+        dec_ms = time_steps(lambda: plan.decode_stages(w, s, out, STAGE_DECODE, stream=stream), args.steps,
+                            stream, torch)
+        idx_ms = time_steps(lambda: plan.decode_stages(w, s, out, STAGE_INDEX, stream=stream), args.steps,
+                            stream, torch)
+    clk = clocks.stop()
+    if dist:
+        dist.barrier()
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = world * out_bytes / (ms_per_step / 1e3) / 1e9
+    if plan.device_status()[0] != 0:
+        raise SystemExit("device reported a corrupt stream")
+
+    # accuracy: PRD of a few streams against their original signals
+    idx = np.random.default_rng(1).choice(wl.n_streams, size=min(8, wl.n_streams), replace=False)
+    num = den = 0.0
+    for i in idx:
+        x = siggen.signal(int(wl.domains[i]), int(wl.seeds[i]), int(wl.lengths[i])).astype(np.float64)
+        xh = plan.segment_view(out, int(i)).double().cpu().numpy()
+        num += float(np.sum((x - xh) ** 2))
+        den += float(np.sum(x ** 2))
+    prd = 100.0 * (num / den) ** 0.5
+
+    peak, peak_kind = measured_peaks()
+    dec_avg = statistics.mean(dec_ms)
+    achieved = (out_bytes + in_bytes) / (dec_avg / 1e3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "peak_kind": peak_kind, "traffic": args.traffic, "kernel": "k_decode (fused decode)",
+                "algorithmic_bytes_per_launch": out_bytes + in_bytes, "launch_ms": dec_avg,
+                "index_ms": statistics.mean(idx_ms), "nominal_frac": achieved / 7900.0}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": wl.name, "n_streams": wl.n_streams, "n_samples": n_samples,
+                       "out_bytes": out_bytes, "compressed_bytes": in_bytes, "params": PARAMS,
+                       "domains": "eeg,seismic,power,met", "schedule": "persistent, CUDA graph",
+                       "tuning": tuned, "l2": "no flush: inputs + outputs "
+                       f"{(out_bytes + in_bytes) / 2 ** 30:.1f} GiB >> L2 129 MB",
+                       "setup_s": {"generate_encode": round(t_encode, 1), "plan": round(t_plan, 3)}},
+            "trials_ms": {"median": statistics.median(trials), "mean": statistics.mean(trials), "min": min(trials),
+                          "max": max(trials), "n": len(trials)},
+            "roofline": roofline, "gpu_launches": args.steps * plan.launches_per_decode, "clocks": clk,
+            "prd_percent_sample": prd}
+
+    # plain baseline: one set of launches per stream, same streams, same output
+    if not args.no_plain and rank == 0:
+        pplan = Plan(doms, batch.segments, device=local, schedule="per_segment")
+        out2 = torch.zeros_like(out)
+        with torch.cuda.stream(stream):
+            pplan.decode(w, s, out=out2, stream=stream)
+            pms = time_steps(lambda: pplan.decode(w, s, out=out2, stream=stream), 3, stream, torch)
+        torch.cuda.synchronize()
+        same = bool(torch.equal(out, out2))
+        pv = out_bytes / (statistics.mean(pms) / 1e3) / 1e9
+        line["plain"] = {"value": pv, "unit": UNIT, "ms_per_step": statistics.mean(pms),
+                         "launches_per_step": pplan.launches_per_decode, "identical_output": same,
+                         "batched_over_plain": value / world / pv}
+        pplan.close()
+        del out2
+
+    # end to end through the C ABI with host buffers: H2D of the compressed
+    # batch + decode + D2H of every sample, inside the timed region
+    if not args.no_e2e:
+        h_w = torch.from_numpy(batch.words.view(np.int64)).pin_memory()
+        h_s = torch.from_numpy(batch.symlen).pin_memory()
+        h_o = torch.empty(out.numel(), dtype=torch.float32).pin_memory()
+        plan.decode_host(h_w, h_s, h_o, w, s, out, stream=stream)  # warm-up
+        e2e = []
+        for _ in range(args.e2e_steps):
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            plan.decode_host(h_w, h_s, h_o, w, s, out, stream=stream)
+            e2e.append(time.perf_counter() - t)
+        e_s = statistics.mean(e2e)
+        if dist:
+            tt = torch.tensor([e_s], device=dev, dtype=torch.float64)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            e_s = float(tt.item())
+        line["e2e"] = {"value": world * out_bytes / e_s / 1e9, "unit": UNIT, "h2d_bytes_per_step": in_bytes,
+                       "d2h_bytes_per_step": 4 * plan.info["out_extent"], "steps": args.e2e_steps,
+                       "api": "fptc_decode_host (pinned host buffers)"}
+        del h_w, h_s, h_o
+
+    if rank == 0 and not args.no_cpu:
+        idxs, n_threads = cpu_sample(batch, target_s=args.cpu_seconds)
+        t = oracle_sample_time(batch, idxs, n_threads)
+        smp = int(batch.segments["n_samples"][idxs].sum())
+        line["cpu_baseline"] = {"value": 4.0 * smp / t / 1e9, "unit": UNIT, "cores": n_threads, "kind": "oracle",
+                                "sample": f"{len(idxs)} random streams of the workload, {smp} samples, "
+                                          f"{t:.1f} s, FP64 bit-serial decode, OpenMP over streams"}
+    plan.close()
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="fptc", choices=["fptc", "reference"])
+    ap.add_argument("--workload", default="mixed")
+    ap.add_argument("--traffic", type=float, default=None, help="ncu DRAM bytes per decode launch, if measured")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--ref-seconds", type=float, default=12.0)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -93,8 +93,9 @@ typedef struct fptc_segment {
 
 typedef enum fptc_idct {
   FPTC_IDCT_FP32 = 0,    /* FP32 FMAs on the CUDA cores */
-  FPTC_IDCT_TF32 = 1,    /* tensor cores (tcgen05, kind::tf32), FP32 accumulate */
-  FPTC_IDCT_BF16X3 = 2   /* tensor cores, hi/lo BF16 split in three products, FP32 accumulate */
+  FPTC_IDCT_TF32 = 1,    /* tensor cores (tcgen05, kind::tf32), operands rounded to TF32, FP32 accumulate */
+  FPTC_IDCT_BF16X3 = 2,  /* tensor cores, hi/lo BF16 split, three products (hi*hi + lo*hi + hi*lo) */
+  FPTC_IDCT_TF32X3 = 3   /* tensor cores, big/small TF32 split, three products */
 } fptc_idct;
 
 typedef enum fptc_schedule {
@@ -102,13 +103,22 @@ typedef enum fptc_schedule {
   FPTC_SCHEDULE_PER_SEGMENT = 1  /* plain: one set of launches per segment */
 } fptc_schedule;
 
+typedef enum fptc_kernel {
+  FPTC_KERNEL_AUTO = 0,        /* warp-tile if every domain has N = 32, E = 16, else generic */
+  FPTC_KERNEL_GENERIC = 1,     /* any N, E: one block per tile, basis through L1 */
+  FPTC_KERNEL_BLOCK_TILE = 2,  /* N = 32, E = 16: one block per tile, pipelined */
+  FPTC_KERNEL_WARP_TILE = 3,   /* N = 32, E = 16: one warp per 64-window tile, no block barriers */
+  FPTC_KERNEL_TENSOR = 4       /* N = 32, E = 16, tensor-core transform; chosen by idct != FPTC_IDCT_FP32 */
+} fptc_kernel;
+
 typedef struct fptc_plan_options {
   uint32_t idct;          /* fptc_idct */
   uint32_t schedule;      /* fptc_schedule */
-  uint32_t tile_samples;  /* target output samples per tile (rounded to whole windows); 0 = 4096 */
+  uint32_t tile_samples;  /* target output samples per tile (whole windows); 0 = 8192 if every domain
+                             has N = 32, E = 16, else 4096 */
   uint32_t threads;       /* threads per CTA: 128, 256 or 512; 0 = 256 */
   uint32_t ctas_per_sm;   /* persistent CTAs per SM; 0 = as many as fit */
-  uint32_t generic;       /* 1 = force the generic (any N, E) kernel */
+  uint32_t kernel;        /* fptc_kernel: which decode kernel; 0 = choose */
   uint32_t reserved[2];   /* must be 0 */
 } fptc_plan_options;
 
@@ -132,7 +142,7 @@ typedef struct fptc_plan_info {
   uint32_t ctas_per_sm;
   uint32_t idct;
   uint32_t schedule;
-  uint32_t specialized;         /* 1 if the fixed-shape kernel serves every domain */
+  uint32_t kernel;              /* fptc_kernel in use (never AUTO) */
   uint32_t smem_bytes;          /* dynamic shared memory per CTA of the decode kernel */
 } fptc_plan_info;
 
@@ -169,6 +179,16 @@ fptc_status fptc_plan_level_offsets(const fptc_plan *plan, uint64_t *offsets);
 fptc_status fptc_decode_batch(fptc_plan *plan, const uint64_t *d_words, const uint8_t *d_symlen, float *d_out,
                               uint8_t *d_levels, const float *d_scale, fptc_stream stream);
 
+/* The stages of fptc_decode_batch run separately, for per-stage timing:
+ * FPTC_STAGE_INDEX runs the SymLen index kernels (symlen scan, tile starts),
+ * FPTC_STAGE_DECODE the fused decode kernel, which reads the tile starts the
+ * last index stage of this plan wrote (so d_symlen must be unchanged since).
+ * stages = FPTC_STAGE_INDEX | FPTC_STAGE_DECODE is fptc_decode_batch. */
+#define FPTC_STAGE_INDEX 1u
+#define FPTC_STAGE_DECODE 2u
+fptc_status fptc_decode_stages(fptc_plan *plan, const uint64_t *d_words, const uint8_t *d_symlen, float *d_out,
+                               uint8_t *d_levels, const float *d_scale, uint32_t stages, fptc_stream stream);
+
 /* Adjoint of dequantize + inverse transform + window reassembly for a loss L
  * with dL/dx = d_grad_out (same layout as d_out).  For each window and bin k < E:
  *   g_C[k] = sum_n g_x[n] * (1/2 if k = 0 else cos(pi/N (n+1/2) k)), samples past S contribute 0,
@@ -201,6 +221,7 @@ fptc_status fptc_decode_host(fptc_plan *plan, const uint64_t *h_words, const uin
 #define FPTC_FLAG_BIT_OVERRUN 2u    /* codewords ran past bit 64 of a word */
 #define FPTC_FLAG_INVALID_CODE 4u   /* a bit pattern that is no codeword (incomplete code) */
 #define FPTC_FLAG_SYMBOL_COUNT 8u   /* sum of symlen over a segment != W*E */
+#define FPTC_FLAG_TIMEOUT 16u       /* a bounded wait on a tensor-core completion barrier gave up */
 fptc_status fptc_plan_device_status(fptc_plan *plan, uint32_t *flags, uint64_t *first_bad_segment);
 
 /* Times the candidate tile sizes, CTA sizes and occupancies on the caller's

@@ -12,9 +12,11 @@ _u8, _u16, _u32, _u64, _i32 = ctypes.c_uint8, ctypes.c_uint16, ctypes.c_uint32, 
 _d, _f, _p = ctypes.c_double, ctypes.c_float, ctypes.c_void_p
 
 OK, INVALID_ARGUMENT, UNSUPPORTED, OUT_OF_MEMORY, CUDA_ERROR, CORRUPT_STREAM = range(6)
-FLAG_SYMLEN_RANGE, FLAG_BIT_OVERRUN, FLAG_INVALID_CODE, FLAG_SYMBOL_COUNT = 1, 2, 4, 8
-IDCT = {"fp32": 0, "tf32": 1, "bf16x3": 2}
+FLAG_SYMLEN_RANGE, FLAG_BIT_OVERRUN, FLAG_INVALID_CODE, FLAG_SYMBOL_COUNT, FLAG_TIMEOUT = 1, 2, 4, 8, 16
+STAGE_INDEX, STAGE_DECODE = 1, 2
+IDCT = {"fp32": 0, "tf32": 1, "bf16x3": 2, "tf32x3": 3}
 SCHEDULE = {"persistent": 0, "per_segment": 1}
+KERNEL = {"auto": 0, "generic": 1, "block_tile": 2, "warp_tile": 3, "tensor": 4}
 
 
 class CDomain(ctypes.Structure):
@@ -29,7 +31,7 @@ class CSegment(ctypes.Structure):
 
 class CPlanOptions(ctypes.Structure):
     _fields_ = [("idct", _u32), ("schedule", _u32), ("tile_samples", _u32), ("threads", _u32),
-                ("ctas_per_sm", _u32), ("generic", _u32), ("reserved", _u32 * 2)]
+                ("ctas_per_sm", _u32), ("kernel", _u32), ("reserved", _u32 * 2)]
 
 
 class CPlanInfo(ctypes.Structure):
@@ -37,7 +39,7 @@ class CPlanInfo(ctypes.Structure):
                 ("out_extent", _u64), ("n_samples_total", _u64), ("n_words_total", _u64),
                 ("n_levels_total", _u64), ("device_bytes", _u64), ("n_domains", _u32), ("device", _u32),
                 ("sm_count", _u32), ("threads", _u32), ("grid", _u32), ("ctas_per_sm", _u32), ("idct", _u32),
-                ("schedule", _u32), ("specialized", _u32), ("smem_bytes", _u32)]
+                ("schedule", _u32), ("kernel", _u32), ("smem_bytes", _u32)]
 
 
 class FptcError(RuntimeError):
@@ -53,6 +55,7 @@ SIGNATURES = {
     "fptc_plan_get_info": (_i32, [_p, _p]),
     "fptc_plan_level_offsets": (_i32, [_p, _p]),
     "fptc_decode_batch": (_i32, [_p, _p, _p, _p, _p, _p, _p]),
+    "fptc_decode_stages": (_i32, [_p, _p, _p, _p, _p, _p, _u32, _p]),
     "fptc_decode_backward": (_i32, [_p, _p, _p, _p, _p, _p, _p, _p, _p]),
     "fptc_decode_host": (_i32, [_p, _p, _p, _p, _p, _p, _p, _p]),
     "fptc_plan_device_status": (_i32, [_p, ctypes.POINTER(_u32), ctypes.POINTER(_u64)]),

@@ -200,12 +200,11 @@ void *kernel_ptr() {
   return reinterpret_cast<void *>(&k_decode<THREADS, FIXED>);
 }
 
-void *pick(int kind, uint32_t threads) {
-  const bool fixed = kind == 1;
+void *pick(int, uint32_t threads) {
   switch (threads) {
-    case 128: return fixed ? kernel_ptr<128, true>() : kernel_ptr<128, false>();
-    case 256: return fixed ? kernel_ptr<256, true>() : kernel_ptr<256, false>();
-    case 512: return fixed ? kernel_ptr<512, true>() : kernel_ptr<512, false>();
+    case 128: return kernel_ptr<128, false>();
+    case 256: return kernel_ptr<256, false>();
+    case 512: return kernel_ptr<512, false>();
     default: return nullptr;
   }
 }

@@ -6,6 +6,8 @@
 
 #include <cuda_runtime.h>
 
+#include "fptc.h"
+
 namespace fptc {
 
 // Index work unit: the symlen array of a segment is cut into chunks of this many
@@ -21,6 +23,7 @@ constexpr unsigned int kFlagSymlenRange = 1u;
 constexpr unsigned int kFlagBitOverrun = 2u;
 constexpr unsigned int kFlagInvalidCode = 4u;
 constexpr unsigned int kFlagSymbolCount = 8u;
+constexpr unsigned int kFlagTimeout = 16u;
 
 // Per-domain tables in device memory (copied to shared memory by the kernels).
 struct DomainDev {
@@ -30,7 +33,7 @@ struct DomainDev {
   uint32_t lut_offset;     // first entry of this domain's decode table
   uint32_t basis_offset;   // first float of this domain's E x N inverse-transform basis
   float scale[3];          // the plan's A_0, A_1, A_2 rounded to float
-  uint32_t pad;
+  uint32_t complete;       // 1 if the code lengths meet Kraft with equality (no invalid prefix)
   float unit[2][256];      // reconstruction at A_z = 1 for zones 0 and 1 (FP64 -> FP32)
 };
 
@@ -104,6 +107,29 @@ struct DecodeParams {
   uint32_t coef_cap;              // tile_windows * E capacity of the shared tile buffers
 };
 
+// Shared-memory layout of the warp-tile kernel (decode_warp.cu).
+constexpr uint32_t kWarpMaxDomains = 8;
+struct WarpParams {
+  uint32_t n_domains;
+  uint32_t warp_off;    // first byte of the per-warp buffers
+  uint32_t warp_bytes;  // bytes per warp
+  uint32_t pad;
+  uint32_t lut_off[kWarpMaxDomains];  // bytes
+  uint32_t tab_off[kWarpMaxDomains];  // bytes
+};
+
+// Shared-memory layout of the tensor-core kernel (decode_tc.cu), bytes.
+struct TcParams {
+  uint32_t a_off, a_bytes;        // per-warpgroup A operands
+  uint32_t b_off;                 // B operands
+  uint32_t coef_off, coef_bytes;  // per-warp coefficient buffers
+  uint32_t misc_off;              // mbarriers, tensor-memory address
+  uint32_t dom_off;               // per-domain descriptors
+  uint32_t tab_first;             // first per-domain table
+  uint32_t n_domains;
+  uint32_t pad[3];
+};
+
 struct BackwardParams {
   DecodeParams d;              // levels/words source, segments, tables
   const uint8_t *levels_in;    // saved levels, or null: decode again
@@ -116,12 +142,34 @@ struct BackwardParams {
 
 // Launch wrappers (index.cu, decode.cu, backward.cu).
 cudaError_t launch_index(const IndexParams &p, cudaStream_t stream);
-// kind: 0 = generic, 1 = fixed N = 32, E = 16 (CUDA-core FP32)
+// generic kernel (any N, E)
 cudaError_t launch_decode(const DecodeParams &p, int kind, uint32_t threads, uint32_t grid, size_t smem,
                           cudaStream_t stream);
 cudaError_t decode_smem_config(int kind, uint32_t threads, size_t smem);
 cudaError_t decode_occupancy(int kind, uint32_t threads, size_t smem, int *ctas_per_sm);
 size_t decode_smem_bytes(int kind, uint32_t threads, uint32_t lut_cap, uint32_t coef_cap);
+
+// pipelined kernel for N = 32, E = 16 (decode_fixed.cu)
+cudaError_t launch_fixed(const DecodeParams &p, uint32_t threads, uint32_t grid, size_t smem, cudaStream_t stream);
+cudaError_t fixed_smem_config(uint32_t threads, size_t smem);
+cudaError_t fixed_occupancy(uint32_t threads, size_t smem, int *ctas_per_sm);
+size_t fixed_smem_bytes(uint32_t threads, uint32_t lut_cap, uint32_t coef_cap);
+
+// warp-tile kernel for N = 32, E = 16 (decode_warp.cu); tiles of warp_tile_windows() windows
+uint32_t warp_tile_windows();
+size_t warp_smem_layout(uint32_t threads, const uint32_t *lmax, uint32_t n_domains, WarpParams *wp);
+cudaError_t warp_smem_config(uint32_t threads, size_t smem);
+cudaError_t warp_occupancy(uint32_t threads, size_t smem, int *ctas_per_sm);
+cudaError_t launch_warp(const DecodeParams &p, const WarpParams &wp, uint32_t threads, uint32_t grid, size_t smem,
+                        cudaStream_t stream);
+
+// tensor-core kernel for N = 32, E = 16 (decode_tc.cu); mode = fptc_idct (not FP32)
+uint32_t tc_tile_windows();
+size_t tc_smem_layout(uint32_t threads, const uint32_t *lmax, uint32_t n_domains, TcParams *tp);
+cudaError_t tc_smem_config(uint32_t mode, uint32_t threads, size_t smem);
+cudaError_t tc_occupancy(uint32_t mode, uint32_t threads, size_t smem, int *ctas_per_sm);
+cudaError_t launch_tc(const DecodeParams &p, const TcParams &tp, uint32_t mode, uint32_t threads, uint32_t grid,
+                      size_t smem, cudaStream_t stream);
 
 cudaError_t launch_backward(const BackwardParams &p, uint32_t threads, uint32_t grid, size_t smem,
                             cudaStream_t stream);

@@ -45,7 +45,9 @@ struct fptc_plan {
   DevStatus *d_status = nullptr;
   size_t device_bytes = 0;
   // launch settings
-  int kind = 0;
+  int kind = FPTC_KERNEL_GENERIC;   // fptc_kernel in use
+  WarpParams wp{};
+  TcParams tp{};
   uint32_t threads = 256, grid = 0, ctas_per_sm = 0;
   size_t smem = 0;
   uint32_t lut_cap = 0, coef_cap = 0, gx_cap = 0, basis_cap = 0;
@@ -143,11 +145,36 @@ fptc_status configure_launch(fptc_plan *p) {
     return FPTC_ERR_INVALID_ARGUMENT;
   }
   p->threads = threads;
-  p->smem = decode_smem_bytes(p->kind, threads, p->lut_cap, p->coef_cap);
-  cudaError_t e = decode_smem_config(p->kind, threads, p->smem);
-  if (e != cudaSuccess) return cuda_fail(e, "decode shared-memory size");
+  cudaError_t e;
   int occ = 0;
-  e = decode_occupancy(p->kind, threads, p->smem, &occ);
+  if (p->kind == FPTC_KERNEL_BLOCK_TILE) {
+    p->smem = fixed_smem_bytes(threads, p->lut_cap, p->coef_cap);
+    e = fixed_smem_config(threads, p->smem);
+    if (e != cudaSuccess) return cuda_fail(e, "decode shared-memory size");
+    e = fixed_occupancy(threads, p->smem, &occ);
+  } else if (p->kind == FPTC_KERNEL_TENSOR) {
+    std::vector<uint32_t> lm;
+    for (const auto &d : p->domains) lm.push_back(d.lmax);
+    p->smem = tc_smem_layout(threads, lm.data(), (uint32_t)lm.size(), &p->tp);
+    e = tc_smem_config(p->opts.idct, threads, p->smem);
+    if (e != cudaSuccess) return cuda_fail(e, "decode shared-memory size");
+    e = tc_occupancy(p->opts.idct, threads, p->smem, &occ);
+    // tensor memory: 32 columns per warpgroup (rounded up to a power of two), 512 per SM
+    const uint32_t nwg = threads / 128, cols = nwg <= 1 ? 32u : (nwg == 2 ? 64u : 128u);
+    if (e == cudaSuccess) occ = std::min<int>(occ, (int)(512u / cols));
+  } else if (p->kind == FPTC_KERNEL_WARP_TILE) {
+    std::vector<uint32_t> lm;
+    for (const auto &d : p->domains) lm.push_back(d.lmax);
+    p->smem = warp_smem_layout(threads, lm.data(), (uint32_t)lm.size(), &p->wp);
+    e = warp_smem_config(threads, p->smem);
+    if (e != cudaSuccess) return cuda_fail(e, "decode shared-memory size");
+    e = warp_occupancy(threads, p->smem, &occ);
+  } else {
+    p->smem = decode_smem_bytes(p->kind, threads, p->lut_cap, p->coef_cap);
+    e = decode_smem_config(p->kind, threads, p->smem);
+    if (e != cudaSuccess) return cuda_fail(e, "decode shared-memory size");
+    e = decode_occupancy(p->kind, threads, p->smem, &occ);
+  }
   if (e != cudaSuccess) return cuda_fail(e, "decode occupancy");
   if (occ < 1) {
     set_error("decode kernel does not fit an SM (%zu bytes shared memory)", p->smem);
@@ -239,7 +266,7 @@ DecodeParams decode_params(const fptc_plan *p, const uint64_t *d_words, const ui
 
 // Index + decode of queue segments [s0, s1) (tiles and chunks of those segments).
 cudaError_t run_range(const fptc_plan *p, const IndexParams &ip0, const DecodeParams &dp0, uint32_t s0, uint32_t s1,
-                      bool index, cudaStream_t st) {
+                      bool index, cudaStream_t st, bool decode = true) {
   if (s1 <= s0) return cudaSuccess;
   const SegDev &a = p->segs[s0];
   const SegDev &b = p->segs[s1 - 1];
@@ -252,6 +279,7 @@ cudaError_t run_range(const fptc_plan *p, const IndexParams &ip0, const DecodePa
     cudaError_t e = launch_index(ip, st);
     if (e != cudaSuccess) return e;
   }
+  if (!decode) return cudaSuccess;
   DecodeParams dp = dp0;
   dp.seg_begin = s0;
   dp.seg_end = s1;
@@ -259,6 +287,9 @@ cudaError_t run_range(const fptc_plan *p, const IndexParams &ip0, const DecodePa
   dp.tile_end = b.tile_base + b.n_tiles;
   const uint64_t tiles = dp.tile_end - dp.tile_begin;
   const uint32_t grid = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(p->grid, tiles));
+  if (p->kind == FPTC_KERNEL_BLOCK_TILE) return launch_fixed(dp, p->threads, grid, p->smem, st);
+  if (p->kind == FPTC_KERNEL_WARP_TILE) return launch_warp(dp, p->wp, p->threads, grid, p->smem, st);
+  if (p->kind == FPTC_KERNEL_TENSOR) return launch_tc(dp, p->tp, p->opts.idct, p->threads, grid, p->smem, st);
   return launch_decode(dp, p->kind, p->threads, grid, p->smem, st);
 }
 
@@ -334,15 +365,34 @@ fptc_status fptc_plan_create(fptc_plan **out, int device, const fptc_domain *dom
   o.idct = FPTC_IDCT_FP32;
   o.schedule = FPTC_SCHEDULE_PERSISTENT;
   if (opts) o = *opts;
-  if (o.idct > FPTC_IDCT_BF16X3 || o.schedule > FPTC_SCHEDULE_PER_SEGMENT || o.reserved[0] || o.reserved[1]) {
+  if (o.idct > FPTC_IDCT_TF32X3 || o.schedule > FPTC_SCHEDULE_PER_SEGMENT || o.reserved[0] || o.reserved[1]) {
     set_error("invalid plan options");
     return FPTC_ERR_INVALID_ARGUMENT;
   }
-  if (o.idct != FPTC_IDCT_FP32) {
-    set_error("tensor-core inverse transform is not available in this build");
+  if (o.kernel > FPTC_KERNEL_TENSOR) {
+    set_error("unknown kernel %u", o.kernel);
+    return FPTC_ERR_INVALID_ARGUMENT;
+  }
+  bool all_fixed = true;
+  for (uint32_t d = 0; d < n_domains; ++d) all_fixed = all_fixed && domains[d].N == 32 && domains[d].E == 16;
+  const bool warp_ok = all_fixed && n_domains <= kWarpMaxDomains;
+  if ((o.kernel == FPTC_KERNEL_BLOCK_TILE && !all_fixed) || (o.kernel == FPTC_KERNEL_WARP_TILE && !warp_ok)) {
+    set_error("the fixed-shape kernels need N = 32, E = 16 in every domain (and at most %u domains for the "
+              "warp-tile kernel)", kWarpMaxDomains);
     return FPTC_ERR_UNSUPPORTED;
   }
-  if (o.tile_samples == 0) o.tile_samples = 4096;
+  if (o.idct != FPTC_IDCT_FP32 || o.kernel == FPTC_KERNEL_TENSOR) {
+    if (!warp_ok || o.idct == FPTC_IDCT_FP32) {
+      set_error("the tensor-core transform needs N = 32, E = 16 in every domain (at most %u domains) and "
+                "idct = TF32, BF16X3 or TF32X3", kWarpMaxDomains);
+      return FPTC_ERR_UNSUPPORTED;
+    }
+    o.kernel = FPTC_KERNEL_TENSOR;
+  }
+  if (o.kernel == FPTC_KERNEL_AUTO) o.kernel = warp_ok ? FPTC_KERNEL_WARP_TILE : FPTC_KERNEL_GENERIC;
+  if (o.kernel == FPTC_KERNEL_WARP_TILE) o.tile_samples = warp_tile_windows() * 32;
+  if (o.kernel == FPTC_KERNEL_TENSOR) o.tile_samples = tc_tile_windows() * 32;
+  if (o.tile_samples == 0) o.tile_samples = o.kernel == FPTC_KERNEL_BLOCK_TILE ? 8192 : 4096;
   if (o.tile_samples > 65536) {
     set_error("tile_samples must be <= 65536");
     return FPTC_ERR_INVALID_ARGUMENT;
@@ -419,6 +469,12 @@ fptc_status fptc_plan_create(fptc_plan **out, int device, const fptc_domain *dom
     dd.B2 = dm.B2;
     dd.lmax = dm.lmax;
     for (int z = 0; z < 3; ++z) dd.scale[z] = static_cast<float>(dm.scale[z]);
+    {
+      uint64_t kraft = 0;
+      for (int sy = 0; sy < 256; ++sy)
+        if (dm.code_len[sy]) kraft += uint64_t(1) << (dm.lmax - dm.code_len[sy]);
+      dd.complete = kraft == (uint64_t(1) << dm.lmax);
+    }
     unit_tables(dm, dd.unit);
     max_lmax = std::max(max_lmax, dm.lmax);
     while (luts.size() % 8) luts.push_back(0);  // 16-byte aligned table starts
@@ -434,9 +490,7 @@ fptc_status fptc_plan_create(fptc_plan **out, int device, const fptc_domain *dom
     p->basis_cap = std::max(p->basis_cap, dm.N * dm.E);
   }
   p->lut_cap = 1u << max_lmax;
-  bool fixed = !o.generic;
-  for (const auto &dm : p->domains) fixed = fixed && dm.N == 32 && dm.E == 16;
-  p->kind = fixed ? 1 : 0;
+  p->kind = (int)o.kernel;
 
   // ---- tile queue: segments ordered by output offset
   p->queue.resize(n_segments);
@@ -569,7 +623,7 @@ fptc_status fptc_plan_get_info(const fptc_plan *p, fptc_plan_info *info) {
   info->ctas_per_sm = p->ctas_per_sm;
   info->idct = p->opts.idct;
   info->schedule = p->opts.schedule;
-  info->specialized = p->kind == 1;
+  info->kernel = (uint32_t)p->kind;
   info->smem_bytes = (uint32_t)p->smem;
   return FPTC_OK;
 }
@@ -593,15 +647,20 @@ uint32_t fptc_plan_launches_per_decode(const fptc_plan *p) {
   return n;
 }
 
-fptc_status fptc_decode_batch(fptc_plan *p, const uint64_t *d_words, const uint8_t *d_symlen, float *d_out,
-                              uint8_t *d_levels, const float *d_scale, fptc_stream stream) {
+fptc_status fptc_decode_stages(fptc_plan *p, const uint64_t *d_words, const uint8_t *d_symlen, float *d_out,
+                               uint8_t *d_levels, const float *d_scale, uint32_t stages, fptc_stream stream) {
   clear_error();
   fptc_status st = check_plan(p);
   if (st != FPTC_OK) return st;
-  if (p->segs.empty()) return FPTC_OK;
-  if ((st = check_ptr(d_words, 8, p->words_extent > 0, "d_words")) != FPTC_OK ||
+  if (stages & ~(FPTC_STAGE_INDEX | FPTC_STAGE_DECODE)) {
+    set_error("unknown stage bits 0x%x", stages);
+    return FPTC_ERR_INVALID_ARGUMENT;
+  }
+  if (p->segs.empty() || !stages) return FPTC_OK;
+  const bool idx = stages & FPTC_STAGE_INDEX, dec = stages & FPTC_STAGE_DECODE;
+  if ((st = check_ptr(d_words, 8, dec && p->words_extent > 0, "d_words")) != FPTC_OK ||
       (st = check_ptr(d_symlen, 1, p->words_extent > 0, "d_symlen")) != FPTC_OK ||
-      (st = check_ptr(d_out, 16, p->out_extent > 0, "d_out")) != FPTC_OK ||
+      (st = check_ptr(d_out, 16, dec && p->out_extent > 0, "d_out")) != FPTC_OK ||
       (st = check_ptr(d_scale, 4, false, "d_scale")) != FPTC_OK)
     return st;
   DeviceGuard g(p->device);
@@ -611,12 +670,18 @@ fptc_status fptc_decode_batch(fptc_plan *p, const uint64_t *d_words, const uint8
   const DecodeParams dp = decode_params(p, d_words, d_symlen, d_out, d_levels, d_scale);
   cudaError_t e = cudaSuccess;
   if (p->opts.schedule == FPTC_SCHEDULE_PERSISTENT) {
-    e = run_range(p, ip, dp, 0, (uint32_t)p->segs.size(), true, s);
+    e = run_range(p, ip, dp, 0, (uint32_t)p->segs.size(), idx, s, dec);
   } else {
-    for (uint32_t i = 0; i < p->segs.size() && e == cudaSuccess; ++i) e = run_range(p, ip, dp, i, i + 1, true, s);
+    for (uint32_t i = 0; i < p->segs.size() && e == cudaSuccess; ++i) e = run_range(p, ip, dp, i, i + 1, idx, s, dec);
   }
   if (e != cudaSuccess) return cuda_fail(e, "decode launch");
   return FPTC_OK;
+}
+
+fptc_status fptc_decode_batch(fptc_plan *p, const uint64_t *d_words, const uint8_t *d_symlen, float *d_out,
+                              uint8_t *d_levels, const float *d_scale, fptc_stream stream) {
+  return fptc_decode_stages(p, d_words, d_symlen, d_out, d_levels, d_scale, FPTC_STAGE_INDEX | FPTC_STAGE_DECODE,
+                            stream);
 }
 
 fptc_status fptc_decode_backward(fptc_plan *p, const uint64_t *d_words, const uint8_t *d_symlen,
@@ -744,43 +809,62 @@ fptc_status fptc_plan_autotune(fptc_plan *p, const uint64_t *d_words, const uint
   DeviceGuard g(p->device);
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   const fptc_plan_options keep = p->opts;
-  const uint32_t tiles[] = {2048, 4096, 8192};
-  const uint32_t thr[] = {128, 256, 512};
+  const int keep_kind = p->kind;
+  bool fixed = true;
+  for (const auto &d : p->domains) fixed = fixed && d.N == 32 && d.E == 16;
+  struct Cand {
+    uint32_t kernel, tile_samples, threads;
+  };
+  std::vector<Cand> cands;
+  for (uint32_t th : {128u, 256u, 512u}) {
+    if (keep.idct != FPTC_IDCT_FP32) {
+      cands.push_back({FPTC_KERNEL_TENSOR, tc_tile_windows() * 32, th});
+      continue;
+    }
+    if (fixed && p->domains.size() <= kWarpMaxDomains) cands.push_back({FPTC_KERNEL_WARP_TILE, warp_tile_windows() * 32, th});
+    if (fixed)
+      for (uint32_t ts : {4096u, 8192u}) cands.push_back({FPTC_KERNEL_BLOCK_TILE, ts, th});
+    else
+      for (uint32_t ts : {2048u, 4096u, 8192u}) cands.push_back({FPTC_KERNEL_GENERIC, ts, th});
+  }
   fptc_plan_options win = keep;
+  int win_kind = keep_kind;
   float win_ms = 1e30f;
   cudaEvent_t a, b;
   cudaEventCreate(&a);
   cudaEventCreate(&b);
-  for (uint32_t ts : tiles) {
-    for (uint32_t th : thr) {
-      p->opts = keep;
-      p->opts.tile_samples = ts;
-      p->opts.threads = th;
-      p->opts.ctas_per_sm = 0;
-      layout_tiles(p, ts);
-      if (upload_layout(p) != FPTC_OK || configure_launch(p) != FPTC_OK) continue;
-      if (fptc_decode_batch(p, d_words, d_symlen, d_out, nullptr, nullptr, stream) != FPTC_OK) continue;
-      std::vector<float> ms;
-      for (uint32_t t = 0; t < trials; ++t) {
-        cudaEventRecord(a, s);
-        fptc_decode_batch(p, d_words, d_symlen, d_out, nullptr, nullptr, stream);
-        cudaEventRecord(b, s);
-        cudaEventSynchronize(b);
-        float m = 0;
-        cudaEventElapsedTime(&m, a, b);
-        ms.push_back(m);
-      }
-      std::sort(ms.begin(), ms.end());
-      const float med = ms[ms.size() / 2];
-      if (med < win_ms) {
-        win_ms = med;
-        win = p->opts;
-      }
+  for (const Cand &c : cands) {
+    p->opts = keep;
+    p->opts.kernel = c.kernel;
+    p->opts.tile_samples = c.tile_samples;
+    p->opts.threads = c.threads;
+    p->opts.ctas_per_sm = 0;
+    p->kind = (int)c.kernel;
+    layout_tiles(p, c.tile_samples);
+    if (upload_layout(p) != FPTC_OK || configure_launch(p) != FPTC_OK) continue;
+    if (fptc_decode_batch(p, d_words, d_symlen, d_out, nullptr, nullptr, stream) != FPTC_OK) continue;
+    std::vector<float> ms;
+    for (uint32_t t = 0; t < trials; ++t) {
+      cudaEventRecord(a, s);
+      fptc_decode_batch(p, d_words, d_symlen, d_out, nullptr, nullptr, stream);
+      cudaEventRecord(b, s);
+      cudaEventSynchronize(b);
+      float m = 0;
+      cudaEventElapsedTime(&m, a, b);
+      ms.push_back(m);
+    }
+    std::sort(ms.begin(), ms.end());
+    const float med = ms[ms.size() / 2];
+    if (med < win_ms) {
+      win_ms = med;
+      win = p->opts;
+      win_kind = p->kind;
     }
   }
   cudaEventDestroy(a);
   cudaEventDestroy(b);
   p->opts = win;
+  p->kind = win_kind;
   layout_tiles(p, win.tile_samples);
   st = upload_layout(p);
   if (st == FPTC_OK) st = configure_launch(p);

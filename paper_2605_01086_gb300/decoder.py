@@ -45,7 +45,7 @@ class Plan:
     n_samples, out_offset, domain (see ``codec.segments_array``)."""
 
     def __init__(self, domains, segments, device=None, idct: str = "fp32", schedule: str = "persistent",
-                 tile_samples: int = 0, threads: int = 0, ctas_per_sm: int = 0, generic: bool = False):
+                 tile_samples: int = 0, threads: int = 0, ctas_per_sm: int = 0, kernel: str = "auto"):
         if not torch.cuda.is_available():
             raise RuntimeError("the FPTC decoder needs a CUDA GPU")
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else int(device))
@@ -55,7 +55,8 @@ class Plan:
         o = CPlanOptions()
         o.idct = _lib.IDCT[idct]
         o.schedule = _lib.SCHEDULE[schedule]
-        o.tile_samples, o.threads, o.ctas_per_sm, o.generic = tile_samples, threads, ctas_per_sm, int(generic)
+        o.tile_samples, o.threads, o.ctas_per_sm = tile_samples, threads, ctas_per_sm
+        o.kernel = _lib.KERNEL[kernel]
         cds = c_domains(self.domains)
         h = ctypes.c_void_p()
         check(lib().fptc_plan_create(ctypes.byref(h), self.device.index, cds, len(self.domains),
@@ -123,6 +124,14 @@ class Plan:
             _require(scale, torch.float32, self.device, "scale", 3 * len(self.domains))
         check(lib().fptc_decode_batch(self._h, _dptr(words), _dptr(symlen), _dptr(out), _dptr(levels), _dptr(scale),
                                       _stream(stream, self.device)))
+        return out
+
+    def decode_stages(self, words, symlen, out, stages: int, levels=None, scale=None, stream=None):
+        """fptc_decode_stages: stages = STAGE_INDEX (1) | STAGE_DECODE (2)."""
+        self._check_inputs(words, symlen)
+        _require(out, torch.float32, self.device, "out", self.info["out_extent"])
+        check(lib().fptc_decode_stages(self._h, _dptr(words), _dptr(symlen), _dptr(out), _dptr(levels), _dptr(scale),
+                                       int(stages), _stream(stream, self.device)))
         return out
 
     def backward(self, grad_out, words=None, symlen=None, levels=None, scale=None, grad_coeffs=None,

@@ -143,11 +143,31 @@ void sg_eeg(uint64_t seed, float *x, uint64_t S) {
   double mean = s1 / (double)S;
   double var = s2 / (double)S - mean * mean;
   double scale = var > 0.0 ? 10.0 / sqrt(var) : 0.0;
-  for (uint64_t n = 0; n < S; ++n) {
-    double t = (double)n / 256.0;
-    double v = 0.0;
-    for (int j = 0; j < 8; ++j) v += a[j] * sin(2.0 * M_PI * f[j] * t + ph[j]);
-    x[n] = (float)(v + scale * (double)x[n]);
+  /* sinusoids: exact phase at the start of every 256-sample block, then a
+   * complex rotation per sample inside the block */
+  double cr[8], sr[8];
+  for (int j = 0; j < 8; ++j) {
+    cr[j] = cos(2.0 * M_PI * f[j] / 256.0);
+    sr[j] = sin(2.0 * M_PI * f[j] / 256.0);
+  }
+  for (uint64_t b0 = 0; b0 < S; b0 += 256) {
+    double c[8], sn[8];
+    for (int j = 0; j < 8; ++j) {
+      double ph0 = 2.0 * M_PI * f[j] * ((double)b0 / 256.0) + ph[j];
+      c[j] = cos(ph0);
+      sn[j] = sin(ph0);
+    }
+    uint64_t b1 = b0 + 256 < S ? b0 + 256 : S;
+    for (uint64_t n = b0; n < b1; ++n) {
+      double v = 0.0;
+      for (int j = 0; j < 8; ++j) {
+        v += a[j] * sn[j];
+        double c2 = c[j] * cr[j] - sn[j] * sr[j];
+        sn[j] = sn[j] * cr[j] + c[j] * sr[j];
+        c[j] = c2;
+      }
+      x[n] = (float)(v + scale * (double)x[n]);
+    }
   }
 }
 

@@ -1,7 +1,8 @@
 """GPU parity of the batch decoder against the FP64 oracle (through the C ABI):
 decoded levels bit-exact, samples within 1e-5 relative L2 per stream
 (FP32 path).  Covers the EEG stream of 65,536 samples, mixed-domain batches
-with ragged lengths, both kernels (fixed 32/16 and generic), both schedules,
+with ragged lengths, the three decode kernels (warp-tile and block-tile for
+N = 32 / E = 16, generic for any shape), both schedules,
 tile and CTA sizes, crafted codebooks (L_max-long codes, 64 one-bit codes per
 word, incomplete codes, one-symbol windows), other (N, E) shapes, misaligned
 outputs, run-time scales and corrupted streams."""
@@ -46,20 +47,26 @@ def crafted_batch(domains, levels_list, lengths, dom_idx):
 
 def test_eeg_single_stream():
     b = encode_workload(siggen.eeg_1x65536())
-    plan = make_plan(b)
-    assert plan.info["specialized"] == 1
-    _, _, out, lv = gpu_decode(plan, b)
-    compare_with_oracle(plan, b, out, lv)
-    assert plan.device_status()[0] == 0
+    for kernel in KERNELS:
+        plan = make_plan(b, kernel=kernel)
+        assert plan.info["kernel"] == KERNEL_IDS[kernel]
+        _, _, out, lv = gpu_decode(plan, b)
+        compare_with_oracle(plan, b, out, lv)
+        assert plan.device_status()[0] == 0
+    assert make_plan(b).info["kernel"] == KERNEL_IDS["warp_tile"]
 
 
-@pytest.mark.parametrize("generic", [False, True])
+KERNELS = ["warp_tile", "block_tile", "generic"]
+KERNEL_IDS = {"generic": 1, "block_tile": 2, "warp_tile": 3}
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
 @pytest.mark.parametrize("schedule", ["persistent", "per_segment"])
-def test_mixed_batch_ragged(generic, schedule):
+def test_mixed_batch_ragged(kernel, schedule):
     wl = siggen.mixed_10000_logu(n=48, lo=1, hi=200000)
     b = encode_workload(wl)
-    plan = make_plan(b, generic=generic, schedule=schedule)
-    assert plan.info["specialized"] == (0 if generic else 1)
+    plan = make_plan(b, kernel=kernel, schedule=schedule)
+    assert plan.info["kernel"] == KERNEL_IDS[kernel]
     _, _, out, lv = gpu_decode(plan, b, out_fill=float("nan"))
     compare_with_oracle(plan, b, out, lv)
     assert plan.device_status()[0] == 0
@@ -70,8 +77,8 @@ def test_mixed_batch_ragged(generic, schedule):
 def test_tile_and_cta_sizes(tile_samples, threads):
     wl = siggen.mixed_10000_logu(n=24, lo=100, hi=100000)
     b = encode_workload(wl)
-    for generic in (False, True):
-        plan = make_plan(b, tile_samples=tile_samples, threads=threads, generic=generic)
+    for kernel in KERNELS:
+        plan = make_plan(b, tile_samples=tile_samples, threads=threads, kernel=kernel)
         _, _, out, lv = gpu_decode(plan, b)
         compare_with_oracle(plan, b, out, lv)
 
@@ -83,8 +90,9 @@ def test_edge_lengths_and_misaligned_outputs():
                          np.array([siggen.stream_seed(9, i) for i in range(n)], np.uint64),
                          np.array(lengths, np.uint64))
     b = encode_workload(wl)
-    for align, base in ((4, 0), (1, 0), (1, 3)):
-        plan = make_plan(b, out_align=align, out_base=base)
+    for align, base, kernel in ((4, 0, "warp_tile"), (1, 0, "warp_tile"), (1, 3, "warp_tile"), (1, 3, "block_tile"),
+                                (1, 3, "generic")):
+        plan = make_plan(b, out_align=align, out_base=base, kernel=kernel)
         _, _, out, lv = gpu_decode(plan, b, out_fill=float("nan"))
         compare_with_oracle(plan, b, out, lv)
         # nothing outside the segments' outputs was written
@@ -121,8 +129,8 @@ def test_long_codes_lmax16():
     levels = [rng.integers(0, 256, size=((S + 31) // 32) * 16).astype(np.uint8) for S in lens]
     b = crafted_batch([o], levels, lens, [0, 0, 0])
     assert b.symlen.max() <= 13
-    for generic in (False, True):
-        plan = make_plan(b, generic=generic)
+    for kernel in KERNELS:
+        plan = make_plan(b, kernel=kernel)
         _, _, out, lv = gpu_decode(plan, b)
         compare_with_oracle(plan, b, out, lv)
 
@@ -151,7 +159,7 @@ def test_incomplete_code_and_one_symbol_windows():
     X = rng.choice(np.array([128, 120, 140], np.uint8), size=1000)
     b = crafted_batch([o1], [X, X[:1], X[:7]], [4000, 3, 27], [0, 0, 0])
     plan = make_plan(b)
-    assert plan.info["specialized"] == 0
+    assert plan.info["kernel"] == KERNEL_IDS["generic"]
     _, _, out, lv = gpu_decode(plan, b)
     compare_with_oracle(plan, b, out, lv)
 
@@ -210,16 +218,17 @@ def _eight_bit_batch():
     return crafted_batch([o], levels, lens, [0, 0, 0])
 
 
-def _run_corrupt(b):
-    plan = make_plan(b)
+def _run_corrupt(b, kernel="auto"):
+    plan = make_plan(b, kernel=kernel)
     w, s = plan.to_device(b.words, b.symlen)
     out = plan.empty_out().fill_(float("nan"))
     plan.decode(w, s, out=out)
     return plan, out, plan.device_status()
 
 
+@pytest.mark.parametrize("kernel", KERNELS)
 @pytest.mark.parametrize("case", ["symlen_range", "count", "overrun"])
-def test_corrupt_segment_is_flagged_and_confined(case):
+def test_corrupt_segment_is_flagged_and_confined(case, kernel):
     from paper_2605_01086_gb300 import _lib
     b = _eight_bit_batch()
     bad_word = int(b.word_off[1]) + 10
@@ -233,7 +242,7 @@ def test_corrupt_segment_is_flagged_and_confined(case):
         b.symlen[bad_word] += 1
         b.symlen[bad_word + 1] -= 1
         want = _lib.FLAG_BIT_OVERRUN
-    plan, out, (st, flags, first) = _run_corrupt(b)
+    plan, out, (st, flags, first) = _run_corrupt(b, kernel)
     assert st == _lib.CORRUPT_STREAM and flags & want and first == 1
     # the good segments decode exactly
     compare_with_oracle(plan, b, out, None, idx=[0, 2])
