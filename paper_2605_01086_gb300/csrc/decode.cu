@@ -219,6 +219,9 @@ size_t decode_smem_bytes(int, uint32_t threads, uint32_t lut_cap, uint32_t coef_
 cudaError_t decode_smem_config(int kind, uint32_t threads, size_t smem) {
   void *k = pick(kind, threads);
   if (!k) return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                       (int)cudaSharedmemCarveoutMaxShared);
+  if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 

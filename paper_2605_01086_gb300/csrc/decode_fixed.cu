@@ -412,6 +412,9 @@ size_t fixed_smem_bytes(uint32_t threads, uint32_t lut_cap, uint32_t coef_cap) {
 cudaError_t fixed_smem_config(uint32_t threads, size_t smem) {
   void *k = fpick(threads);
   if (!k) return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                       (int)cudaSharedmemCarveoutMaxShared);
+  if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 

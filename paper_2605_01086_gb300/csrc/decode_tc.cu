@@ -12,6 +12,9 @@
 // mbarrier; then every warp reads its 32 rows of D with tcgen05.ld (lane i of
 // warp w holds row 32w + i = one window) and stores the window's 32 samples.
 //
+// A kernel that uses tensor memory runs one CTA per SM (the occupancy the CUDA
+// runtime reports for it is 1), so all warpgroups of an SM live in one CTA.
+//
 // Precision forms (the integer decode is exact in every form):
 //   TF32    one product, operands rounded to TF32 (10-bit mantissa);
 //   TF32X3  C = C_big + C_small, B = B_big + B_small (TF32 each), three
@@ -45,19 +48,28 @@ __device__ __forceinline__ uint32_t smem_u32(const void *p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
-__device__ __forceinline__ void named_barrier(uint32_t id, uint32_t threads) {
-  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(threads) : "memory");
-}
-
-// OR of a predicate over the threads of a named barrier (and a barrier).
-__device__ __forceinline__ bool barrier_any(uint32_t id, uint32_t threads, bool v) {
+// OR of a predicate over the 128 threads of named barrier ID (and a barrier).
+// The id is a compile-time constant: a run-time id makes the compiler reserve
+// every hardware barrier of the SM for one CTA.
+template <int ID>
+__device__ __forceinline__ bool bar_any_c(bool v) {
   uint32_t r;
   asm volatile(
-      "{\n .reg .pred pi, po;\n setp.ne.u32 pi, %1, 0;\n bar.red.or.pred po, %2, %3, pi;\n selp.u32 %0, 1, 0, po;\n}\n"
+      "{\n .reg .pred pi, po;\n setp.ne.u32 pi, %1, 0;\n bar.red.or.pred po, %2, 128, pi;\n selp.u32 %0, 1, 0, po;\n}\n"
       : "=r"(r)
-      : "r"((uint32_t)v), "r"(id), "r"(threads)
+      : "r"((uint32_t)v), "n"(ID)
       : "memory");
   return r != 0;
+}
+
+// Barrier over the 128 threads of warpgroup wg (ids 1..4), returning the OR of v.
+__device__ __forceinline__ bool wg_barrier_any(uint32_t wg, bool v) {
+  switch (wg) {
+    case 0: return bar_any_c<1>(v);
+    case 1: return bar_any_c<2>(v);
+    case 2: return bar_any_c<3>(v);
+    default: return bar_any_c<4>(v);
+  }
 }
 
 __device__ __forceinline__ void fence_proxy_async_smem() {
@@ -249,7 +261,7 @@ constexpr int tc_min_blocks() {
 
 template <int MODE, int NWG>
 __global__ void __launch_bounds__(NWG * 128, tc_min_blocks<NWG>()) k_decode_tc(const DecodeParams p, const TcParams tp) {
-  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr int WPT = 2;
   const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t wg = warp >> 2, wq = warp & 3;  // warpgroup, warp within it
@@ -259,8 +271,8 @@ __global__ void __launch_bounds__(NWG * 128, tc_min_blocks<NWG>()) k_decode_tc(c
   float *const coef = reinterpret_cast<float *>(smem_raw + tp.coef_off + warp * tp.coef_bytes) + kGuard;
   uint8_t *const lev = smem_raw + tp.coef_off + warp * tp.coef_bytes + (kGuard + kTS) * 4 + kGuard;
   unsigned char *const b_base = smem_raw + tp.b_off;                             // B operand(s)
-  uint64_t *const mbar = reinterpret_cast<uint64_t *>(smem_raw + tp.misc_off);   // [NWG]
-  uint32_t *const tmem_slot = reinterpret_cast<uint32_t *>(smem_raw + tp.misc_off + 8 * NWG);
+  uint64_t *const mbar = reinterpret_cast<uint64_t *>(smem_raw + tp.misc_off);   // [NWG][2]
+  uint32_t *const tmem_slot = reinterpret_cast<uint32_t *>(smem_raw + tp.misc_off + 16 * NWG);
   DomTc *const ds = reinterpret_cast<DomTc *>(smem_raw + tp.dom_off);
 
   const uint64_t n_all = p.tile_end - p.tile_begin;
@@ -319,10 +331,10 @@ __global__ void __launch_bounds__(NWG * 128, tc_min_blocks<NWG>()) k_decode_tc(c
     }
   }
   if (threadIdx.x == 0) {
-    for (int i = 0; i < NWG; ++i) mbar_init(smem_u32(mbar + i), 1);
+    for (int i = 0; i < 2 * NWG; ++i) mbar_init(smem_u32(mbar + i), 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  constexpr uint32_t kCols = NWG == 1 ? 32u : (NWG == 2 ? 64u : 128u);
+  constexpr uint32_t kCols = NWG == 1 ? 64u : (NWG == 2 ? 128u : 256u);  // two 32-column D per warpgroup
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
                  "r"(kCols)
@@ -334,23 +346,81 @@ __global__ void __launch_bounds__(NWG * 128, tc_min_blocks<NWG>()) k_decode_tc(c
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
-  const uint32_t d_tmem = tmem + wg * 32u;                 // this warpgroup's 32 columns
+  const uint32_t d_tmem = tmem + wg * 64u;                 // this warpgroup's two 32-column D buffers
   const uint32_t my_tmem = d_tmem + ((wq * 32u) << 16);    // lanes 32 wq .. 32 wq + 31
 
   const bool want_lev = p.levels != nullptr;
-  unsigned err = 0;
-  uint32_t phase = 0;
+  uint32_t phase[2] = {0u, 0u};
   bool timeout = false;
 
-  // ---- warpgroup tiles: 4 consecutive warp tiles g = t0 + 4 G + wq, G = wg, wg + NWG, ...
-  for (uint64_t G = wg;; G += NWG) {
-    const uint64_t gbase = t0 + 4 * G;
-    if (gbase >= t1) break;  // uniform over the warpgroup
-    const uint64_t g = gbase + wq;
-    EpiCtx ep{nullptr, 0, 0, 0, 0};
+  // Warpgroup tile k = 4 consecutive warp tiles t0 + 4 (wg + k NWG) + wq.  The
+  // pipeline: decode tile k+1 into A[(k+1) & 1] while the products of tile k
+  // run on the tensor core into D[k & 1]; then wait, store tile k, barrier,
+  // issue tile k+1.
+  auto gbase_of = [&](uint64_t k) -> uint64_t { return t0 + 4 * (wg + k * NWG); };
+  EpiCtx ep0{nullptr, 0, 0, 0, 0}, ep1{nullptr, 0, 0, 0, 0};  // per A/D buffer (no dynamic index: registers)
+
+  // Per-warp prefetch state: the segment cursor, the context and words of the
+  // next tile this warp decodes, the context of the one after (records only).
+  uint32_t s_cur = find_segment(p.segs, p.seg_begin, p.seg_end, min(gbase_of(0) + wq, t1 - 1));
+  bool bad_cur = true, bad_nxt = true;
+  uint32_t s_nxt = s_cur;
+  TcTile cx_cur{0, 0, 0}, cx_nxt{0, 0, 0};
+  uint64_t pw[WPT];
+  uint32_t psl[WPT];
+  // context of warp tile g (segment cursor s advanced to it); records only
+  auto ctx_of = [&](uint64_t g, uint32_t &s, bool &bad, TcTile &cx) {
+    bad = true;
+    if (g >= t1) return;
+    while (g >= p.segs[s].tile_base + p.segs[s].n_tiles) ++s;
+    bad = p.seg_bad[s] != 0;
+    if (bad) return;
+    const SegDev &sg = p.segs[s];
+    const uint64_t tin = g - sg.tile_base;
+    TileRec rn{0, 0, 0};
+    if (tin + 1 < sg.n_tiles) rn = p.tiles[g + 1];
+    cx = tc_ctx(sg, tin, p.tiles[g], rn);
+  };
+  auto load_words = [&](bool bad, const TcTile &cx) {
+#pragma unroll
+    for (int u = 0; u < WPT; ++u) {
+      const uint32_t i = lane * WPT + u;
+      const bool in = !bad && i < cx.nw;
+      psl[u] = in ? (uint32_t)__ldg(p.symlen + cx.fw + i) : 0u;
+      pw[u] = in ? __ldg(p.words + cx.fw + i) : 0ull;
+    }
+  };
+  ctx_of(gbase_of(0) + wq, s_cur, bad_cur, cx_cur);
+  load_words(bad_cur, cx_cur);
+  s_nxt = s_cur;
+  ctx_of(gbase_of(1) + wq, s_nxt, bad_nxt, cx_nxt);
+
+  // decode + repack of warpgroup tile k (whose context and words are loaded)
+  // into A buffer `buf`; then start the loads of tile k+1 and the records of
+  // tile k+2
+  auto produce = [&](uint64_t k, uint32_t buf) {
+    const uint64_t g = gbase_of(k) + wq;
+    EpiCtx e{nullptr, 0, 0, 0, 0};
+    unsigned err = 0;
+    uint64_t wd0[WPT];
+    uint32_t sl0[WPT];
+#pragma unroll
+    for (int u = 0; u < WPT; ++u) {
+      wd0[u] = pw[u];
+      sl0[u] = psl[u];
+    }
+    const bool bad = bad_cur;
+    const uint32_t s = s_cur;
+    const TcTile cx = cx_cur;
+    // rotate the prefetch: words of tile k+1 now, records of tile k+2
+    s_cur = s_nxt;
+    bad_cur = bad_nxt;
+    cx_cur = cx_nxt;
+    load_words(bad_cur, cx_cur);
+    s_nxt = s_cur;
+    ctx_of(gbase_of(k + 2) + wq, s_nxt, bad_nxt, cx_nxt);
     if (g < t1) {
-      const uint32_t s = find_segment(p.segs, p.seg_begin, p.seg_end, g);
-      if (!p.seg_bad[s]) {
+      if (!bad) {
         const SegDev &sg = p.segs[s];
         const DomTc dd = ds[sg.domain];
         const uint64_t tin = g - sg.tile_base;
@@ -358,9 +428,6 @@ __global__ void __launch_bounds__(NWG * 128, tc_min_blocks<NWG>()) k_decode_tc(c
         const uint64_t left = sg.n_windows - win0;
         const uint32_t nwin = left < (uint64_t)kT ? (uint32_t)left : (uint32_t)kT;
         const int32_t tsyms = (int32_t)(nwin * kE);
-        TileRec rn{0, 0, 0};
-        if (tin + 1 < sg.n_tiles) rn = p.tiles[g + 1];
-        const TcTile cx = tc_ctx(sg, tin, p.tiles[g], rn);
         const uint16_t *lut = reinterpret_cast<const uint16_t *>(smem_raw + dd.lut_off);
         const float *deq = reinterpret_cast<const float *>(smem_raw + dd.tab_off);
         int32_t base = -(int32_t)cx.skip;
@@ -370,10 +437,15 @@ __global__ void __launch_bounds__(NWG * 128, tc_min_blocks<NWG>()) k_decode_tc(c
           uint32_t tsum = 0;
 #pragma unroll
           for (int u = 0; u < WPT; ++u) {
-            const uint32_t i = c0 + lane * WPT + u;
-            const bool in = i < cx.nw;
-            sl[u] = in ? (uint32_t)__ldg(p.symlen + cx.fw + i) : 0u;
-            wd[u] = in ? __ldg(p.words + cx.fw + i) : 0ull;
+            if (c0 == 0) {
+              wd[u] = wd0[u];
+              sl[u] = sl0[u];
+            } else {
+              const uint32_t i = c0 + lane * WPT + u;
+              const bool in = i < cx.nw;
+              sl[u] = in ? (uint32_t)__ldg(p.symlen + cx.fw + i) : 0u;
+              wd[u] = in ? __ldg(p.words + cx.fw + i) : 0ull;
+            }
             tsum += sl[u];
           }
           uint32_t x = tsum;
@@ -389,26 +461,24 @@ __global__ void __launch_bounds__(NWG * 128, tc_min_blocks<NWG>()) k_decode_tc(c
           base += (int32_t)total;
           if (base >= tsyms) break;
         }
-        if (err) {
-          flag_bad(p.status, err, sg.caller_index);
-          err = 0;
-        }
+        if (err) flag_bad(p.status, err, sg.caller_index);
         __syncwarp();
         if (want_lev) {
           uint8_t *dst = p.levels + sg.level_offset + win0 * kE;
           for (int32_t i = lane; i < tsyms; i += 32) dst[i] = lev[i];
         }
-        ep.out = p.out + sg.out_offset;
-        ep.s0 = win0 * kN;
-        ep.S = sg.n_samples;
-        ep.nwin = nwin;
-        ep.aligned = sg.out_aligned;
+        e.out = p.out + sg.out_offset;
+        e.s0 = win0 * kN;
+        e.S = sg.n_samples;
+        e.nwin = nwin;
+        e.aligned = sg.out_aligned;
       }
     }
-    // ---- repack: lane i moves window i of this warp's tile into the A operand
+    // repack: lane i moves window i of this warp's tile into the A operand(s)
     // (rows of windows that are not in the tile keep stale values; their D rows
     // are never stored)
-    if (lane < ep.nwin) {
+    unsigned char *const a = a_base + buf * tp.a_buf;
+    if (lane < e.nwin) {
       const uint32_t r = wq * 32u + lane;
       const float4 *src = reinterpret_cast<const float4 *>(coef + lane * kE);
       float4 c[4];
@@ -432,9 +502,9 @@ __global__ void __launch_bounds__(NWG * 128, tc_min_blocks<NWG>()) k_decode_tc(c
         }
 #pragma unroll
         for (int j = 0; j < 2; ++j) {
-          *reinterpret_cast<uint4 *>(a_base + off_bf16_chunk(r, j)) =
+          *reinterpret_cast<uint4 *>(a + off_bf16_chunk(r, j)) =
               make_uint4(h[4 * j], h[4 * j + 1], h[4 * j + 2], h[4 * j + 3]);
-          *reinterpret_cast<uint4 *>(a_base + 4096 + off_bf16_chunk(r, j)) =
+          *reinterpret_cast<uint4 *>(a + 4096 + off_bf16_chunk(r, j)) =
               make_uint4(l[4 * j], l[4 * j + 1], l[4 * j + 2], l[4 * j + 3]);
         }
       } else {
@@ -442,73 +512,98 @@ __global__ void __launch_bounds__(NWG * 128, tc_min_blocks<NWG>()) k_decode_tc(c
         for (int j = 0; j < 4; ++j) {
           const float4 big = make_float4(tf32_round(c[j].x), tf32_round(c[j].y), tf32_round(c[j].z),
                                          tf32_round(c[j].w));
-          *reinterpret_cast<float4 *>(a_base + off_tf32_chunk(r, j)) = big;
+          *reinterpret_cast<float4 *>(a + off_tf32_chunk(r, j)) = big;
           if (MODE == FPTC_IDCT_TF32X3) {
             const float4 sm = make_float4(tf32_round(c[j].x - big.x), tf32_round(c[j].y - big.y),
                                           tf32_round(c[j].z - big.z), tf32_round(c[j].w - big.w));
-            *reinterpret_cast<float4 *>(a_base + 8192 + off_tf32_chunk(r, j)) = sm;
+            *reinterpret_cast<float4 *>(a + 8192 + off_tf32_chunk(r, j)) = sm;
           }
         }
       }
     }
     fence_proxy_async_smem();
-    tc_fence_before();
-    named_barrier(1 + wg, 128);
-    tc_fence_after();
-    // ---- one thread issues the products for the warpgroup's 128 rows
+    if (buf)
+      ep1 = e;
+    else
+      ep0 = e;
+  };
+
+  // one thread issues the products of A buffer `buf` into D buffer `buf`
+  auto issue = [&](uint32_t buf) {
     if (wq == 0 && lane == 0) {
-      const uint32_t a = smem_u32(a_base), b = smem_u32(b_base);
+      tc_fence_after();
+      const uint32_t a = smem_u32(a_base + buf * tp.a_buf), b = smem_u32(b_base);
+      const uint32_t d = d_tmem + buf * 32u;
       if (MODE == FPTC_IDCT_BF16X3) {
         constexpr uint32_t id = instr_desc(kFmtBF16, kRows, kN);
-        mma_f16(d_tmem, smem_desc(a, 128, 256), smem_desc(b, 128, 256), id, 0);                // hi * hi
-        mma_f16(d_tmem, smem_desc(a + 4096, 128, 256), smem_desc(b, 128, 256), id, 1);         // lo * hi
-        mma_f16(d_tmem, smem_desc(a, 128, 256), smem_desc(b + 1024, 128, 256), id, 1);         // hi * lo
+        mma_f16(d, smem_desc(a, 128, 256), smem_desc(b, 128, 256), id, 0);          // hi * hi
+        mma_f16(d, smem_desc(a + 4096, 128, 256), smem_desc(b, 128, 256), id, 1);   // lo * hi
+        mma_f16(d, smem_desc(a, 128, 256), smem_desc(b + 1024, 128, 256), id, 1);   // hi * lo
       } else {
         constexpr uint32_t id = instr_desc(kFmtTF32, kRows, kN);
 #pragma unroll
         for (uint32_t h = 0; h < 2; ++h) {  // bins 0..7, 8..15
-          mma_tf32(d_tmem, smem_desc(a + 256 * h, 128, 512), smem_desc(b + 256 * h, 128, 512), id, h);
+          mma_tf32(d, smem_desc(a + 256 * h, 128, 512), smem_desc(b + 256 * h, 128, 512), id, h);
           if (MODE == FPTC_IDCT_TF32X3) {
-            mma_tf32(d_tmem, smem_desc(a + 256 * h, 128, 512), smem_desc(b + 2048 + 256 * h, 128, 512), id, 1);
-            mma_tf32(d_tmem, smem_desc(a + 8192 + 256 * h, 128, 512), smem_desc(b + 256 * h, 128, 512), id, 1);
+            mma_tf32(d, smem_desc(a + 256 * h, 128, 512), smem_desc(b + 2048 + 256 * h, 128, 512), id, 1);
+            mma_tf32(d, smem_desc(a + 8192 + 256 * h, 128, 512), smem_desc(b + 256 * h, 128, 512), id, 1);
           }
         }
       }
-      mma_commit(smem_u32(mbar + wg));
+      mma_commit(smem_u32(mbar + 2 * wg + buf));
     }
-    // ---- wait for the products (bounded), read this warp's rows, store
-    {
-      uint32_t it = 0;
-      while (!mbar_try_wait(smem_u32(mbar + wg), phase)) {
-        if (++it >= kWaitLimit) {
-          timeout = true;
-          break;
+  };
+
+  if (gbase_of(0) < t1) {
+    produce(0, 0);
+    tc_fence_before();
+    wg_barrier_any(wg, false);
+    issue(0);
+    for (uint64_t k = 0;; ++k) {
+      const uint32_t buf = (uint32_t)(k & 1);
+      const bool has_next = gbase_of(k + 1) < t1;  // uniform over the warpgroup
+      if (has_next) produce(k + 1, buf ^ 1u);
+      // wait for tile k's products (bounded)
+      {
+        uint32_t it = 0;
+        while (!mbar_try_wait(smem_u32(mbar + 2 * wg + buf), phase[buf])) {
+          if (++it >= kWaitLimit) {
+            timeout = true;
+            break;
+          }
+        }
+        phase[buf] ^= 1u;
+      }
+      if (!timeout) {
+        tc_fence_after();
+        uint32_t v[32];
+        tmem_ld32(my_tmem + buf * 32u, v);
+        const EpiCtx e = buf ? ep1 : ep0;
+        if (lane < e.nwin) {
+          const uint64_t s0 = e.s0 + (uint64_t)lane * kN;
+          float *dst = e.out + s0;
+          if (s0 + kN <= e.S && e.aligned) {
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+              __stcs(reinterpret_cast<float4 *>(dst) + j,
+                     make_float4(__uint_as_float(v[4 * j]), __uint_as_float(v[4 * j + 1]),
+                                 __uint_as_float(v[4 * j + 2]), __uint_as_float(v[4 * j + 3])));
+          } else {
+#pragma unroll
+            for (int n = 0; n < kN; ++n)
+              if (s0 + n < e.S) dst[n] = __uint_as_float(v[n]);
+          }
         }
       }
-      phase ^= 1u;
-    }
-    if (barrier_any(1 + wg, 128, timeout)) {  // same decision in every warp of the warpgroup
-      if (threadIdx.x % 128 == 0) atomicOr(&p.status->flags, kFlagTimeout);
-      break;
-    }
-    tc_fence_after();
-    uint32_t v[32];
-    tmem_ld32(my_tmem, v);
-    tc_fence_before();
-    if (lane < ep.nwin) {
-      const uint64_t s0 = ep.s0 + (uint64_t)lane * kN;
-      float *dst = ep.out + s0;
-      if (s0 + kN <= ep.S && ep.aligned) {
-#pragma unroll
-        for (int j = 0; j < 8; ++j)
-          __stcs(reinterpret_cast<float4 *>(dst) + j,
-                 make_float4(__uint_as_float(v[4 * j]), __uint_as_float(v[4 * j + 1]), __uint_as_float(v[4 * j + 2]),
-                             __uint_as_float(v[4 * j + 3])));
-      } else {
-#pragma unroll
-        for (int n = 0; n < kN; ++n)
-          if (s0 + n < ep.S) dst[n] = __uint_as_float(v[n]);
+      // every warp of the warpgroup: tile k+1 repacked, tile k read; one
+      // decision about a timeout for all of them
+      tc_fence_before();
+      if (wg_barrier_any(wg, timeout)) {
+        if (threadIdx.x % 128 == 0) atomicOr(&p.status->flags, kFlagTimeout);
+        break;
       }
+      if (!has_next) break;
+      issue(buf ^ 1u);
     }
   }
   // ---- release tensor memory (every warp has finished its tcgen05.ld)
@@ -544,11 +639,13 @@ void *tcpick(uint32_t mode, uint32_t threads) {
 uint32_t tc_tile_windows() { return kT; }
 
 // Shared-memory layout of the tensor-core kernel; returns total bytes.
-size_t tc_smem_layout(uint32_t threads, const uint32_t *lmax, uint32_t n_domains, TcParams *tp) {
+size_t tc_smem_layout(uint32_t mode, uint32_t threads, const uint32_t *lmax, uint32_t n_domains, TcParams *tp) {
   const uint32_t nwg = threads / 128;
   size_t o = 0;
   tp->a_off = 0;
-  tp->a_bytes = 16384;                 // up to two 128 x 64-byte operands (TF32X3) per warpgroup
+  // one A buffer: 128 x 64 B (TF32), twice that (TF32X3: big, small), or 2 x 128 x 32 B (BF16X3: hi, lo)
+  tp->a_buf = mode == FPTC_IDCT_TF32X3 ? 16384u : 8192u;
+  tp->a_bytes = 2 * tp->a_buf;         // double buffered
   o += (size_t)nwg * tp->a_bytes;
   tp->b_off = (uint32_t)o;
   o += 4096;                           // up to two 32 x 64-byte operands
@@ -557,7 +654,7 @@ size_t tc_smem_layout(uint32_t threads, const uint32_t *lmax, uint32_t n_domains
   o += (size_t)(threads / 32) * tp->coef_bytes;
   o = align16(o);
   tp->misc_off = (uint32_t)o;
-  o += 8 * nwg + 16;
+  o += 16 * nwg + 16;
   o = align16(o);
   tp->dom_off = (uint32_t)o;
   o += align16(sizeof(DomTc) * (n_domains ? n_domains : 1));
@@ -570,7 +667,16 @@ size_t tc_smem_layout(uint32_t threads, const uint32_t *lmax, uint32_t n_domains
 cudaError_t tc_smem_config(uint32_t mode, uint32_t threads, size_t smem) {
   void *k = tcpick(mode, threads);
   if (!k) return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                       (int)cudaSharedmemCarveoutMaxShared);
+  if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+cudaError_t tc_attributes(uint32_t mode, uint32_t threads, cudaFuncAttributes *attr) {
+  void *k = tcpick(mode, threads);
+  if (!k) return cudaErrorInvalidValue;
+  return cudaFuncGetAttributes(attr, k);
 }
 
 cudaError_t tc_occupancy(uint32_t mode, uint32_t threads, size_t smem, int *ctas_per_sm) {

@@ -416,6 +416,9 @@ size_t warp_smem_layout(uint32_t threads, const uint32_t *lmax, uint32_t n_domai
 cudaError_t warp_smem_config(uint32_t threads, size_t smem) {
   void *k = wpick(threads);
   if (!k) return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                       (int)cudaSharedmemCarveoutMaxShared);
+  if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 

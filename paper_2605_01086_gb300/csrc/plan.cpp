@@ -5,6 +5,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <numeric>
@@ -139,7 +140,7 @@ void layout_tiles(fptc_plan *p, uint32_t tile_samples) {
 }
 
 fptc_status configure_launch(fptc_plan *p) {
-  const uint32_t threads = p->opts.threads ? p->opts.threads : 256u;
+  const uint32_t threads = p->opts.threads ? p->opts.threads : (p->kind == FPTC_KERNEL_TENSOR ? 512u : 256u);
   if (threads != 128 && threads != 256 && threads != 512) {
     set_error("threads must be 128, 256 or 512 (got %u)", threads);
     return FPTC_ERR_INVALID_ARGUMENT;
@@ -155,12 +156,18 @@ fptc_status configure_launch(fptc_plan *p) {
   } else if (p->kind == FPTC_KERNEL_TENSOR) {
     std::vector<uint32_t> lm;
     for (const auto &d : p->domains) lm.push_back(d.lmax);
-    p->smem = tc_smem_layout(threads, lm.data(), (uint32_t)lm.size(), &p->tp);
+    p->smem = tc_smem_layout(p->opts.idct, threads, lm.data(), (uint32_t)lm.size(), &p->tp);
     e = tc_smem_config(p->opts.idct, threads, p->smem);
     if (e != cudaSuccess) return cuda_fail(e, "decode shared-memory size");
     e = tc_occupancy(p->opts.idct, threads, p->smem, &occ);
-    // tensor memory: 32 columns per warpgroup (rounded up to a power of two), 512 per SM
-    const uint32_t nwg = threads / 128, cols = nwg <= 1 ? 32u : (nwg == 2 ? 64u : 128u);
+    // tensor memory: 2 x 32 columns per warpgroup (a power of two per CTA), 512 per SM
+    const uint32_t nwg = threads / 128, cols = nwg <= 1 ? 64u : (nwg == 2 ? 128u : 256u);
+    if (std::getenv("FPTC_DEBUG")) {
+      cudaFuncAttributes fa{};
+      tc_attributes(p->opts.idct, threads, &fa);
+      std::fprintf(stderr, "fptc: tensor kernel threads %u regs %d static smem %zu max dyn smem %d dyn %zu occupancy %d\n",
+                   threads, fa.numRegs, fa.sharedSizeBytes, fa.maxDynamicSharedSizeBytes, p->smem, occ);
+    }
     if (e == cudaSuccess) occ = std::min<int>(occ, (int)(512u / cols));
   } else if (p->kind == FPTC_KERNEL_WARP_TILE) {
     std::vector<uint32_t> lm;
