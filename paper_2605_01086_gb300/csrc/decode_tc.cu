@@ -670,7 +670,7 @@ cudaError_t tc_smem_config(uint32_t mode, uint32_t threads, size_t smem) {
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout,
                                        (int)cudaSharedmemCarveoutMaxShared);
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  return set_dynamic_smem_limit(k, smem);
 }
 
 cudaError_t tc_attributes(uint32_t mode, uint32_t threads, cudaFuncAttributes *attr) {

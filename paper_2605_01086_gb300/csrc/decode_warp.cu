@@ -419,7 +419,7 @@ cudaError_t warp_smem_config(uint32_t threads, size_t smem) {
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout,
                                        (int)cudaSharedmemCarveoutMaxShared);
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  return set_dynamic_smem_limit(k, smem);
 }
 
 cudaError_t warp_occupancy(uint32_t threads, size_t smem, int *ctas_per_sm) {

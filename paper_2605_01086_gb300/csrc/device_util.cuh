@@ -117,4 +117,16 @@ __device__ __forceinline__ void load_deq(float *s_deq, const DomainDev &dm, cons
 
 __host__ __device__ constexpr size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 
+// The dynamic shared-memory limit is a per-kernel attribute shared by every plan
+// in the process: raise it to the device's opt-in maximum (never lower it to one
+// plan's need, which would break the launches of a plan that needs more).
+inline cudaError_t set_dynamic_smem_limit(const void *kernel, size_t need) {
+  int dev = 0, optin = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e != cudaSuccess) return e;
+  if (need > (size_t)optin) return cudaErrorInvalidValue;
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+}
+
 }  // namespace fptc
