@@ -232,6 +232,30 @@ fptc_status fptc_plan_device_status(fptc_plan *plan, uint32_t *flags, uint64_t *
 fptc_status fptc_plan_autotune(fptc_plan *plan, const uint64_t *d_words, const uint8_t *d_symlen, float *d_out,
                                uint32_t trials, fptc_stream stream, fptc_plan_options *best, float *best_ms);
 
+/* Allocation-free decode of ONE stream, for callers that cannot allocate device
+ * memory when they decode (inside a framework's memory pool or an allocator
+ * callback, where a cudaMalloc would re-enter the allocator; serving paths that
+ * forbid allocation after start-up; processes whose device memory another
+ * runtime has reserved).  The paper has no counterpart: it is an interface
+ * convenience, not part of the method.
+ * Same result as a plan with one segment (word_offset 0, out_offset 0) and the
+ * generic kernel: index kernels + decode kernel of Sec. 4.2, samples written to
+ * d_out[0 .. n_samples).  All working memory (domain tables, records, index
+ * scratch, status word) is one file-scope device array of about 1.3 MB that
+ * every device which loads the library keeps until exit; nothing is allocated
+ * and no library routine that allocates is called.
+ * Limits: n_samples <= 67,108,864 and domain->lmax <= 12, else
+ * FPTC_ERR_UNSUPPORTED with a message.  Device-side stream errors are not
+ * reported by this call (decode with a plan for that).
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) on the current device: make that first call before
+ * any stream capture.  Every call shares the array, so calls whose work
+ * overlaps on the GPU (different streams, or other host threads) race; serialize
+ * them.  Asynchronous on `stream` (host-to-device copies of the small tables
+ * from host memory are staged before the call returns). */
+fptc_status fptc_decode_stream_noalloc(const fptc_domain *domain, const uint64_t *d_words, const uint8_t *d_symlen,
+                                       uint64_t n_words, uint64_t n_samples, float *d_out, fptc_stream stream);
+
 /* Kernel launches of one fptc_decode_batch call with the plan's current settings. */
 uint32_t fptc_plan_launches_per_decode(const fptc_plan *plan);
 

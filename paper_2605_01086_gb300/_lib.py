@@ -58,6 +58,7 @@ SIGNATURES = {
     "fptc_decode_stages": (_i32, [_p, _p, _p, _p, _p, _p, _u32, _p]),
     "fptc_decode_backward": (_i32, [_p, _p, _p, _p, _p, _p, _p, _p, _p]),
     "fptc_decode_host": (_i32, [_p, _p, _p, _p, _p, _p, _p, _p]),
+    "fptc_decode_stream_noalloc": (_i32, [_p, _p, _p, _u64, _u64, _p, _p]),
     "fptc_plan_device_status": (_i32, [_p, ctypes.POINTER(_u32), ctypes.POINTER(_u64)]),
     "fptc_plan_autotune": (_i32, [_p, _p, _p, _p, _u32, _p, _p, ctypes.POINTER(_f)]),
     "fptc_plan_launches_per_decode": (_u32, [_p]),

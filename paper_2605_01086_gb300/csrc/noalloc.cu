@@ -1,0 +1,264 @@
+// fptc_decode_stream_noalloc: decode one compressed stream without allocating.
+//
+// Some callers cannot allocate device memory at the time they decode: code that
+// runs inside a framework's memory pool or an allocator callback (where a
+// cudaMalloc would re-enter the allocator or break its accounting), real-time
+// or embedded-serving paths that forbid any allocation after start-up, and
+// processes whose device memory is fully reserved by another runtime.  For them
+// this entry point runs the same SymLen index kernels and the same generic
+// decode kernel as a plan, but every piece of working memory (the domain
+// tables, the segment/chunk/tile records, the index scratch and the status
+// word) lives in one file-scope device array of fixed size.  The caller still
+// passes the input words/symlen and the output buffer.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+
+#include "fptc.h"
+#include "fptc_codec.h"
+#include "fptc_internal.h"
+#include "host_util.h"
+
+namespace fptc {
+namespace {
+
+// Limits of the allocation-free path (see fptc.h).
+constexpr uint64_t kNaMaxSamples = 1ull << 26;                   // 67,108,864 samples per call
+constexpr uint32_t kNaTileSamples = 4096;                        // generic kernel tile size
+constexpr uint64_t kNaMaxWords = kNaMaxSamples;                  // words <= symbols <= samples (E <= N)
+constexpr uint64_t kNaMaxChunks = (kNaMaxWords + kChunkWords - 1) / kChunkWords;
+constexpr uint32_t kNaMaxLmax = 12;                              // decode table of 4096 entries
+
+// Byte layout of the scratch array (each piece 256-byte aligned).
+constexpr size_t a256(size_t x) { return (x + 255) & ~size_t(255); }
+constexpr size_t kOffStatus = 0;
+constexpr size_t kOffSegBad = a256(kOffStatus + sizeof(DevStatus));
+constexpr size_t kOffSeg = a256(kOffSegBad + sizeof(uint32_t));
+constexpr size_t kOffDom = a256(kOffSeg + sizeof(SegDev));
+constexpr size_t kOffLut = a256(kOffDom + sizeof(DomainDev));
+constexpr size_t kOffBasis = a256(kOffLut + (size_t(2) << kNaMaxLmax));
+constexpr size_t kOffChunkSum = a256(kOffBasis + 128 * 128 * sizeof(float));
+constexpr size_t kOffChunkOff = a256(kOffChunkSum + kNaMaxChunks * sizeof(uint32_t));
+constexpr size_t kOffChunks = a256(kOffChunkOff + kNaMaxChunks * sizeof(uint64_t));
+constexpr size_t kOffTiles = a256(kOffChunks + kNaMaxChunks * sizeof(ChunkDev));
+// a tile holds floor(4096 / N) windows, i.e. >= 4096 - N + 1 >= 3969 samples (N <= 128)
+constexpr uint64_t kNaTileCap = kNaMaxSamples / 3968 + 2;
+constexpr size_t kScratchBytes = a256(kOffTiles + kNaTileCap * sizeof(TileRec));
+
+static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
+
+// Device address of g_scratch, per device (host code may not use the symbol itself).
+constexpr int kMaxDevices = 64;
+std::mutex g_setup_mu;
+void *g_scratch_ptr[kMaxDevices] = {nullptr};
+
+fptc_status scratch_for_current_device(int dev, unsigned char **out) {
+  if (dev < 0 || dev >= kMaxDevices) {
+    set_error("device %d out of range for the allocation-free path", dev);
+    return FPTC_ERR_UNSUPPORTED;
+  }
+  std::lock_guard<std::mutex> lk(g_setup_mu);
+  if (!g_scratch_ptr[dev]) {
+    void *ptr = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&ptr, g_scratch);
+    if (e != cudaSuccess || !ptr) {
+      set_error("cudaGetSymbolAddress of the decode scratch failed: %s", cudaGetErrorString(e));
+      return FPTC_ERR_CUDA;
+    }
+    g_scratch_ptr[dev] = ptr;
+  }
+  *out = static_cast<unsigned char *>(g_scratch_ptr[dev]);
+  return FPTC_OK;
+}
+
+}  // namespace
+}  // namespace fptc
+
+using namespace fptc;
+
+extern "C" fptc_status fptc_decode_stream_noalloc(const fptc_domain *domain, const uint64_t *d_words,
+                                                  const uint8_t *d_symlen, uint64_t n_words, uint64_t n_samples,
+                                                  float *d_out, fptc_stream stream) {
+  clear_error();
+  fptc_status st = fptc_validate_domain(domain);
+  if (st != FPTC_OK) return st;
+  const fptc_domain &dm = *domain;
+  if (dm.lmax > kNaMaxLmax) {
+    set_error("the allocation-free decode supports lmax <= %u (got %u)", kNaMaxLmax, dm.lmax);
+    return FPTC_ERR_UNSUPPORTED;
+  }
+  if (n_samples > kNaMaxSamples) {
+    set_error("the allocation-free decode takes at most %llu samples per call (got %llu)",
+              (unsigned long long)kNaMaxSamples, (unsigned long long)n_samples);
+    return FPTC_ERR_UNSUPPORTED;
+  }
+  const uint64_t W = (n_samples + dm.N - 1) / dm.N;
+  const uint64_t L = W * dm.E;
+  if (n_words < (L + 63) / 64 || n_words > L) {
+    set_error("%llu words cannot hold %llu symbols", (unsigned long long)n_words, (unsigned long long)L);
+    return FPTC_ERR_INVALID_ARGUMENT;
+  }
+  if (n_samples == 0) return FPTC_OK;
+  if (!d_words || !d_symlen || !d_out || (reinterpret_cast<uintptr_t>(d_words) & 7u) ||
+      (reinterpret_cast<uintptr_t>(d_out) & 3u)) {
+    set_error("d_words (8-byte aligned), d_symlen and d_out (4-byte aligned) are required");
+    return FPTC_ERR_INVALID_ARGUMENT;
+  }
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) {
+    set_error("cudaGetDevice: %s", cudaGetErrorString(e));
+    return FPTC_ERR_CUDA;
+  }
+  unsigned char *scr = nullptr;
+  if ((st = scratch_for_current_device(dev, &scr)) != FPTC_OK) return st;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+
+  // ---- host-side records (no heap allocation: fixed-size locals)
+  DomainDev dd;
+  std::memset(&dd, 0, sizeof(dd));
+  dd.N = dm.N;
+  dd.E = dm.E;
+  dd.B1 = dm.B1;
+  dd.B2 = dm.B2;
+  dd.lmax = dm.lmax;
+  dd.tile_windows = std::max<uint32_t>(1u, kNaTileSamples / dm.N);
+  dd.lut_offset = 0;
+  dd.basis_offset = 0;
+  for (int z = 0; z < 3; ++z) dd.scale[z] = static_cast<float>(dm.scale[z]);
+  {
+    uint64_t kraft = 0;
+    for (int sy = 0; sy < 256; ++sy)
+      if (dm.code_len[sy]) kraft += uint64_t(1) << (dm.lmax - dm.code_len[sy]);
+    dd.complete = kraft == (uint64_t(1) << dm.lmax);
+  }
+  {
+    const double mu = dm.mu, a = dm.alpha1, span = 1.0 - dm.alpha1;
+    for (int Lv = 0; Lv < 256; ++Lv) {
+      double u0 = 0.0, u1 = 0.0;
+      if (Lv > 128) {
+        u0 = (std::pow(1.0 + mu, (Lv - 128) / 127.0) - 1.0) / mu;
+        u1 = a + (Lv - 129) / 126.0 * span;
+      } else if (Lv < 128) {
+        u0 = -(std::pow(1.0 + mu, (128 - Lv) / 128.0) - 1.0) / mu;
+        u1 = -(a + (127 - Lv) / 127.0 * span);
+      }
+      dd.unit[0][Lv] = static_cast<float>(u0);
+      dd.unit[1][Lv] = static_cast<float>(u1);
+    }
+  }
+  uint16_t lut[1u << kNaMaxLmax];
+  if ((st = fptc_build_decode_table(&dm, lut)) != FPTC_OK) return st;
+  SegDev sg;
+  std::memset(&sg, 0, sizeof(sg));
+  sg.word_offset = 0;
+  sg.n_words = n_words;
+  sg.n_samples = n_samples;
+  sg.out_offset = 0;
+  sg.level_offset = 0;
+  sg.n_windows = W;
+  sg.tile_base = 0;
+  sg.n_tiles = (W + dd.tile_windows - 1) / dd.tile_windows;
+  sg.chunk_base = 0;
+  sg.n_chunks = (uint32_t)((n_words + kChunkWords - 1) / kChunkWords);
+  sg.domain = 0;
+  sg.caller_index = 0;
+  sg.out_aligned = (reinterpret_cast<uintptr_t>(d_out) & 15u) == 0;
+  if (sg.n_tiles > kNaTileCap) {
+    set_error("too many tiles for the allocation-free decode");
+    return FPTC_ERR_UNSUPPORTED;
+  }
+  const DevStatus st0{0u, 0u, ~0ull};
+  const uint32_t zero = 0;
+
+  // ---- upload (copies only; the status word and segment flag start cleared)
+  e = cudaMemcpyAsync(scr + kOffStatus, &st0, sizeof(st0), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(scr + kOffSegBad, &zero, sizeof(zero), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(scr + kOffSeg, &sg, sizeof(sg), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(scr + kOffDom, &dd, sizeof(dd), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(scr + kOffLut, lut, sizeof(uint16_t) << dm.lmax, cudaMemcpyHostToDevice, s);
+  // Copies from pageable host memory are staged before cudaMemcpyAsync returns,
+  // so the local buffers below may be reused or go out of scope right away.
+  if (e == cudaSuccess) {
+    float basis[128 * 128];
+    for (uint32_t k = 0; k < dm.E; ++k)
+      for (uint32_t n = 0; n < dm.N; ++n)
+        basis[k * dm.N + n] = k == 0 ? 0.5f : static_cast<float>(std::cos(M_PI * (2.0 * n + 1.0) * k / (2.0 * dm.N)));
+    e = cudaMemcpyAsync(scr + kOffBasis, basis, (size_t)dm.E * dm.N * sizeof(float), cudaMemcpyHostToDevice, s);
+  }
+  {
+    ChunkDev part[256];
+    for (uint64_t c0 = 0; c0 < sg.n_chunks && e == cudaSuccess; c0 += 256) {
+      const uint64_t m = std::min<uint64_t>(256, sg.n_chunks - c0);
+      for (uint64_t i = 0; i < m; ++i) {
+        const uint64_t c = c0 + i;
+        part[i].word_begin = c * kChunkWords;
+        part[i].n_words = (uint32_t)std::min<uint64_t>(kChunkWords, n_words - c * kChunkWords);
+        part[i].seg = 0;
+      }
+      e = cudaMemcpyAsync(scr + kOffChunks + c0 * sizeof(ChunkDev), part, m * sizeof(ChunkDev),
+                          cudaMemcpyHostToDevice, s);
+    }
+  }
+  if (e != cudaSuccess) {
+    set_error("allocation-free decode upload: %s", cudaGetErrorString(e));
+    return FPTC_ERR_CUDA;
+  }
+
+  // ---- index + generic decode kernel on the scratch
+  IndexParams ip{};
+  ip.symlen = d_symlen;
+  ip.segs = reinterpret_cast<const SegDev *>(scr + kOffSeg);
+  ip.domains = reinterpret_cast<const DomainDev *>(scr + kOffDom);
+  ip.chunks = reinterpret_cast<const ChunkDev *>(scr + kOffChunks);
+  ip.chunk_sum = reinterpret_cast<uint32_t *>(scr + kOffChunkSum);
+  ip.chunk_off = reinterpret_cast<uint64_t *>(scr + kOffChunkOff);
+  ip.seg_bad = reinterpret_cast<uint32_t *>(scr + kOffSegBad);
+  ip.tiles = reinterpret_cast<TileRec *>(scr + kOffTiles);
+  ip.status = reinterpret_cast<DevStatus *>(scr + kOffStatus);
+  ip.chunk_begin = 0;
+  ip.chunk_end = sg.n_chunks;
+  ip.seg_begin = 0;
+  ip.seg_end = 1;
+  e = launch_index(ip, s);
+  if (e != cudaSuccess) {
+    set_error("allocation-free index launch: %s", cudaGetErrorString(e));
+    return FPTC_ERR_CUDA;
+  }
+  DecodeParams dp{};
+  dp.words = d_words;
+  dp.symlen = d_symlen;
+  dp.out = d_out;
+  dp.levels = nullptr;
+  dp.scale = nullptr;
+  dp.segs = ip.segs;
+  dp.domains = ip.domains;
+  dp.luts = reinterpret_cast<const uint16_t *>(scr + kOffLut);
+  dp.basis = reinterpret_cast<const float *>(scr + kOffBasis);
+  dp.tiles = ip.tiles;
+  dp.seg_bad = ip.seg_bad;
+  dp.status = ip.status;
+  dp.tile_begin = 0;
+  dp.tile_end = sg.n_tiles;
+  dp.seg_begin = 0;
+  dp.seg_end = 1;
+  dp.lut_cap = 1u << dm.lmax;
+  dp.coef_cap = dd.tile_windows * dm.E;
+  const uint32_t threads = 256;
+  const size_t smem = decode_smem_bytes(FPTC_KERNEL_GENERIC, threads, dp.lut_cap, dp.coef_cap);
+  if ((e = decode_smem_config(FPTC_KERNEL_GENERIC, threads, smem)) == cudaSuccess) {
+    int occ = 1, sms = 1;
+    decode_occupancy(FPTC_KERNEL_GENERIC, threads, smem, &occ);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const uint32_t grid = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>((uint64_t)sms * std::max(occ, 1),
+                                                                              sg.n_tiles));
+    e = launch_decode(dp, FPTC_KERNEL_GENERIC, threads, grid, smem, s);
+  }
+  if (e != cudaSuccess) {
+    set_error("allocation-free decode launch: %s", cudaGetErrorString(e));
+    return FPTC_ERR_CUDA;
+  }
+  return FPTC_OK;
+}
