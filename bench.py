@@ -154,6 +154,28 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
+def _kernel_source_hash(kind: int):
+    import hashlib
+    files = {1: "decode.cu", 2: "decode_fixed.cu", 3: "decode_warp.cu", 4: "decode_tc.cu"}
+    f = os.path.join(ROOT, "paper_2605_01086_gb300", "csrc", files.get(kind, "decode.cu"))
+    with open(f, "rb") as fh:
+        return hashlib.sha1(fh.read()).hexdigest()[:12]
+
+
+def measured_traffic(kind: int, n_samples: int):
+    """DRAM bytes per launch from the committed ncu summary (profiles/dram_traffic.txt:
+    'kind sha1 bytes_per_sample'), scaled to this launch; None if the kernel changed since."""
+    p = os.path.join(ROOT, "profiles", "dram_traffic.txt")
+    if not os.path.exists(p):
+        return None
+    h = _kernel_source_hash(kind)
+    for line in open(p):
+        f = line.split("#", 1)[0].split()
+        if len(f) == 3 and int(f[0]) == kind and f[1] == h:
+            return float(f[2]) * n_samples
+    return None
+
+
 def oracle_sample_time(batch, idx, n_threads):
     """Times the FP64 CPU oracle decoder on the streams idx (OpenMP over streams)."""
     import oracle
@@ -247,7 +269,9 @@ def run(args):
     in_bytes = 9 * int(batch.segments["n_words"].sum())
 
     t0 = time.perf_counter()
-    plan = Plan(doms, batch.segments, device=local)
+    plan = Plan(doms, batch.segments, device=local, kernel=args.kernel or "auto", threads=args.threads)
+    if args.kernel:
+        args.no_autotune = True
     t_plan = time.perf_counter() - t0
     w, s = plan.to_device(batch.words, batch.symlen)
     out = plan.empty_out().zero_()
@@ -320,9 +344,13 @@ def run(args):
 
     peak, peak_kind = measured_peaks()
     dec_avg = statistics.mean(dec_ms)
+    kernel_names = {1: "k_decode (generic)", 2: "k_decode_fixed (block tile)", 3: "k_decode_warp (warp tile)",
+                    4: "k_decode_tc (tensor core)"}
+    kname = kernel_names.get(plan.info["kernel"], "?")
+    traffic = args.traffic if args.traffic is not None else measured_traffic(plan.info["kernel"], n_samples)
     achieved = (out_bytes + in_bytes) / (dec_avg / 1e3) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "peak_kind": peak_kind, "traffic": args.traffic, "kernel": "k_decode (fused decode)",
+                "peak_kind": peak_kind, "traffic": traffic, "kernel": kname,
                 "algorithmic_bytes_per_launch": out_bytes + in_bytes, "launch_ms": dec_avg,
                 "index_ms": statistics.mean(idx_ms), "nominal_frac": achieved / 7900.0}
 
@@ -339,6 +367,28 @@ def run(args):
                           "max": max(trials), "n": len(trials)},
             "roofline": roofline, "gpu_launches": args.steps * plan.launches_per_decode, "clocks": clk,
             "prd_percent_sample": prd}
+
+    # tensor-core forms of the inverse transform on the same streams: throughput
+    # and relative L2 distance to the FP32 output (the FP64 comparison is in the tests)
+    if not args.no_forms and rank == 0:
+        forms = {}
+        ref = out.clone()
+        for idct in ("tf32x3", "bf16x3", "tf32"):
+            fplan = Plan(doms, batch.segments, device=local, idct=idct)
+            out3 = torch.zeros_like(out)
+            with torch.cuda.stream(stream):
+                fplan.autotune(w, s, out3, trials=2, stream=stream)
+                fplan.decode(w, s, out=out3, stream=stream)
+                fms = time_steps(lambda: fplan.decode(w, s, out=out3, stream=stream), 5, stream, torch)
+            torch.cuda.synchronize()
+            rel = float(torch.linalg.vector_norm((out3 - ref).double()) / torch.linalg.vector_norm(ref.double()))
+            forms[idct] = {"value": out_bytes / (statistics.median(fms) / 1e3) / 1e9, "unit": UNIT,
+                           "ms_per_step": statistics.median(fms), "rel_l2_vs_fp32": rel,
+                           "threads": fplan.info["threads"]}
+            fplan.close()
+            del out3
+        line["forms"] = forms
+        del ref
 
     # plain baseline: one set of launches per stream, same streams, same output
     if not args.no_plain and rank == 0:
@@ -410,6 +460,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--no-forms", action="store_true")
+    ap.add_argument("--kernel", default=None, help="fix the decode kernel (no autotuning): warp_tile, block_tile, generic")
+    ap.add_argument("--threads", type=int, default=0)
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
