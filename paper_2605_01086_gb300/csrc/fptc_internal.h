@@ -113,7 +113,7 @@ struct WarpParams {
   uint32_t n_domains;
   uint32_t warp_off;    // first byte of the per-warp buffers
   uint32_t warp_bytes;  // bytes per warp
-  uint32_t pad;
+  uint32_t basis_off;   // paired inverse-transform basis
   uint32_t lut_off[kWarpMaxDomains];  // bytes
   uint32_t tab_off[kWarpMaxDomains];  // bytes
 };

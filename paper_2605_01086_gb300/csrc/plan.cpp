@@ -140,9 +140,23 @@ void layout_tiles(fptc_plan *p, uint32_t tile_samples) {
 }
 
 fptc_status configure_launch(fptc_plan *p) {
-  const uint32_t threads = p->opts.threads ? p->opts.threads : (p->kind == FPTC_KERNEL_TENSOR ? 512u : 256u);
-  if (threads != 128 && threads != 256 && threads != 512) {
-    set_error("threads must be 128, 256 or 512 (got %u)", threads);
+  uint32_t threads = p->opts.threads ? p->opts.threads : (p->kind == FPTC_KERNEL_TENSOR ? 512u : 256u);
+  if (p->kind == FPTC_KERNEL_WARP_TILE && p->opts.threads == 0) {
+    // as many warps per SM as one CTA's shared memory allows (32 at most)
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    std::vector<uint32_t> lm;
+    for (const auto &d : p->domains) lm.push_back(d.lmax);
+    WarpParams probe{};
+    threads = 1024;
+    while (threads > 128 && warp_smem_layout(threads, lm.data(), (uint32_t)lm.size(), &probe) > (size_t)optin)
+      threads /= 2;
+  }
+  const bool t_ok = threads == 128 || threads == 256 || threads == 512 ||
+                    (threads == 1024 && p->kind == FPTC_KERNEL_WARP_TILE);
+  if (!t_ok) {
+    set_error("threads must be 128, 256 or 512 (1024 also for the warp-tile kernel; got %u)", threads);
     return FPTC_ERR_INVALID_ARGUMENT;
   }
   p->threads = threads;
@@ -191,12 +205,12 @@ fptc_status configure_launch(fptc_plan *p) {
   const uint64_t full = (uint64_t)p->sm_count * p->ctas_per_sm;
   p->grid = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(full, p->n_tiles));
   // backward
-  p->b_threads = threads;
-  p->b_smem = backward_smem_bytes(threads, p->lut_cap, p->coef_cap, p->gx_cap, p->basis_cap);
-  e = backward_smem_config(threads, p->b_smem);
+  p->b_threads = threads > 512 ? 256u : threads;
+  p->b_smem = backward_smem_bytes(p->b_threads, p->lut_cap, p->coef_cap, p->gx_cap, p->basis_cap);
+  e = backward_smem_config(p->b_threads, p->b_smem);
   if (e != cudaSuccess) return cuda_fail(e, "backward shared-memory size");
   int bocc = 0;
-  e = backward_occupancy(threads, p->b_smem, &bocc);
+  e = backward_occupancy(p->b_threads, p->b_smem, &bocc);
   if (e != cudaSuccess) return cuda_fail(e, "backward occupancy");
   if (bocc < 1) {
     set_error("backward kernel does not fit an SM (%zu bytes shared memory)", p->b_smem);
@@ -396,7 +410,20 @@ fptc_status fptc_plan_create(fptc_plan **out, int device, const fptc_domain *dom
     }
     o.kernel = FPTC_KERNEL_TENSOR;
   }
-  if (o.kernel == FPTC_KERNEL_AUTO) o.kernel = warp_ok ? FPTC_KERNEL_WARP_TILE : FPTC_KERNEL_GENERIC;
+  if (o.kernel == FPTC_KERNEL_AUTO) {
+    // the warp-tile kernel keeps every domain's tables in shared memory: it is
+    // the default when they fit beside at least four warps' buffers
+    bool fits = false;
+    if (warp_ok) {
+      std::vector<uint32_t> lm(n_domains);
+      for (uint32_t d = 0; d < n_domains; ++d) lm[d] = domains[d].lmax;
+      WarpParams probe{};
+      int optin = 0;
+      if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device) != cudaSuccess) optin = 0;
+      fits = warp_smem_layout(128, lm.data(), n_domains, &probe) <= (size_t)optin;
+    }
+    o.kernel = fits ? FPTC_KERNEL_WARP_TILE : (all_fixed ? FPTC_KERNEL_BLOCK_TILE : FPTC_KERNEL_GENERIC);
+  }
   if (o.kernel == FPTC_KERNEL_WARP_TILE) o.tile_samples = warp_tile_windows() * 32;
   if (o.kernel == FPTC_KERNEL_TENSOR) o.tile_samples = tc_tile_windows() * 32;
   if (o.tile_samples == 0) o.tile_samples = o.kernel == FPTC_KERNEL_BLOCK_TILE ? 8192 : 4096;
@@ -823,7 +850,12 @@ fptc_status fptc_plan_autotune(fptc_plan *p, const uint64_t *d_words, const uint
     uint32_t kernel, tile_samples, threads;
   };
   std::vector<Cand> cands;
-  for (uint32_t th : {128u, 256u, 512u}) {
+  for (uint32_t th : {128u, 256u, 512u, 1024u}) {
+    if (th == 1024) {
+      if (keep.idct == FPTC_IDCT_FP32 && fixed && p->domains.size() <= kWarpMaxDomains)
+        cands.push_back({FPTC_KERNEL_WARP_TILE, warp_tile_windows() * 32, th});
+      continue;
+    }
     if (keep.idct != FPTC_IDCT_FP32) {
       cands.push_back({FPTC_KERNEL_TENSOR, tc_tile_windows() * 32, th});
       continue;
