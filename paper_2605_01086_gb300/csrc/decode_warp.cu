@@ -11,12 +11,16 @@
 //     value is known at compile time.  The 64-bit word is shifted through
 //     hi:lo with a marker bit under it, so a word whose codewords need more
 //     than 64 bits shows as an empty buffer at the end (no per-codeword count).
-//  2. Dequantization and inverse DCT in steps of 16 windows.  Lane (r, q)
-//     turns bins 4q..4q+3 of windows r and r+8 into A_z * unit_z(level) (one
-//     table read each) and writes them to a padded row buffer; after a
-//     __syncwarp the four lanes of a window read its 16 coefficients and
-//     compute 4 samples and their 4 mirror samples with FFMA2 (even/odd bin
-//     pairs, B[k][N-1-n] = (-1)^k B[k][n]); 16-byte streaming stores.
+//  2. Dequantization and inverse DCT, one window per lane.  The lane reads its
+//     window's 16 entries, turns each level into A_z * unit_z(level) (one
+//     table read; the bin, hence the zone row, is fixed per register), and
+//     evaluates the inverse of Eq. 1 by the even/odd split of the DCT-III:
+//     x[n] = E[n] + O[n], x[31-n] = E[n] - O[n] with O the odd bins and E the
+//     even bins, itself split the same way twice (E[15-n] = EE[n] - EO[n],
+//     EE[7-n] = EEE[n] - EEO[n]); 229 FP32 operations per window with the
+//     cosines as compile-time constants, so neither a basis nor coefficients
+//     pass through shared memory.  32-byte streaming stores (one full sector
+//     per thread and instruction) where the output is 32-byte aligned.
 //  The tile records of tile g+1 are loaded when tile g starts, the first words
 //  of tile g+1 when tile g's decode ends (hidden by its transform), and the
 //  words of a tile's next decode pass before the current pass.
@@ -34,10 +38,96 @@ constexpr int kTS = kT * kE;               // symbols per tile
 constexpr int kGuard = 64;                 // entries before and after the tile (a word holds <= 64 codewords)
 constexpr int kStage = kTS + 2 * kGuard;   // 16-bit entries per warp
 constexpr int kZStride = 257;              // floats per zone row (zero levels of the zones in different banks)
-constexpr int kStepWin = 16;               // windows per transform step
-constexpr int kRowF = 20;                  // floats per coefficient row: 8 rows read at once hit 8 bank groups
 constexpr int kWPL = 2;                    // words per lane per decode pass
 constexpr int kPassWords = 32 * kWPL;
+// zone mask of Table 1 (B1 = 2, B2 = 16): bins 0, 1 in zone 0, the rest in zone 1
+constexpr uint32_t kZmaskTable1 = 0x55555550u;
+
+// ---- compile-time cosines of the inverse transform (N = 32, E = 16) ----------
+// cos(pi num / den) in double: Taylor series on [0, pi/2] after the reflections
+// cos(2 pi - a) = cos(a) and cos(pi - a) = -cos(a); rounded to float.
+__host__ __device__ constexpr double cos_taylor(double x) {
+  double x2 = x * x, term = 1.0, sum = 1.0;
+  for (int i = 1; i < 24; ++i) {
+    term *= -x2 / ((2.0 * i - 1.0) * (2.0 * i));
+    sum += term;
+  }
+  return sum;
+}
+__host__ __device__ constexpr float cospi_frac(int num, int den) {
+  int r = num % (2 * den);
+  if (r > den) r = 2 * den - r;
+  const double pi = 3.14159265358979323846;
+  return 2 * r <= den ? (float)cos_taylor(pi * r / den) : (float)-cos_taylor(pi * (den - r) / den);
+}
+// B[k][n] = cos(pi (2n+1) k / 64) grouped by the even/odd recursion:
+//   eee[n]    = B[8][n]                       n < 4
+//   eeo[n][j] = B[4(2j+1)][n]                 n < 4, j < 2   (bins 4, 12)
+//   eo[n][j]  = B[2(2j+1)][n]                 n < 8, j < 4   (bins 2, 6, 10, 14)
+//   o[n][j]   = B[2j+1][n]                    n < 16, j < 8  (odd bins)
+struct IdctK {
+  float eee[4];
+  float eeo[4][2];
+  float eo[8][4];
+  float o[16][8];
+};
+__host__ __device__ constexpr IdctK make_idct_k() {
+  IdctK K{};
+  for (int n = 0; n < 4; ++n) K.eee[n] = cospi_frac(2 * n + 1, 8);
+  for (int n = 0; n < 4; ++n)
+    for (int j = 0; j < 2; ++j) K.eeo[n][j] = cospi_frac((2 * n + 1) * (2 * j + 1), 16);
+  for (int n = 0; n < 8; ++n)
+    for (int j = 0; j < 4; ++j) K.eo[n][j] = cospi_frac((2 * n + 1) * (2 * j + 1), 32);
+  for (int n = 0; n < 16; ++n)
+    for (int j = 0; j < 8; ++j) K.o[n][j] = cospi_frac((2 * n + 1) * (2 * j + 1), 64);
+  return K;
+}
+
+// x[0..31] of one window from its 16 coefficients (inverse of Eq. 1, B[0][n] = 1/2);
+// emits the samples as four blocks of 8 through put(block, v[8]).
+template <class Put>
+__device__ __forceinline__ void idct32(const float (&c)[16], Put put) {
+  constexpr IdctK K = make_idct_k();
+  const float h0 = 0.5f * c[0];
+  float ee[8], eo[8];
+#pragma unroll
+  for (int n = 0; n < 4; ++n) {
+    const float eee = fmaf(c[8], K.eee[n], h0);
+    const float eeo = fmaf(c[12], K.eeo[n][1], c[4] * K.eeo[n][0]);
+    ee[n] = eee + eeo;
+    ee[7 - n] = eee - eeo;
+  }
+#pragma unroll
+  for (int n = 0; n < 8; ++n) {
+    float a = c[2] * K.eo[n][0];
+    a = fmaf(c[6], K.eo[n][1], a);
+    a = fmaf(c[10], K.eo[n][2], a);
+    eo[n] = fmaf(c[14], K.eo[n][3], a);
+  }
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    float lo[8], hi[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int n = 8 * j + i;
+      const float e = n < 8 ? ee[n] + eo[n] : ee[15 - n] - eo[15 - n];
+      float o = c[1] * K.o[n][0];
+#pragma unroll
+      for (int t = 1; t < 8; ++t) o = fmaf(c[2 * t + 1], K.o[n][t], o);
+      lo[i] = e + o;       // x[n]
+      hi[7 - i] = e - o;   // x[31 - n]
+    }
+    put(j, lo);
+    put(3 - j, hi);
+  }
+}
+
+// 32-byte streaming store (one full sector per thread)
+__device__ __forceinline__ void st_cs_v8(float *p, const float (&v)[8]) {
+  asm volatile("st.global.cs.v8.f32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(p), "f"(v[0]), "f"(v[1]),
+               "f"(v[2]), "f"(v[3]), "f"(v[4]), "f"(v[5]), "f"(v[6]), "f"(v[7])
+               : "memory");
+}
 
 struct DomW {
   uint32_t lut_off;   // bytes from the start of shared memory: 16-bit entries len | level << 8
@@ -145,26 +235,6 @@ __device__ __forceinline__ void fetch_pass0(const DecodeParams &p, const Ctx &c,
   nb = ib ? (uint32_t)__ldg(p.symlen + c.fw + i + 1) : 0u;
 }
 
-__device__ __forceinline__ void store_window(float *out, uint64_t S, uint64_t s0, uint32_t q, const float2 (&acc)[4],
-                                             uint32_t aligned) {
-  const float4 lo = make_float4(acc[0].x + acc[0].y, acc[1].x + acc[1].y, acc[2].x + acc[2].y, acc[3].x + acc[3].y);
-  const float4 hi = make_float4(acc[3].x - acc[3].y, acc[2].x - acc[2].y, acc[1].x - acc[1].y, acc[0].x - acc[0].y);
-  float *dst = out + s0;
-  if (s0 + kN <= S && aligned) {
-    __stcs(reinterpret_cast<float4 *>(dst + 4 * q), lo);
-    __stcs(reinterpret_cast<float4 *>(dst + kN - 4 - 4 * q), hi);
-  } else {
-    const float lv[4] = {lo.x, lo.y, lo.z, lo.w};
-    const float hv[4] = {hi.x, hi.y, hi.z, hi.w};
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const uint32_t n1 = 4 * q + j, n2 = kN - 4 - 4 * q + j;
-      if (s0 + n1 < S) dst[n1] = lv[j];
-      if (s0 + n2 < S) dst[n2] = hv[j];
-    }
-  }
-}
-
 template <int WARPS>
 __global__ void __launch_bounds__(WARPS * 32, 32 / WARPS) k_decode_warp(const DecodeParams p,
                                                                                  const WarpParams wp) {
@@ -210,26 +280,13 @@ __global__ void __launch_bounds__(WARPS * 32, 32 / WARPS) k_decode_warp(const De
       deq[i] = (L < 256u && z < 2u) ? (z == 0 ? a0 : a1) * dm.unit[z][L] : 0.0f;
     }
   }
-  {
-    // paired basis (B[2m][n], B[2m+1][n]), [m][n]; the same for every N = 32, E = 16 domain
-    float2 *bp = reinterpret_cast<float2 *>(smem_raw + wp.basis_off);
-    const float *b = p.basis + p.domains[0].basis_offset;
-    for (uint32_t i = threadIdx.x; i < (kE / 2) * kN; i += WARPS * 32) {
-      const uint32_t m = i / kN, n = i % kN;
-      bp[i] = make_float2(__ldg(b + (2 * m) * kN + n), __ldg(b + (2 * m + 1) * kN + n));
-    }
-  }
   __syncthreads();
 
   unsigned char *const wbase = smem_raw + wp.warp_off + warp * wp.warp_bytes;
   uint64_t *const wbuf = reinterpret_cast<uint64_t *>(wbase);                       // first-pass words
   TileRec *const rec = reinterpret_cast<TileRec *>(wbase + kPassWords * 8);          // records g, g + 1
   uint16_t *const stage = reinterpret_cast<uint16_t *>(wbase + kPassWords * 8 + 32) + kGuard;  // tile position 0
-  float *const cbuf0 = reinterpret_cast<float *>(wbase + kPassWords * 8 + 32 + kStage * 2);
-  float *const cbuf1 = cbuf0 + kStepWin * kRowF;
-  const float4 *const bas4 = reinterpret_cast<const float4 *>(smem_raw + wp.basis_off);  // [m][16]
   const bool want_lev = p.levels != nullptr;
-  const uint32_t r = lane >> 2, q = lane & 3u;
 
   // ---- this warp's tiles: an even split of the launch's tile range over all warps
   const uint64_t n_all = p.tile_end - p.tile_begin;
@@ -311,72 +368,61 @@ __global__ void __launch_bounds__(WARPS * 32, 32 / WARPS) k_decode_warp(const De
     }
     __syncwarp();
 
-    // ---- 2. dequantization + inverse transform + reassembly, 16 windows per step
+    // ---- 2. dequantization + inverse transform + reassembly, one window per lane
     if (cur.ok) {
       const float *deq = reinterpret_cast<const float *>(smem_raw + dd.deq_off);
-      const float *row0 = deq + ((dd.zmask >> (8 * q + 0)) & 3u) * kZStride;
-      const float *row1 = deq + ((dd.zmask >> (8 * q + 2)) & 3u) * kZStride;
-      const float *row2 = deq + ((dd.zmask >> (8 * q + 4)) & 3u) * kZStride;
-      const float *row3 = deq + ((dd.zmask >> (8 * q + 6)) & 3u) * kZStride;
+      const bool table1 = dd.zmask == kZmaskTable1;  // bins 0, 1 in zone 0, bins 2..15 in zone 1
       float *const out = p.out + sg.out_offset;
       const uint64_t S = sg.n_samples;
       const uint32_t aligned = sg.out_aligned;
+      const bool vec32 = (aligned & 2u) && (reinterpret_cast<uintptr_t>(p.out) & 31u) == 0;
       uint8_t *const lev = want_lev ? p.levels + sg.level_offset + win0 * kE : nullptr;
 #pragma unroll 1
-      for (uint32_t w0 = 0; w0 < nwin; w0 += kStepWin) {
-        float *const cb = (w0 & kStepWin) ? cbuf1 : cbuf0;
+      for (uint32_t w = lane; w < nwin; w += 32) {
+        const uint4 e0 = *reinterpret_cast<const uint4 *>(stage + w * kE);
+        const uint4 e1 = *reinterpret_cast<const uint4 *>(stage + w * kE + 8);
+        const uint32_t ev[8] = {e0.x, e0.y, e0.z, e0.w, e1.x, e1.y, e1.z, e1.w};
+        float c[16];
+        if (table1) {
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const uint32_t w = w0 + r + 8 * h;
-          const uint2 ev = *reinterpret_cast<const uint2 *>(stage + w * kE + 4 * q);
-          float4 c;
-          c.x = row0[(ev.x >> 8) & 0xffu];
-          c.y = row1[ev.x >> 24];
-          c.z = row2[(ev.y >> 8) & 0xffu];
-          c.w = row3[ev.y >> 24];
-          *reinterpret_cast<float4 *>(cb + (r + 8 * h) * kRowF + 4 * q) = c;
-          if (want_lev && w < nwin) {
-            const uint32_t l4 = __byte_perm(ev.x, ev.y, 0x7531);
-            uint8_t *dl = lev + w * kE + 4 * q;
-            if ((reinterpret_cast<uintptr_t>(dl) & 3u) == 0) {
-              *reinterpret_cast<uint32_t *>(dl) = l4;
-            } else {
+          for (int k = 0; k < 16; ++k) {
+            const uint32_t sym = (k & 1) ? (ev[k >> 1] >> 24) : ((ev[k >> 1] >> 8) & 0xffu);
+            c[k] = deq[(k < 2 ? 0 : kZStride) + sym];
+          }
+        } else {
 #pragma unroll
-              for (int j = 0; j < 4; ++j) dl[j] = (uint8_t)(l4 >> (8 * j));
-            }
+          for (int k = 0; k < 16; ++k) {
+            const uint32_t sym = (k & 1) ? (ev[k >> 1] >> 24) : ((ev[k >> 1] >> 8) & 0xffu);
+            c[k] = deq[((dd.zmask >> (2 * k)) & 3u) * kZStride + sym];
           }
         }
-        __syncwarp();
-        const uint32_t wa = w0 + r, wb = wa + 8;
-        if (wa < nwin) {
-          const float4 *ca = reinterpret_cast<const float4 *>(cb + r * kRowF);
-          const float4 *cbv = reinterpret_cast<const float4 *>(cb + (r + 8) * kRowF);
-          float2 accA[4], accB[4];
+        if (want_lev) {
+          const uint4 l16 = make_uint4(__byte_perm(e0.x, e0.y, 0x7531), __byte_perm(e0.z, e0.w, 0x7531),
+                                       __byte_perm(e1.x, e1.y, 0x7531), __byte_perm(e1.z, e1.w, 0x7531));
+          uint8_t *dl = lev + w * kE;
+          if ((reinterpret_cast<uintptr_t>(dl) & 15u) == 0) {
+            *reinterpret_cast<uint4 *>(dl) = l16;
+          } else {
+            const uint32_t lw[4] = {l16.x, l16.y, l16.z, l16.w};
 #pragma unroll
-          for (int j = 0; j < 4; ++j) accA[j] = accB[j] = make_float2(0.f, 0.f);
-#pragma unroll
-          for (int kk = 0; kk < kE / 4; ++kk) {
-            const float4 a = ca[kk], b = cbv[kk];
-            const float2 a01 = make_float2(a.x, a.y), a23 = make_float2(a.z, a.w);
-            const float2 b01 = make_float2(b.x, b.y), b23 = make_float2(b.z, b.w);
-#pragma unroll
-            for (int hh = 0; hh < 2; ++hh) {
-              const int m = 2 * kk + hh;  // bins 2m, 2m+1
-              const float4 p01 = bas4[m * (kN / 2) + 2 * q];      // columns 4q, 4q+1
-              const float4 p23 = bas4[m * (kN / 2) + 2 * q + 1];  // columns 4q+2, 4q+3
-              const float2 cA = hh ? a23 : a01, cB = hh ? b23 : b01;
-              accA[0] = __ffma2_rn(cA, make_float2(p01.x, p01.y), accA[0]);
-              accA[1] = __ffma2_rn(cA, make_float2(p01.z, p01.w), accA[1]);
-              accA[2] = __ffma2_rn(cA, make_float2(p23.x, p23.y), accA[2]);
-              accA[3] = __ffma2_rn(cA, make_float2(p23.z, p23.w), accA[3]);
-              accB[0] = __ffma2_rn(cB, make_float2(p01.x, p01.y), accB[0]);
-              accB[1] = __ffma2_rn(cB, make_float2(p01.z, p01.w), accB[1]);
-              accB[2] = __ffma2_rn(cB, make_float2(p23.x, p23.y), accB[2]);
-              accB[3] = __ffma2_rn(cB, make_float2(p23.z, p23.w), accB[3]);
-            }
+            for (int j = 0; j < 16; ++j) dl[j] = (uint8_t)(lw[j >> 2] >> (8 * (j & 3)));
           }
-          store_window(out, S, (win0 + wa) * kN, q, accA, aligned);
-          if (wb < nwin) store_window(out, S, (win0 + wb) * kN, q, accB, aligned);
+        }
+        const uint64_t s0 = (win0 + w) * kN;
+        float *const dst = out + s0;
+        if (s0 + kN <= S && vec32) {
+          idct32(c, [&](int b, const float(&v)[8]) { st_cs_v8(dst + 8 * b, v); });
+        } else if (s0 + kN <= S && (aligned & 1u)) {
+          idct32(c, [&](int b, const float(&v)[8]) {
+            __stcs(reinterpret_cast<float4 *>(dst + 8 * b), make_float4(v[0], v[1], v[2], v[3]));
+            __stcs(reinterpret_cast<float4 *>(dst + 8 * b) + 1, make_float4(v[4], v[5], v[6], v[7]));
+          });
+        } else {
+          idct32(c, [&](int b, const float(&v)[8]) {
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+              if (s0 + 8 * b + i < S) dst[8 * b + i] = v[i];
+          });
         }
       }
     }
@@ -413,11 +459,10 @@ size_t warp_smem_layout(uint32_t threads, const uint32_t *lmax, uint32_t n_domai
     wp->tab_off[d] = (uint32_t)o;
     o += align16(3u * kZStride * 4);
   }
-  wp->basis_off = (uint32_t)o;
-  o += (size_t)(kE / 2) * kN * 8;
+  wp->basis_off = 0;
   o = align16(o);
   wp->warp_off = (uint32_t)o;
-  wp->warp_bytes = (uint32_t)align16((size_t)kPassWords * 8 + 32 + (size_t)kStage * 2 + 2 * (size_t)kStepWin * kRowF * 4);
+  wp->warp_bytes = (uint32_t)align16((size_t)kPassWords * 8 + 32 + (size_t)kStage * 2);
   return o + (size_t)(threads / 32) * wp->warp_bytes;
 }
 

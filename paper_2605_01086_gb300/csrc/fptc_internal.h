@@ -51,7 +51,7 @@ struct SegDev {
   uint32_t n_chunks;
   uint32_t domain;
   uint32_t caller_index; // position in the caller's segment array
-  uint32_t out_aligned;  // out_offset % 4 == 0: 16-byte vector stores allowed
+  uint32_t out_aligned;  // bit 0: out_offset % 4 == 0 (16-byte stores), bit 1: % 8 == 0 (32-byte stores)
 };
 
 struct ChunkDev {

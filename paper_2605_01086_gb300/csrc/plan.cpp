@@ -556,7 +556,7 @@ fptc_status fptc_plan_create(fptc_plan **out, int device, const fptc_domain *dom
     sd.n_windows = (s.n_samples + d.N - 1) / d.N;
     sd.domain = s.domain;
     sd.caller_index = ci;
-    sd.out_aligned = (s.out_offset % 4) == 0;
+    sd.out_aligned = ((s.out_offset % 4) == 0 ? 1u : 0u) | ((s.out_offset % 8) == 0 ? 2u : 0u);
     sd.chunk_base = chunk;
     sd.n_chunks = (uint32_t)((s.n_words + kChunkWords - 1) / kChunkWords);
     for (uint32_t c = 0; c < sd.n_chunks; ++c) {
