@@ -242,7 +242,7 @@ fptc_status fptc_plan_autotune(fptc_plan *plan, const uint64_t *d_words, const u
  * Same result as a plan with one segment (word_offset 0, out_offset 0) and the
  * generic kernel: index kernels + decode kernel of Sec. 4.2, samples written to
  * d_out[0 .. n_samples).  All working memory (domain tables, records, index
- * scratch, status word) is one file-scope device array of about 1.3 MB that
+ * scratch, status word) is one file-scope device array of about 2 MB that
  * every device which loads the library keeps until exit; nothing is allocated
  * and no library routine that allocates is called.
  * Limits: n_samples <= 67,108,864 and domain->lmax <= 12, else

@@ -1,6 +1,6 @@
 // Fused decode for the Table 1 shape (N = 32, E = 16) with one warp per tile.
 //
-// Each warp owns a contiguous range of tiles of 64 windows (1024 symbols, 2048
+// Each warp owns a contiguous range of tiles of 128 windows (2048 symbols, 4096
 // samples) and runs Sec. 4.2 on each with no block-wide barrier:
 //  1. SymLen decode.  A pass gives every lane two consecutive words; a warp
 //     scan of their symbol counts places each word's codewords (compaction,
@@ -33,12 +33,12 @@ namespace {
 
 constexpr int kN = 32;
 constexpr int kE = 16;
-constexpr int kT = 64;                     // windows per tile
+constexpr int kT = 128;                    // windows per tile
 constexpr int kTS = kT * kE;               // symbols per tile
 constexpr int kGuard = 64;                 // entries before and after the tile (a word holds <= 64 codewords)
 constexpr int kStage = kTS + 2 * kGuard;   // 16-bit entries per warp
 constexpr int kZStride = 257;              // floats per zone row (zero levels of the zones in different banks)
-constexpr int kWPL = 2;                    // words per lane per decode pass
+constexpr int kWPL = 2;                    // consecutive words per lane per decode pass
 constexpr int kPassWords = 32 * kWPL;
 // zone mask of Table 1 (B1 = 2, B2 = 16): bins 0, 1 in zone 0, the rest in zone 1
 constexpr uint32_t kZmaskTable1 = 0x55555550u;
@@ -188,15 +188,16 @@ __device__ __forceinline__ Ctx make_ctx(const DecodeParams &p, uint64_t g, uint3
   return c;
 }
 
-// Words i0 + 2 lane, i0 + 2 lane + 1 of a tile (zero beyond its word count).
+// Words i0 + kWPL lane + u (u < kWPL) of a tile (zero beyond its word count).
 __device__ __forceinline__ void load_pass(const DecodeParams &p, const Ctx &c, uint32_t i0, uint32_t lane,
-                                          uint64_t &wa, uint64_t &wb, uint32_t &na, uint32_t &nb) {
-  const uint32_t i = i0 + 2 * lane;
-  const bool ia = c.ok && i < c.nw, ib = c.ok && i + 1 < c.nw;
-  wa = ia ? __ldg(p.words + c.fw + i) : 0ull;
-  wb = ib ? __ldg(p.words + c.fw + i + 1) : 0ull;
-  na = ia ? (uint32_t)__ldg(p.symlen + c.fw + i) : 0u;
-  nb = ib ? (uint32_t)__ldg(p.symlen + c.fw + i + 1) : 0u;
+                                          uint64_t (&w)[kWPL], uint32_t (&n)[kWPL]) {
+#pragma unroll
+  for (int u = 0; u < kWPL; ++u) {
+    const uint32_t i = i0 + kWPL * lane + u;
+    const bool in = c.ok && i < c.nw;
+    w[u] = in ? __ldg(p.words + c.fw + i) : 0ull;
+    n[u] = in ? (uint32_t)__ldg(p.symlen + c.fw + i) : 0u;
+  }
 }
 
 __device__ __forceinline__ uint32_t smem_addr(const void *ptr) {
@@ -222,17 +223,20 @@ __device__ __forceinline__ void fetch_records(const DecodeParams &p, uint64_t g,
   cp_async_commit();
 }
 
-// First pass of a tile: words 2 lane, 2 lane + 1 into wbuf (copies), their
-// symbol counts into registers (zero beyond the tile's words).
-__device__ __forceinline__ void fetch_pass0(const DecodeParams &p, const Ctx &c, uint32_t lane, uint64_t *wbuf,
-                                            uint32_t &na, uint32_t &nb) {
-  const uint32_t i = 2 * lane;
-  const bool ia = c.ok && i < c.nw, ib = c.ok && i + 1 < c.nw;
-  if (ia) cp_async8(wbuf + i, p.words + c.fw + i);
-  if (ib) cp_async8(wbuf + i + 1, p.words + c.fw + i + 1);
+// First pass of a tile: words kWPL lane + u into wbuf (copies), their symbol
+// counts packed one per byte into a register (zero beyond the tile's words).
+__device__ __forceinline__ uint32_t fetch_pass0(const DecodeParams &p, const Ctx &c, uint32_t lane, uint64_t *wbuf) {
+  uint32_t packed = 0;
+#pragma unroll
+  for (int u = 0; u < kWPL; ++u) {
+    const uint32_t i = kWPL * lane + u;
+    if (c.ok && i < c.nw) {
+      cp_async8(wbuf + i, p.words + c.fw + i);
+      packed |= (uint32_t)__ldg(p.symlen + c.fw + i) << (8 * u);
+    }
+  }
   cp_async_commit();
-  na = ia ? (uint32_t)__ldg(p.symlen + c.fw + i) : 0u;
-  nb = ib ? (uint32_t)__ldg(p.symlen + c.fw + i + 1) : 0u;
+  return packed;
 }
 
 template <int WARPS>
@@ -301,8 +305,7 @@ __global__ void __launch_bounds__(WARPS * 32, 32 / WARPS) k_decode_warp(const De
   fetch_records(p, tw0, lane, rec);
   cp_async_wait_all();
   __syncwarp();
-  uint32_t pna, pnb;
-  fetch_pass0(p, make_ctx(p, tw0, s, rec[0], rec[1]), lane, wbuf, pna, pnb);
+  uint32_t pn = fetch_pass0(p, make_ctx(p, tw0, s, rec[0], rec[1]), lane, wbuf);
 
   for (uint64_t g = tw0; g < tw1; ++g) {
     // ---- tile g: its records and first words have been requested
@@ -310,8 +313,13 @@ __global__ void __launch_bounds__(WARPS * 32, 32 / WARPS) k_decode_warp(const De
     __syncwarp();
     while (g >= p.segs[s].tile_base + p.segs[s].n_tiles) ++s;
     const Ctx cur = make_ctx(p, g, s, rec[0], rec[1]);
-    uint64_t wa = wbuf[2 * lane], wb = wbuf[2 * lane + 1];
-    uint32_t na = pna, nb = pnb;
+    uint64_t w[kWPL];
+    uint32_t n[kWPL];
+#pragma unroll
+    for (int u = 0; u < kWPL; ++u) {
+      w[u] = wbuf[kWPL * lane + u];
+      n[u] = (pn >> (8 * u)) & 0xffu;
+    }
     __syncwarp();
     const uint64_t g1 = g + 1;
     if (g1 < tw1) fetch_records(p, g1, lane, rec);  // consumed after the decode
@@ -329,10 +337,20 @@ __global__ void __launch_bounds__(WARPS * 32, 32 / WARPS) k_decode_warp(const De
       int32_t base = -(int32_t)cur.skip;
       uint32_t bad = 0;
       for (uint32_t c0 = 0; c0 < cur.nw; c0 += kPassWords) {
-        uint64_t xa = 0, xb = 0;
-        uint32_t xna = 0, xnb = 0;
-        if (c0 + kPassWords < cur.nw) load_pass(p, cur, c0 + kPassWords, lane, xa, xb, xna, xnb);
-        const uint32_t tot = na + nb;
+        uint64_t xw[kWPL];
+        uint32_t xn[kWPL];
+        if (c0 + kPassWords < cur.nw) {
+          load_pass(p, cur, c0 + kPassWords, lane, xw, xn);
+        } else {
+#pragma unroll
+          for (int u = 0; u < kWPL; ++u) {
+            xw[u] = 0;
+            xn[u] = 0;
+          }
+        }
+        uint32_t tot = 0;
+#pragma unroll
+        for (int u = 0; u < kWPL; ++u) tot += n[u];
         uint32_t x = tot;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -342,17 +360,24 @@ __global__ void __launch_bounds__(WARPS * 32, 32 / WARPS) k_decode_warp(const De
         const uint32_t total = __shfl_sync(0xffffffffu, x, 31);
         uint16_t *dst = stage + base + (int32_t)(x - tot);
         if (dd.complete) {
-          bad |= decode_word<false>(wa, na, dst, lut, dd.shift);
-          bad |= decode_word<false>(wb, nb, dst + na, lut, dd.shift);
+#pragma unroll
+          for (int u = 0; u < kWPL; ++u) {
+            bad |= decode_word<false>(w[u], n[u], dst, lut, dd.shift);
+            dst += n[u];
+          }
         } else {
-          bad |= decode_word<true>(wa, na, dst, lut, dd.shift);
-          bad |= decode_word<true>(wb, nb, dst + na, lut, dd.shift);
+#pragma unroll
+          for (int u = 0; u < kWPL; ++u) {
+            bad |= decode_word<true>(w[u], n[u], dst, lut, dd.shift);
+            dst += n[u];
+          }
         }
         base += (int32_t)total;
-        wa = xa;
-        wb = xb;
-        na = xna;
-        nb = xnb;
+#pragma unroll
+        for (int u = 0; u < kWPL; ++u) {
+          w[u] = xw[u];
+          n[u] = xn[u];
+        }
       }
       bad = __reduce_or_sync(0xffffffffu, bad);
       if (bad && lane == 0) flag_bad(p.status, bad, sg.caller_index);
@@ -364,7 +389,7 @@ __global__ void __launch_bounds__(WARPS * 32, 32 / WARPS) k_decode_warp(const De
       __syncwarp();
       uint32_t s1 = s;
       while (g1 >= p.segs[s1].tile_base + p.segs[s1].n_tiles) ++s1;
-      fetch_pass0(p, make_ctx(p, g1, s1, rec[0], rec[1]), lane, wbuf, pna, pnb);
+      pn = fetch_pass0(p, make_ctx(p, g1, s1, rec[0], rec[1]), lane, wbuf);
     }
     __syncwarp();
 

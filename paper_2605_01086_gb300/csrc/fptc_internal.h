@@ -2,6 +2,7 @@
 // Nothing here is part of the C ABI.
 #pragma once
 
+#include <algorithm>
 #include <cstdint>
 
 #include <cuda_runtime.h>
@@ -10,11 +11,13 @@
 
 namespace fptc {
 
-// Index work unit: the symlen array of a segment is cut into chunks of this many
-// words; the symbol offsets of the SymLen words (Sec. 4.2.1) are an exclusive
-// scan over chunks, then over words inside a chunk.
-constexpr uint32_t kChunkWords = 2048;
-constexpr uint32_t kIndexThreads = 256;  // kChunkWords / kIndexThreads = 8 words per thread
+// Index work unit: a segment's symlen bytes are cut into chunks of 31 aligned
+// 16-byte blocks (496 words, fewer in the segment's first and last chunk); the
+// symbol offsets of the SymLen words (Sec. 4.2.1) are an exclusive scan over
+// chunks, then over words inside a chunk.
+constexpr uint32_t kChunkWords = 496;
+// Chunks of a segment of n words for any placement of its first byte.
+__host__ __device__ constexpr uint64_t chunks_of(uint64_t n) { return n ? ((n + 15) / 16 + 1 + 30) / 31 : 0; }
 constexpr uint32_t kMaxLmax = 16;
 constexpr uint32_t kChunkBad = 0xFFFFFFFFu;  // chunk sum sentinel: a symlen > 64 was seen
 
@@ -54,12 +57,6 @@ struct SegDev {
   uint32_t out_aligned;  // bit 0: out_offset % 4 == 0 (16-byte stores), bit 1: % 8 == 0 (32-byte stores)
 };
 
-struct ChunkDev {
-  uint64_t word_begin;
-  uint32_t n_words;
-  uint32_t seg;          // queue index of the owning segment
-};
-
 // Start of a tile in the SymLen stream: the word holding the tile's first symbol
 // and how many earlier symbols of that word belong to the previous tile.
 struct TileRec {
@@ -78,7 +75,6 @@ struct IndexParams {
   const uint8_t *symlen;
   const SegDev *segs;
   const DomainDev *domains;
-  const ChunkDev *chunks;
   uint32_t *chunk_sum;
   uint64_t *chunk_off;
   uint32_t *seg_bad;
@@ -86,6 +82,8 @@ struct IndexParams {
   DevStatus *status;
   uint64_t chunk_begin, chunk_end;  // chunk range of this launch
   uint32_t seg_begin, seg_end;      // segment range of this launch
+  uint32_t grid;                    // CTAs of the chunk kernels (0: a default)
+  uint32_t pad;
 };
 
 struct DecodeParams {

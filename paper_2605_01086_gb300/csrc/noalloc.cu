@@ -27,7 +27,7 @@ namespace {
 constexpr uint64_t kNaMaxSamples = 1ull << 26;                   // 67,108,864 samples per call
 constexpr uint32_t kNaTileSamples = 4096;                        // generic kernel tile size
 constexpr uint64_t kNaMaxWords = kNaMaxSamples;                  // words <= symbols <= samples (E <= N)
-constexpr uint64_t kNaMaxChunks = (kNaMaxWords + kChunkWords - 1) / kChunkWords;
+constexpr uint64_t kNaMaxChunks = chunks_of(kNaMaxWords);
 constexpr uint32_t kNaMaxLmax = 12;                              // decode table of 4096 entries
 
 // Byte layout of the scratch array (each piece 256-byte aligned).
@@ -40,8 +40,7 @@ constexpr size_t kOffLut = a256(kOffDom + sizeof(DomainDev));
 constexpr size_t kOffBasis = a256(kOffLut + (size_t(2) << kNaMaxLmax));
 constexpr size_t kOffChunkSum = a256(kOffBasis + 128 * 128 * sizeof(float));
 constexpr size_t kOffChunkOff = a256(kOffChunkSum + kNaMaxChunks * sizeof(uint32_t));
-constexpr size_t kOffChunks = a256(kOffChunkOff + kNaMaxChunks * sizeof(uint64_t));
-constexpr size_t kOffTiles = a256(kOffChunks + kNaMaxChunks * sizeof(ChunkDev));
+constexpr size_t kOffTiles = a256(kOffChunkOff + kNaMaxChunks * sizeof(uint64_t));
 // a tile holds floor(4096 / N) windows, i.e. >= 4096 - N + 1 >= 3969 samples (N <= 128)
 constexpr uint64_t kNaTileCap = kNaMaxSamples / 3968 + 2;
 constexpr size_t kScratchBytes = a256(kOffTiles + kNaTileCap * sizeof(TileRec));
@@ -161,7 +160,7 @@ extern "C" fptc_status fptc_decode_stream_noalloc(const fptc_domain *domain, con
   sg.tile_base = 0;
   sg.n_tiles = (W + dd.tile_windows - 1) / dd.tile_windows;
   sg.chunk_base = 0;
-  sg.n_chunks = (uint32_t)((n_words + kChunkWords - 1) / kChunkWords);
+  sg.n_chunks = (uint32_t)chunks_of(n_words);
   sg.domain = 0;
   sg.caller_index = 0;
   sg.out_aligned = (reinterpret_cast<uintptr_t>(d_out) & 15u) == 0;
@@ -188,20 +187,6 @@ extern "C" fptc_status fptc_decode_stream_noalloc(const fptc_domain *domain, con
         basis[k * dm.N + n] = k == 0 ? 0.5f : static_cast<float>(std::cos(M_PI * (2.0 * n + 1.0) * k / (2.0 * dm.N)));
     e = cudaMemcpyAsync(scr + kOffBasis, basis, (size_t)dm.E * dm.N * sizeof(float), cudaMemcpyHostToDevice, s);
   }
-  {
-    ChunkDev part[256];
-    for (uint64_t c0 = 0; c0 < sg.n_chunks && e == cudaSuccess; c0 += 256) {
-      const uint64_t m = std::min<uint64_t>(256, sg.n_chunks - c0);
-      for (uint64_t i = 0; i < m; ++i) {
-        const uint64_t c = c0 + i;
-        part[i].word_begin = c * kChunkWords;
-        part[i].n_words = (uint32_t)std::min<uint64_t>(kChunkWords, n_words - c * kChunkWords);
-        part[i].seg = 0;
-      }
-      e = cudaMemcpyAsync(scr + kOffChunks + c0 * sizeof(ChunkDev), part, m * sizeof(ChunkDev),
-                          cudaMemcpyHostToDevice, s);
-    }
-  }
   if (e != cudaSuccess) {
     set_error("allocation-free decode upload: %s", cudaGetErrorString(e));
     return FPTC_ERR_CUDA;
@@ -212,7 +197,6 @@ extern "C" fptc_status fptc_decode_stream_noalloc(const fptc_domain *domain, con
   ip.symlen = d_symlen;
   ip.segs = reinterpret_cast<const SegDev *>(scr + kOffSeg);
   ip.domains = reinterpret_cast<const DomainDev *>(scr + kOffDom);
-  ip.chunks = reinterpret_cast<const ChunkDev *>(scr + kOffChunks);
   ip.chunk_sum = reinterpret_cast<uint32_t *>(scr + kOffChunkSum);
   ip.chunk_off = reinterpret_cast<uint64_t *>(scr + kOffChunkOff);
   ip.seg_bad = reinterpret_cast<uint32_t *>(scr + kOffSegBad);
@@ -222,6 +206,7 @@ extern "C" fptc_status fptc_decode_stream_noalloc(const fptc_domain *domain, con
   ip.chunk_end = sg.n_chunks;
   ip.seg_begin = 0;
   ip.seg_end = 1;
+  ip.grid = 0;
   e = launch_index(ip, s);
   if (e != cudaSuccess) {
     set_error("allocation-free index launch: %s", cudaGetErrorString(e));

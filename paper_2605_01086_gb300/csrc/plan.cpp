@@ -28,14 +28,12 @@ struct fptc_plan {
   std::vector<uint32_t> queue;           // queue position -> caller index
   std::vector<SegDev> segs;              // queue order
   std::vector<DomainDev> dom_dev;
-  std::vector<ChunkDev> chunks;
   std::vector<uint64_t> level_off;       // caller order
   uint64_t n_tiles = 0, n_chunks = 0, n_levels = 0;
   uint64_t words_extent = 0, out_extent = 0, n_samples = 0, n_words = 0;
   // device memory owned by the plan
   DomainDev *d_domains = nullptr;
   SegDev *d_segs = nullptr;
-  ChunkDev *d_chunks = nullptr;
   uint16_t *d_luts = nullptr;
   float *d_basis = nullptr;
   uint32_t *d_chunk_sum = nullptr;
@@ -90,7 +88,6 @@ cudaError_t upload(T **dst, const std::vector<T> &src, size_t *bytes) {
 void free_device(fptc_plan *p) {
   cudaFree(p->d_domains);
   cudaFree(p->d_segs);
-  cudaFree(p->d_chunks);
   cudaFree(p->d_luts);
   cudaFree(p->d_basis);
   cudaFree(p->d_chunk_sum);
@@ -248,7 +245,7 @@ IndexParams index_params(const fptc_plan *p, const uint8_t *d_symlen) {
   ip.symlen = d_symlen;
   ip.segs = p->d_segs;
   ip.domains = p->d_domains;
-  ip.chunks = p->d_chunks;
+  ip.grid = (uint32_t)p->sm_count * 8u;
   ip.chunk_sum = p->d_chunk_sum;
   ip.chunk_off = p->d_chunk_off;
   ip.seg_bad = p->d_seg_bad;
@@ -558,14 +555,7 @@ fptc_status fptc_plan_create(fptc_plan **out, int device, const fptc_domain *dom
     sd.caller_index = ci;
     sd.out_aligned = ((s.out_offset % 4) == 0 ? 1u : 0u) | ((s.out_offset % 8) == 0 ? 2u : 0u);
     sd.chunk_base = chunk;
-    sd.n_chunks = (uint32_t)((s.n_words + kChunkWords - 1) / kChunkWords);
-    for (uint32_t c = 0; c < sd.n_chunks; ++c) {
-      ChunkDev ch;
-      ch.word_begin = s.word_offset + (uint64_t)c * kChunkWords;
-      ch.n_words = (uint32_t)std::min<uint64_t>(kChunkWords, s.n_words - (uint64_t)c * kChunkWords);
-      ch.seg = (uint32_t)qi;
-      p->chunks.push_back(ch);
-    }
+    sd.n_chunks = (uint32_t)chunks_of(s.n_words);
     chunk += sd.n_chunks;
   }
   p->n_chunks = chunk;
@@ -589,7 +579,6 @@ fptc_status fptc_plan_create(fptc_plan **out, int device, const fptc_domain *dom
     size_t b = 0;
     if ((e = upload(&p->d_domains, p->dom_dev, &b)) != cudaSuccess ||
         (e = upload(&p->d_segs, p->segs, &b)) != cudaSuccess ||
-        (e = upload(&p->d_chunks, p->chunks, &b)) != cudaSuccess ||
         (e = upload(&p->d_luts, luts, &b)) != cudaSuccess || (e = upload(&p->d_basis, basis, &b)) != cudaSuccess) {
       st = cuda_fail(e, "plan upload");
     }
