@@ -116,7 +116,7 @@ typedef struct fptc_plan_options {
   uint32_t schedule;      /* fptc_schedule */
   uint32_t tile_samples;  /* target output samples per tile (whole windows); 0 = 8192 if every domain
                              has N = 32, E = 16, else 4096 */
-  uint32_t threads;       /* threads per CTA: 128, 256 or 512 (also 1024 for the warp-tile kernel);
+  uint32_t threads;       /* threads per CTA: 128, 256 or 512 (also 768, 1024 for the warp-tile kernel);
                              0 = 256, or for the warp-tile kernel the most that fit */
   uint32_t ctas_per_sm;   /* persistent CTAs per SM; 0 = as many as fit */
   uint32_t kernel;        /* fptc_kernel: which decode kernel; 0 = choose */

@@ -6,7 +6,7 @@
 //     scan of their symbol counts places each word's codewords (compaction,
 //     Sec. 4.2.1).  A lane decodes a word with one decode-table lookup per
 //     codeword and stores the table entry (code length | level << 8) as a
-//     16-bit value at the codeword's tile position.  Nothing else happens per
+//     16-bit value at the codeword's tile position (two per 32-bit store).  Nothing else happens per
 //     codeword: the dequantization waits for step 2, where the bin of every
 //     value is known at compile time.  The 64-bit word is shifted through
 //     hi:lo with a marker bit under it, so a word whose codewords need more
@@ -129,6 +129,23 @@ __device__ __forceinline__ void st_cs_v8(float *p, const float (&v)[8]) {
                : "memory");
 }
 
+// A window whose output is not 32-byte aligned or that ends the segment
+// (m < 32 samples): 16-byte or scalar stores.  Kept out of line.
+__device__ __noinline__ void idct32_store_slow(const float (&c)[16], float *dst, uint32_t m, uint32_t vec16) {
+  if (m == kN && vec16) {
+    idct32(c, [&](int b, const float(&v)[8]) {
+      __stcs(reinterpret_cast<float4 *>(dst + 8 * b), make_float4(v[0], v[1], v[2], v[3]));
+      __stcs(reinterpret_cast<float4 *>(dst + 8 * b) + 1, make_float4(v[4], v[5], v[6], v[7]));
+    });
+  } else {
+    idct32(c, [&](int b, const float(&v)[8]) {
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+        if ((uint32_t)(8 * b + i) < m) dst[8 * b + i] = v[i];
+    });
+  }
+}
+
 struct DomW {
   uint32_t lut_off;   // bytes from the start of shared memory: 16-bit entries len | level << 8
   uint32_t deq_off;   // bytes: zone rows [3][kZStride] floats (row 2 zero)
@@ -149,14 +166,26 @@ __device__ __forceinline__ uint32_t decode_word(uint64_t w, uint32_t n, uint16_t
                                                 const uint16_t *__restrict__ lut, uint32_t shift) {
   uint32_t hi = (uint32_t)(w >> 32), lo = (uint32_t)w, mk = 0x80000000u;
   uint32_t low = 31u;
-  for (uint32_t j = 0; j < n; ++j) {
+  auto step = [&]() -> uint32_t {
     const uint32_t e = lut[hi >> shift];
     hi = __funnelshift_l(lo, hi, e);
     lo = __funnelshift_l(mk, lo, e);
     mk = __funnelshift_l(0u, mk, e);
-    dst[j] = (uint16_t)e;
     if (CHECKED) low = min(low, e & 31u);
+    return e;
+  };
+  // entries go out two per 32-bit store where both are this word's
+  uint32_t j = 0;
+  if (n && (reinterpret_cast<uintptr_t>(dst) & 2u)) {
+    dst[0] = (uint16_t)step();
+    j = 1;
   }
+  for (; j + 2 <= n; j += 2) {
+    const uint32_t e0 = step();
+    const uint32_t e1 = step();
+    *reinterpret_cast<uint32_t *>(dst + j) = __byte_perm(e0, e1, 0x5410);
+  }
+  if (j < n) dst[j] = (uint16_t)step();
   return ((hi | lo | mk) == 0u ? kFlagBitOverrun : 0u) | ((CHECKED && low == 0u) ? kFlagInvalidCode : 0u);
 }
 
@@ -240,7 +269,7 @@ __device__ __forceinline__ uint32_t fetch_pass0(const DecodeParams &p, const Ctx
 }
 
 template <int WARPS>
-__global__ void __launch_bounds__(WARPS * 32, 32 / WARPS) k_decode_warp(const DecodeParams p,
+__global__ void __launch_bounds__(WARPS * 32, WARPS > 16 ? 1 : 32 / WARPS) k_decode_warp(const DecodeParams p,
                                                                                  const WarpParams wp) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   DomW *const dw = reinterpret_cast<DomW *>(smem_raw);
@@ -435,20 +464,10 @@ __global__ void __launch_bounds__(WARPS * 32, 32 / WARPS) k_decode_warp(const De
         }
         const uint64_t s0 = (win0 + w) * kN;
         float *const dst = out + s0;
-        if (s0 + kN <= S && vec32) {
+        if (s0 + kN <= S && vec32)
           idct32(c, [&](int b, const float(&v)[8]) { st_cs_v8(dst + 8 * b, v); });
-        } else if (s0 + kN <= S && (aligned & 1u)) {
-          idct32(c, [&](int b, const float(&v)[8]) {
-            __stcs(reinterpret_cast<float4 *>(dst + 8 * b), make_float4(v[0], v[1], v[2], v[3]));
-            __stcs(reinterpret_cast<float4 *>(dst + 8 * b) + 1, make_float4(v[4], v[5], v[6], v[7]));
-          });
-        } else {
-          idct32(c, [&](int b, const float(&v)[8]) {
-#pragma unroll
-            for (int i = 0; i < 8; ++i)
-              if (s0 + 8 * b + i < S) dst[8 * b + i] = v[i];
-          });
-        }
+        else
+          idct32_store_slow(c, dst, s0 + kN <= S ? kN : (uint32_t)(S - s0), aligned & 1u);
       }
     }
     __syncwarp();  // the staging entries are rewritten by the next tile
@@ -465,6 +484,7 @@ void *wpick(uint32_t threads) {
     case 128: return wptr<4>();
     case 256: return wptr<8>();
     case 512: return wptr<16>();
+    case 768: return wptr<24>();
     case 1024: return wptr<32>();
     default: return nullptr;
   }

@@ -151,9 +151,9 @@ fptc_status configure_launch(fptc_plan *p) {
       threads /= 2;
   }
   const bool t_ok = threads == 128 || threads == 256 || threads == 512 ||
-                    (threads == 1024 && p->kind == FPTC_KERNEL_WARP_TILE);
+                    ((threads == 768 || threads == 1024) && p->kind == FPTC_KERNEL_WARP_TILE);
   if (!t_ok) {
-    set_error("threads must be 128, 256 or 512 (1024 also for the warp-tile kernel; got %u)", threads);
+    set_error("threads must be 128, 256 or 512 (768 and 1024 also for the warp-tile kernel; got %u)", threads);
     return FPTC_ERR_INVALID_ARGUMENT;
   }
   p->threads = threads;
