@@ -133,9 +133,10 @@ def segments_array(word_offset, n_words, n_samples, out_offset, domain) -> np.nd
     return s
 
 
-def packed_out_offsets(n_samples, align: int = 8) -> np.ndarray:
-    """Output offsets of consecutive segments, each rounded up to `align` floats (8: 32 bytes,
-    the alignment at which the warp-tile kernel stores a full 32-byte sector per instruction)."""
+def packed_out_offsets(n_samples, align: int = 32) -> np.ndarray:
+    """Output offsets of consecutive segments, each rounded up to `align` floats (32: 128 bytes,
+    the alignment at which the warp-tile kernel stores whole 32-window tiles with the TMA unit;
+    8 floats still allow its 32-byte stores)."""
     n_samples = np.asarray(n_samples, dtype=np.uint64)
     padded = (n_samples + np.uint64(align - 1)) // np.uint64(align) * np.uint64(align)
     off = np.zeros(len(n_samples), np.uint64)
@@ -144,7 +145,7 @@ def packed_out_offsets(n_samples, align: int = 8) -> np.ndarray:
     return off
 
 
-def encode_batch(domains, x_flat, x_offsets, lengths, domain_idx, n_threads: int = 0, out_align: int = 8) -> Batch:
+def encode_batch(domains, x_flat, x_offsets, lengths, domain_idx, n_threads: int = 0, out_align: int = 32) -> Batch:
     """Encodes many signals on the host threads; output offsets packed with `out_align` floats alignment."""
     x = np.ascontiguousarray(x_flat, dtype=np.float32)
     x_offsets = np.ascontiguousarray(x_offsets, dtype=np.uint64)

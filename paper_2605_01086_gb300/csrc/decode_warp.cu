@@ -5,27 +5,36 @@
 //  1. SymLen decode.  A pass gives every lane two consecutive words; a warp
 //     scan of their symbol counts places each word's codewords (compaction,
 //     Sec. 4.2.1).  A lane decodes a word with one decode-table lookup per
-//     codeword and stores the table entry (code length | level << 8) as a
-//     16-bit value at the codeword's tile position (two per 32-bit store).  Nothing else happens per
+//     codeword and stores the codeword's level as one byte at its tile
+//     position (two per 16-bit store).  Nothing else happens per
 //     codeword: the dequantization waits for step 2, where the bin of every
 //     value is known at compile time.  The 64-bit word is shifted through
 //     hi:lo with a marker bit under it, so a word whose codewords need more
 //     than 64 bits shows as an empty buffer at the end (no per-codeword count).
 //  2. Dequantization and inverse DCT, one window per lane.  The lane reads its
-//     window's 16 entries, turns each level into A_z * unit_z(level) (one
-//     table read; the bin, hence the zone row, is fixed per register), and
-//     evaluates the inverse of Eq. 1 by the even/odd split of the DCT-III:
+//     window's 16 levels, turns each into A_z * unit_z(level) (one table read;
+//     the bin, hence the zone row, is fixed per register), and evaluates the
+//     inverse of Eq. 1 by the even/odd split of the DCT-III:
 //     x[n] = E[n] + O[n], x[31-n] = E[n] - O[n] with O the odd bins and E the
 //     even bins, itself split the same way twice (E[15-n] = EE[n] - EO[n],
 //     EE[7-n] = EEE[n] - EEO[n]); 229 FP32 operations per window with the
 //     cosines as compile-time constants, so neither a basis nor coefficients
-//     pass through shared memory.  32-byte streaming stores (one full sector
-//     per thread and instruction) where the output is 32-byte aligned.
+//     pass through shared memory.
+//  3. Output.  Where the segment's output starts on a 128-byte boundary and
+//     all 32 windows of a step are whole, the lanes write their windows into
+//     the warp's shared staging tile in the 128-byte swizzled layout (chunk c
+//     of row r at c ^ (r & 7): conflict-free) and one lane stores the tile
+//     with a TMA tensor store (the output viewed as rows of 32 floats), so the
+//     output never passes through the L1 load/store pipe.  Other windows use
+//     32-byte (or 16-byte, or scalar) streaming stores.
 //  The tile records of tile g+1 are loaded when tile g starts, the first words
 //  of tile g+1 when tile g's decode ends (hidden by its transform), and the
 //  words of a tile's next decode pass before the current pass.
 // The decode tables, dequantization rows and basis of every domain stay in
 // shared memory for the whole kernel.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include "device_util.cuh"
 
 namespace fptc {
@@ -36,10 +45,13 @@ constexpr int kE = 16;
 constexpr int kT = 128;                    // windows per tile
 constexpr int kTS = kT * kE;               // symbols per tile
 constexpr int kGuard = 64;                 // entries before and after the tile (a word holds <= 64 codewords)
-constexpr int kStage = kTS + 2 * kGuard;   // 16-bit entries per warp
+constexpr int kStage = kTS + 2 * kGuard;   // level bytes per warp
 constexpr int kZStride = 257;              // floats per zone row (zero levels of the zones in different banks)
 constexpr int kWPL = 2;                    // consecutive words per lane per decode pass
 constexpr int kPassWords = 32 * kWPL;
+constexpr int kStepWin = 32;               // windows per transform step (one per lane)
+constexpr int kOutTile = kStepWin * kN * 4;  // bytes of a step's output (TMA box 32 x 32 floats)
+constexpr int kMiscBytes = kPassWords * 8 + 32 + kStage;  // per warp: first-pass words, records, levels
 // zone mask of Table 1 (B1 = 2, B2 = 16): bins 0, 1 in zone 0, the rest in zone 1
 constexpr uint32_t kZmaskTable1 = 0x55555550u;
 
@@ -129,6 +141,19 @@ __device__ __forceinline__ void st_cs_v8(float *p, const float (&v)[8]) {
                : "memory");
 }
 
+// TMA tensor store of a staged 32 x 32-float tile to rows [row, row + 32) of
+// the output, and the waits on it (bulk async-group of the issuing thread).
+__device__ __forceinline__ void tma_store_rows(const CUtensorMap *map, const void *smem_tile, int32_t row) {
+  asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
+                   reinterpret_cast<uint64_t>(map)),
+               "r"(0), "r"(row), "r"(static_cast<uint32_t>(__cvta_generic_to_shared(smem_tile)))
+               : "memory");
+  asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void tma_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void tma_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_shared() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
 // A window whose output is not 32-byte aligned or that ends the segment
 // (m < 32 samples): 16-byte or scalar stores.  Kept out of line.
 __device__ __noinline__ void idct32_store_slow(const float (&c)[16], float *dst, uint32_t m, uint32_t vec16) {
@@ -162,7 +187,7 @@ struct DomW {
 // CHECKED (incomplete code): an entry of length 0 marks a prefix with no
 // codeword.  Returns error flags.
 template <bool CHECKED>
-__device__ __forceinline__ uint32_t decode_word(uint64_t w, uint32_t n, uint16_t *__restrict__ dst,
+__device__ __forceinline__ uint32_t decode_word(uint64_t w, uint32_t n, uint8_t *__restrict__ dst,
                                                 const uint16_t *__restrict__ lut, uint32_t shift) {
   uint32_t hi = (uint32_t)(w >> 32), lo = (uint32_t)w, mk = 0x80000000u;
   uint32_t low = 31u;
@@ -174,18 +199,18 @@ __device__ __forceinline__ uint32_t decode_word(uint64_t w, uint32_t n, uint16_t
     if (CHECKED) low = min(low, e & 31u);
     return e;
   };
-  // entries go out two per 32-bit store where both are this word's
+  // levels go out two per 16-bit store where both are this word's
   uint32_t j = 0;
-  if (n && (reinterpret_cast<uintptr_t>(dst) & 2u)) {
-    dst[0] = (uint16_t)step();
+  if (n && (reinterpret_cast<uintptr_t>(dst) & 1u)) {
+    dst[0] = (uint8_t)(step() >> 8);
     j = 1;
   }
   for (; j + 2 <= n; j += 2) {
     const uint32_t e0 = step();
     const uint32_t e1 = step();
-    *reinterpret_cast<uint32_t *>(dst + j) = __byte_perm(e0, e1, 0x5410);
+    *reinterpret_cast<uint16_t *>(dst + j) = (uint16_t)__byte_perm(e0, e1, 0x0051);
   }
-  if (j < n) dst[j] = (uint16_t)step();
+  if (j < n) dst[j] = (uint8_t)(step() >> 8);
   return ((hi | lo | mk) == 0u ? kFlagBitOverrun : 0u) | ((CHECKED && low == 0u) ? kFlagInvalidCode : 0u);
 }
 
@@ -269,8 +294,8 @@ __device__ __forceinline__ uint32_t fetch_pass0(const DecodeParams &p, const Ctx
 }
 
 template <int WARPS>
-__global__ void __launch_bounds__(WARPS * 32, WARPS > 16 ? 1 : 32 / WARPS) k_decode_warp(const DecodeParams p,
-                                                                                 const WarpParams wp) {
+__global__ void __launch_bounds__(WARPS * 32, WARPS > 16 ? 1 : 32 / WARPS) k_decode_warp(
+    const DecodeParams p, const WarpParams wp, const __grid_constant__ CUtensorMap out_map) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   DomW *const dw = reinterpret_cast<DomW *>(smem_raw);
   const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -315,11 +340,16 @@ __global__ void __launch_bounds__(WARPS * 32, WARPS > 16 ? 1 : 32 / WARPS) k_dec
   }
   __syncthreads();
 
-  unsigned char *const wbase = smem_raw + wp.warp_off + warp * wp.warp_bytes;
+  unsigned char *const wbase = smem_raw + wp.warp_off + warp * kMiscBytes;
   uint64_t *const wbuf = reinterpret_cast<uint64_t *>(wbase);                       // first-pass words
   TileRec *const rec = reinterpret_cast<TileRec *>(wbase + kPassWords * 8);          // records g, g + 1
-  uint16_t *const stage = reinterpret_cast<uint16_t *>(wbase + kPassWords * 8 + 32) + kGuard;  // tile position 0
+  uint8_t *const stage = wbase + kPassWords * 8 + 32 + kGuard;                      // tile position 0
+  // output staging tile: 1024-byte aligned (the period of the 128-byte swizzle)
+  const uintptr_t tiles0 = (reinterpret_cast<uintptr_t>(smem_raw + wp.warp_off + WARPS * kMiscBytes) + 1023) &
+                           ~uintptr_t(1023);
+  unsigned char *const otile = reinterpret_cast<unsigned char *>(tiles0) + warp * kOutTile;
   const bool want_lev = p.levels != nullptr;
+  bool tma_pending = false;
 
   // ---- this warp's tiles: an even split of the launch's tile range over all warps
   const uint64_t n_all = p.tile_end - p.tile_begin;
@@ -387,7 +417,7 @@ __global__ void __launch_bounds__(WARPS * 32, WARPS > 16 ? 1 : 32 / WARPS) k_dec
           if (lane >= (uint32_t)o) x += y;
         }
         const uint32_t total = __shfl_sync(0xffffffffu, x, 31);
-        uint16_t *dst = stage + base + (int32_t)(x - tot);
+        uint8_t *dst = stage + base + (int32_t)(x - tot);
         if (dd.complete) {
 #pragma unroll
           for (int u = 0; u < kWPL; ++u) {
@@ -422,7 +452,7 @@ __global__ void __launch_bounds__(WARPS * 32, WARPS > 16 ? 1 : 32 / WARPS) k_dec
     }
     __syncwarp();
 
-    // ---- 2. dequantization + inverse transform + reassembly, one window per lane
+    // ---- 2./3. dequantization + inverse transform + reassembly, one window per lane
     if (cur.ok) {
       const float *deq = reinterpret_cast<const float *>(smem_raw + dd.deq_off);
       const bool table1 = dd.zmask == kZmaskTable1;  // bins 0, 1 in zone 0, bins 2..15 in zone 1
@@ -430,48 +460,65 @@ __global__ void __launch_bounds__(WARPS * 32, WARPS > 16 ? 1 : 32 / WARPS) k_dec
       const uint64_t S = sg.n_samples;
       const uint32_t aligned = sg.out_aligned;
       const bool vec32 = (aligned & 2u) && (reinterpret_cast<uintptr_t>(p.out) & 31u) == 0;
+      const bool tma_seg = wp.out_tma && (aligned & 4u);
       uint8_t *const lev = want_lev ? p.levels + sg.level_offset + win0 * kE : nullptr;
 #pragma unroll 1
-      for (uint32_t w = lane; w < nwin; w += 32) {
-        const uint4 e0 = *reinterpret_cast<const uint4 *>(stage + w * kE);
-        const uint4 e1 = *reinterpret_cast<const uint4 *>(stage + w * kE + 8);
-        const uint32_t ev[8] = {e0.x, e0.y, e0.z, e0.w, e1.x, e1.y, e1.z, e1.w};
-        float c[16];
-        if (table1) {
-#pragma unroll
-          for (int k = 0; k < 16; ++k) {
-            const uint32_t sym = (k & 1) ? (ev[k >> 1] >> 24) : ((ev[k >> 1] >> 8) & 0xffu);
-            c[k] = deq[(k < 2 ? 0 : kZStride) + sym];
-          }
-        } else {
-#pragma unroll
-          for (int k = 0; k < 16; ++k) {
-            const uint32_t sym = (k & 1) ? (ev[k >> 1] >> 24) : ((ev[k >> 1] >> 8) & 0xffu);
-            c[k] = deq[((dd.zmask >> (2 * k)) & 3u) * kZStride + sym];
-          }
+      for (uint32_t w0 = 0; w0 < nwin; w0 += kStepWin) {
+        const uint32_t w = w0 + lane;
+        // all 32 windows of the step whole and inside the segment: one TMA store
+        const bool tma_step = tma_seg && w0 + kStepWin <= nwin && (win0 + w0 + kStepWin) * kN <= S;
+        if (tma_step && tma_pending) {
+          if (lane == 0) tma_wait_read();  // the previous tile has left the staging buffer
+          __syncwarp();
         }
-        if (want_lev) {
-          const uint4 l16 = make_uint4(__byte_perm(e0.x, e0.y, 0x7531), __byte_perm(e0.z, e0.w, 0x7531),
-                                       __byte_perm(e1.x, e1.y, 0x7531), __byte_perm(e1.z, e1.w, 0x7531));
-          uint8_t *dl = lev + w * kE;
-          if ((reinterpret_cast<uintptr_t>(dl) & 15u) == 0) {
-            *reinterpret_cast<uint4 *>(dl) = l16;
+        if (w < nwin) {
+          const uint4 sv = *reinterpret_cast<const uint4 *>(stage + w * kE);
+          const uint32_t sw[4] = {sv.x, sv.y, sv.z, sv.w};
+          float c[16];
+          if (table1) {
+#pragma unroll
+            for (int k = 0; k < 16; ++k) c[k] = deq[(k < 2 ? 0 : kZStride) + ((sw[k >> 2] >> (8 * (k & 3))) & 0xffu)];
           } else {
-            const uint32_t lw[4] = {l16.x, l16.y, l16.z, l16.w};
 #pragma unroll
-            for (int j = 0; j < 16; ++j) dl[j] = (uint8_t)(lw[j >> 2] >> (8 * (j & 3)));
+            for (int k = 0; k < 16; ++k)
+              c[k] = deq[((dd.zmask >> (2 * k)) & 3u) * kZStride + ((sw[k >> 2] >> (8 * (k & 3))) & 0xffu)];
+          }
+          if (want_lev) {
+            uint8_t *dl = lev + w * kE;
+            if ((reinterpret_cast<uintptr_t>(dl) & 15u) == 0) {
+              *reinterpret_cast<uint4 *>(dl) = sv;
+            } else {
+#pragma unroll
+              for (int j = 0; j < 16; ++j) dl[j] = (uint8_t)(sw[j >> 2] >> (8 * (j & 3)));
+            }
+          }
+          const uint64_t s0 = (win0 + w) * kN;
+          float *const dst = out + s0;
+          if (tma_step) {
+            // row `lane` of the staging tile, 16-byte chunk c at c ^ (lane & 7)
+            unsigned char *const row = otile + lane * (kN * 4);
+            const uint32_t sx = lane & 7u;
+            idct32(c, [&](int b, const float(&v)[8]) {
+              *reinterpret_cast<float4 *>(row + (((2 * b) ^ sx) << 4)) = make_float4(v[0], v[1], v[2], v[3]);
+              *reinterpret_cast<float4 *>(row + (((2 * b + 1) ^ sx) << 4)) = make_float4(v[4], v[5], v[6], v[7]);
+            });
+          } else if (s0 + kN <= S && vec32) {
+            idct32(c, [&](int b, const float(&v)[8]) { st_cs_v8(dst + 8 * b, v); });
+          } else {
+            idct32_store_slow(c, dst, s0 + kN <= S ? kN : (uint32_t)(S - s0), aligned & 1u);
           }
         }
-        const uint64_t s0 = (win0 + w) * kN;
-        float *const dst = out + s0;
-        if (s0 + kN <= S && vec32)
-          idct32(c, [&](int b, const float(&v)[8]) { st_cs_v8(dst + 8 * b, v); });
-        else
-          idct32_store_slow(c, dst, s0 + kN <= S ? kN : (uint32_t)(S - s0), aligned & 1u);
+        if (tma_step) {
+          fence_async_shared();
+          __syncwarp();
+          if (lane == 0) tma_store_rows(&out_map, otile, (int32_t)((sg.out_offset >> 5) + win0 + w0));
+          tma_pending = true;
+        }
       }
     }
     __syncwarp();  // the staging entries are rewritten by the next tile
   }
+  if (tma_pending && lane == 0) tma_wait_all();
 }
 
 template <int WARPS>
@@ -504,11 +551,32 @@ size_t warp_smem_layout(uint32_t threads, const uint32_t *lmax, uint32_t n_domai
     wp->tab_off[d] = (uint32_t)o;
     o += align16(3u * kZStride * 4);
   }
-  wp->basis_off = 0;
   o = align16(o);
   wp->warp_off = (uint32_t)o;
-  wp->warp_bytes = (uint32_t)align16((size_t)kPassWords * 8 + 32 + (size_t)kStage * 2);
-  return o + (size_t)(threads / 32) * wp->warp_bytes;
+  wp->warp_bytes = (uint32_t)kMiscBytes;
+  wp->out_tma = 0;
+  const size_t warps = threads / 32;
+  return o + warps * kMiscBytes + 1023 + warps * kOutTile;  // + alignment of the staging tiles
+}
+
+bool encode_out_map(CUtensorMap *map, float *out, uint64_t extent) {
+  static const PFN_cuTensorMapEncodeTiled_v12000 encode = []() -> PFN_cuTensorMapEncodeTiled_v12000 {
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      return nullptr;
+    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }();
+  const uint64_t rows = extent / kN;
+  if (!encode || !out || (reinterpret_cast<uintptr_t>(out) & 15u) || rows == 0 || rows > 0x7FFFFFFFull) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)kN, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)kN * 4};
+  const cuuint32_t box[2] = {(cuuint32_t)kN, (cuuint32_t)kStepWin};
+  const cuuint32_t estride[2] = {1, 1};
+  return encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, out, dims, strides, box, estride, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 cudaError_t warp_smem_config(uint32_t threads, size_t smem) {
@@ -526,14 +594,15 @@ cudaError_t warp_occupancy(uint32_t threads, size_t smem, int *ctas_per_sm) {
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, k, (int)threads, smem);
 }
 
-cudaError_t launch_warp(const DecodeParams &p, const WarpParams &wp, uint32_t threads, uint32_t grid, size_t smem,
-                        cudaStream_t stream) {
+cudaError_t launch_warp(const DecodeParams &p, const WarpParams &wp, const CUtensorMap &out_map, uint32_t threads,
+                        uint32_t grid, size_t smem, cudaStream_t stream) {
   if (p.tile_end <= p.tile_begin || grid == 0) return cudaSuccess;
   void *k = wpick(threads);
   if (!k) return cudaErrorInvalidValue;
   DecodeParams pp = p;
   WarpParams ww = wp;
-  void *args[] = {&pp, &ww};
+  CUtensorMap mm = out_map;
+  void *args[] = {&pp, &ww, &mm};
   return cudaLaunchKernel(k, dim3(grid), dim3(threads), args, smem, stream);
 }
 

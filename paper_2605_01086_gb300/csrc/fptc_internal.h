@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <cstdint>
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include "fptc.h"
@@ -54,7 +55,7 @@ struct SegDev {
   uint32_t n_chunks;
   uint32_t domain;
   uint32_t caller_index; // position in the caller's segment array
-  uint32_t out_aligned;  // bit 0: out_offset % 4 == 0 (16-byte stores), bit 1: % 8 == 0 (32-byte stores)
+  uint32_t out_aligned;  // bit 0: out_offset % 4 == 0 (16-byte stores), bit 1: % 8 (32-byte), bit 2: % 32 (128-byte rows)
 };
 
 // Start of a tile in the SymLen stream: the word holding the tile's first symbol
@@ -111,7 +112,7 @@ struct WarpParams {
   uint32_t n_domains;
   uint32_t warp_off;    // first byte of the per-warp buffers
   uint32_t warp_bytes;  // bytes per warp
-  uint32_t basis_off;   // paired inverse-transform basis
+  uint32_t out_tma;     // 1: the output tensor map is valid (TMA stores for 128-byte aligned segments)
   uint32_t lut_off[kWarpMaxDomains];  // bytes
   uint32_t tab_off[kWarpMaxDomains];  // bytes
 };
@@ -159,8 +160,11 @@ uint32_t warp_tile_windows();
 size_t warp_smem_layout(uint32_t threads, const uint32_t *lmax, uint32_t n_domains, WarpParams *wp);
 cudaError_t warp_smem_config(uint32_t threads, size_t smem);
 cudaError_t warp_occupancy(uint32_t threads, size_t smem, int *ctas_per_sm);
-cudaError_t launch_warp(const DecodeParams &p, const WarpParams &wp, uint32_t threads, uint32_t grid, size_t smem,
-                        cudaStream_t stream);
+cudaError_t launch_warp(const DecodeParams &p, const WarpParams &wp, const CUtensorMap &out_map, uint32_t threads,
+                        uint32_t grid, size_t smem, cudaStream_t stream);
+// Tensor map of an output buffer of `extent` floats viewed as rows of 32 floats
+// (boxes of 32 x 32, 128-byte swizzle); false if it cannot be made.
+bool encode_out_map(CUtensorMap *map, float *out, uint64_t extent);
 
 // tensor-core kernel for N = 32, E = 16 (decode_tc.cu); mode = fptc_idct (not FP32)
 uint32_t tc_tile_windows();

@@ -146,9 +146,12 @@ fptc_status configure_launch(fptc_plan *p) {
     std::vector<uint32_t> lm;
     for (const auto &d : p->domains) lm.push_back(d.lmax);
     WarpParams probe{};
-    threads = 1024;
-    while (threads > 128 && warp_smem_layout(threads, lm.data(), (uint32_t)lm.size(), &probe) > (size_t)optin)
-      threads /= 2;
+    threads = 128;
+    for (uint32_t t : {1024u, 768u, 512u, 256u})
+      if (warp_smem_layout(t, lm.data(), (uint32_t)lm.size(), &probe) <= (size_t)optin) {
+        threads = t;
+        break;
+      }
   }
   const bool t_ok = threads == 128 || threads == 256 || threads == 512 ||
                     ((threads == 768 || threads == 1024) && p->kind == FPTC_KERNEL_WARP_TILE);
@@ -306,7 +309,13 @@ cudaError_t run_range(const fptc_plan *p, const IndexParams &ip0, const DecodePa
   const uint64_t tiles = dp.tile_end - dp.tile_begin;
   const uint32_t grid = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(p->grid, tiles));
   if (p->kind == FPTC_KERNEL_BLOCK_TILE) return launch_fixed(dp, p->threads, grid, p->smem, st);
-  if (p->kind == FPTC_KERNEL_WARP_TILE) return launch_warp(dp, p->wp, p->threads, grid, p->smem, st);
+  if (p->kind == FPTC_KERNEL_WARP_TILE) {
+    WarpParams wp = p->wp;
+    CUtensorMap map;
+    std::memset(&map, 0, sizeof(map));
+    wp.out_tma = encode_out_map(&map, dp.out, p->out_extent) ? 1u : 0u;
+    return launch_warp(dp, wp, map, p->threads, grid, p->smem, st);
+  }
   if (p->kind == FPTC_KERNEL_TENSOR) return launch_tc(dp, p->tp, p->opts.idct, p->threads, grid, p->smem, st);
   return launch_decode(dp, p->kind, p->threads, grid, p->smem, st);
 }
@@ -553,7 +562,8 @@ fptc_status fptc_plan_create(fptc_plan **out, int device, const fptc_domain *dom
     sd.n_windows = (s.n_samples + d.N - 1) / d.N;
     sd.domain = s.domain;
     sd.caller_index = ci;
-    sd.out_aligned = ((s.out_offset % 4) == 0 ? 1u : 0u) | ((s.out_offset % 8) == 0 ? 2u : 0u);
+    sd.out_aligned = ((s.out_offset % 4) == 0 ? 1u : 0u) | ((s.out_offset % 8) == 0 ? 2u : 0u) |
+                     ((s.out_offset % 32) == 0 ? 4u : 0u);
     sd.chunk_base = chunk;
     sd.n_chunks = (uint32_t)chunks_of(s.n_words);
     chunk += sd.n_chunks;
@@ -839,8 +849,8 @@ fptc_status fptc_plan_autotune(fptc_plan *p, const uint64_t *d_words, const uint
     uint32_t kernel, tile_samples, threads;
   };
   std::vector<Cand> cands;
-  for (uint32_t th : {128u, 256u, 512u, 1024u}) {
-    if (th == 1024) {
+  for (uint32_t th : {128u, 256u, 512u, 768u, 1024u}) {
+    if (th > 512) {
       if (keep.idct == FPTC_IDCT_FP32 && fixed && p->domains.size() <= kWarpMaxDomains)
         cands.push_back({FPTC_KERNEL_WARP_TILE, warp_tile_windows() * 32, th});
       continue;
