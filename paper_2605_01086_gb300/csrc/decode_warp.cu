@@ -35,25 +35,12 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
-#include "device_util.cuh"
+#include "warp_tile.cuh"
 
 namespace fptc {
 namespace {
 
-constexpr int kN = 32;
-constexpr int kE = 16;
-constexpr int kT = 128;                    // windows per tile
-constexpr int kTS = kT * kE;               // symbols per tile
-constexpr int kGuard = 64;                 // entries before and after the tile (a word holds <= 64 codewords)
-constexpr int kStage = kTS + 2 * kGuard;   // level bytes per warp
-constexpr int kZStride = 257;              // floats per zone row (zero levels of the zones in different banks)
-constexpr int kWPL = 2;                    // consecutive words per lane per decode pass
-constexpr int kPassWords = 32 * kWPL;
-constexpr int kStepWin = 32;               // windows per transform step (one per lane)
-constexpr int kOutTile = kStepWin * kN * 4;  // bytes of a step's output (TMA box 32 x 32 floats)
-constexpr int kMiscBytes = kPassWords * 8 + 32 + kStage;  // per warp: first-pass words, records, levels
-// zone mask of Table 1 (B1 = 2, B2 = 16): bins 0, 1 in zone 0, the rest in zone 1
-constexpr uint32_t kZmaskTable1 = 0x55555550u;
+using namespace wt;
 
 // ---- compile-time cosines of the inverse transform (N = 32, E = 16) ----------
 // cos(pi num / den) in double: Taylor series on [0, pi/2] after the reflections
@@ -134,26 +121,6 @@ __device__ __forceinline__ void idct32(const float (&c)[16], Put put) {
   }
 }
 
-// 32-byte streaming store (one full sector per thread)
-__device__ __forceinline__ void st_cs_v8(float *p, const float (&v)[8]) {
-  asm volatile("st.global.cs.v8.f32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(p), "f"(v[0]), "f"(v[1]),
-               "f"(v[2]), "f"(v[3]), "f"(v[4]), "f"(v[5]), "f"(v[6]), "f"(v[7])
-               : "memory");
-}
-
-// TMA tensor store of a staged 32 x 32-float tile to rows [row, row + 32) of
-// the output, and the waits on it (bulk async-group of the issuing thread).
-__device__ __forceinline__ void tma_store_rows(const CUtensorMap *map, const void *smem_tile, int32_t row) {
-  asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
-                   reinterpret_cast<uint64_t>(map)),
-               "r"(0), "r"(row), "r"(static_cast<uint32_t>(__cvta_generic_to_shared(smem_tile)))
-               : "memory");
-  asm volatile("cp.async.bulk.commit_group;" ::: "memory");
-}
-__device__ __forceinline__ void tma_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
-__device__ __forceinline__ void tma_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
-__device__ __forceinline__ void fence_async_shared() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-
 // A window whose output is not 32-byte aligned or that ends the segment
 // (m < 32 samples): 16-byte or scalar stores.  Kept out of line.
 __device__ __noinline__ void idct32_store_slow(const float (&c)[16], float *dst, uint32_t m, uint32_t vec16) {
@@ -171,173 +138,14 @@ __device__ __noinline__ void idct32_store_slow(const float (&c)[16], float *dst,
   }
 }
 
-struct DomW {
-  uint32_t lut_off;   // bytes from the start of shared memory: 16-bit entries len | level << 8
-  uint32_t deq_off;   // bytes: zone rows [3][kZStride] floats (row 2 zero)
-  uint32_t shift;     // 32 - lmax
-  uint32_t zmask;     // zone of bin k at bits 2k..2k+1
-  uint32_t complete;  // every prefix decodes (no zero entry)
-  uint32_t pad[3];
-};
-
-// Codewords of one SymLen word, MSB first.  w's bits sit in hi:lo with a marker
-// bit right under them (mk); each codeword shifts the 96 bits left by its
-// length (the entry's low 5 bits: the funnel shifts use the amount mod 32).
-// The marker leaves the buffer iff the codewords used more than 64 bits.
-// CHECKED (incomplete code): an entry of length 0 marks a prefix with no
-// codeword.  Returns error flags.
-template <bool CHECKED>
-__device__ __forceinline__ uint32_t decode_word(uint64_t w, uint32_t n, uint8_t *__restrict__ dst,
-                                                const uint16_t *__restrict__ lut, uint32_t shift) {
-  uint32_t hi = (uint32_t)(w >> 32), lo = (uint32_t)w, mk = 0x80000000u;
-  uint32_t low = 31u;
-  auto step = [&]() -> uint32_t {
-    const uint32_t e = lut[hi >> shift];
-    hi = __funnelshift_l(lo, hi, e);
-    lo = __funnelshift_l(mk, lo, e);
-    mk = __funnelshift_l(0u, mk, e);
-    if (CHECKED) low = min(low, e & 31u);
-    return e;
-  };
-  // levels go out two per 16-bit store where both are this word's
-  uint32_t j = 0;
-  if (n && (reinterpret_cast<uintptr_t>(dst) & 1u)) {
-    dst[0] = (uint8_t)(step() >> 8);
-    j = 1;
-  }
-  for (; j + 2 <= n; j += 2) {
-    const uint32_t e0 = step();
-    const uint32_t e1 = step();
-    *reinterpret_cast<uint16_t *>(dst + j) = (uint16_t)__byte_perm(e0, e1, 0x0051);
-  }
-  if (j < n) dst[j] = (uint8_t)(step() >> 8);
-  return ((hi | lo | mk) == 0u ? kFlagBitOverrun : 0u) | ((CHECKED && low == 0u) ? kFlagInvalidCode : 0u);
-}
-
-// Where a tile's words are (first word, count, codewords of the first word
-// that belong to the previous tile) and its segment.
-struct Ctx {
-  uint64_t fw;
-  uint32_t nw;
-  uint32_t skip;
-  uint32_t seg;
-  uint32_t ok;  // 0: segment flagged by the index, or no tile
-};
-
-__device__ __forceinline__ Ctx make_ctx(const DecodeParams &p, uint64_t g, uint32_t s, const TileRec &r,
-                                        const TileRec &rn) {
-  Ctx c{0, 0, 0, s, 0};
-  const SegDev &sg = p.segs[s];
-  if (p.seg_bad[s] != 0) return c;
-  const uint64_t tin = g - sg.tile_base;
-  c.fw = r.first_word;
-  c.skip = r.skip;
-  uint64_t lw;
-  if (tin + 1 < sg.n_tiles)
-    lw = rn.first_word - (rn.skip == 0 ? 1u : 0u);
-  else
-    lw = sg.word_offset + sg.n_words - 1;
-  c.nw = lw >= c.fw ? (uint32_t)(lw - c.fw + 1) : 0u;
-  c.ok = 1;
-  return c;
-}
-
-// Words i0 + kWPL lane + u (u < kWPL) of a tile (zero beyond its word count).
-__device__ __forceinline__ void load_pass(const DecodeParams &p, const Ctx &c, uint32_t i0, uint32_t lane,
-                                          uint64_t (&w)[kWPL], uint32_t (&n)[kWPL]) {
-#pragma unroll
-  for (int u = 0; u < kWPL; ++u) {
-    const uint32_t i = i0 + kWPL * lane + u;
-    const bool in = c.ok && i < c.nw;
-    w[u] = in ? __ldg(p.words + c.fw + i) : 0ull;
-    n[u] = in ? (uint32_t)__ldg(p.symlen + c.fw + i) : 0u;
-  }
-}
-
-__device__ __forceinline__ uint32_t smem_addr(const void *ptr) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(ptr));
-}
-
-// Asynchronous global -> shared copies (no register staging; completion by
-// cp.async.wait_all in the copying thread).
-__device__ __forceinline__ void cp_async8(void *dst, const void *src) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_addr(dst)), "l"(__cvta_generic_to_global(src))
-               : "memory");
-}
-__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(__cvta_generic_to_global(src))
-               : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
-
-// Records of tiles g and g + 1 into rec[0..1] (lanes 0 and 1).
-__device__ __forceinline__ void fetch_records(const DecodeParams &p, uint64_t g, uint32_t lane, TileRec *rec) {
-  if (lane < 2 && g + lane < p.tile_end) cp_async16(rec + lane, p.tiles + g + lane);
-  cp_async_commit();
-}
-
-// First pass of a tile: words kWPL lane + u into wbuf (copies), their symbol
-// counts packed one per byte into a register (zero beyond the tile's words).
-__device__ __forceinline__ uint32_t fetch_pass0(const DecodeParams &p, const Ctx &c, uint32_t lane, uint64_t *wbuf) {
-  uint32_t packed = 0;
-#pragma unroll
-  for (int u = 0; u < kWPL; ++u) {
-    const uint32_t i = kWPL * lane + u;
-    if (c.ok && i < c.nw) {
-      cp_async8(wbuf + i, p.words + c.fw + i);
-      packed |= (uint32_t)__ldg(p.symlen + c.fw + i) << (8 * u);
-    }
-  }
-  cp_async_commit();
-  return packed;
-}
-
 template <int WARPS>
 __global__ void __launch_bounds__(WARPS * 32, WARPS > 16 ? 1 : 32 / WARPS) k_decode_warp(
     const DecodeParams p, const WarpParams wp, const __grid_constant__ CUtensorMap out_map) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  DomW *const dw = reinterpret_cast<DomW *>(smem_raw);
+  const DomW *const dw = reinterpret_cast<const DomW *>(smem_raw);
   const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 
-  // ---- every domain's tables, once (offsets as in warp_smem_layout; computed
-  // here rather than indexed from the parameter block)
-  uint32_t off = (uint32_t)align16(sizeof(DomW) * (wp.n_domains ? wp.n_domains : 1));
-  for (uint32_t d = 0; d < wp.n_domains; ++d) {
-    const DomainDev &dm = p.domains[d];
-    const uint32_t lut_off = off;
-    const uint32_t deq_off = lut_off + (uint32_t)align16((size_t)2 << dm.lmax);
-    off = deq_off + (uint32_t)align16(3u * kZStride * 4);
-    if (threadIdx.x == 0) {
-      DomW x;
-      x.lut_off = lut_off;
-      x.deq_off = deq_off;
-      x.shift = 32u - dm.lmax;
-      uint32_t zm = 0;
-      for (uint32_t k = 0; k < kE; ++k) zm |= (k < dm.B1 ? 0u : (k < dm.B2 ? 1u : 2u)) << (2 * k);
-      x.zmask = zm;
-      x.complete = dm.complete;
-      x.pad[0] = x.pad[1] = x.pad[2] = 0;
-      dw[d] = x;
-    }
-    // entries level | len << 8 -> len | level << 8 (the length in the low bits feeds the shifts)
-    uint16_t *lut = reinterpret_cast<uint16_t *>(smem_raw + lut_off);
-    const uint16_t *g_lut = p.luts + dm.lut_offset;
-    const uint32_t entries = 1u << dm.lmax;
-    for (uint32_t i = threadIdx.x; i < entries; i += WARPS * 32) {
-      const uint32_t v = __ldg(g_lut + i);
-      lut[i] = (uint16_t)((v >> 8) | ((v & 0xffu) << 8));
-    }
-    float a0 = p.scale ? p.scale[d * 3 + 0] : dm.scale[0];
-    float a1 = p.scale ? p.scale[d * 3 + 1] : dm.scale[1];
-    a0 = a0 > 1e-30f ? a0 : 0.0f;
-    a1 = a1 > 1e-30f ? a1 : 0.0f;
-    float *deq = reinterpret_cast<float *>(smem_raw + deq_off);
-    for (uint32_t i = threadIdx.x; i < 3u * kZStride; i += WARPS * 32) {
-      const uint32_t z = i / kZStride, L = i - z * kZStride;
-      deq[i] = (L < 256u && z < 2u) ? (z == 0 ? a0 : a1) * dm.unit[z][L] : 0.0f;
-    }
-  }
+  load_domain_tables<WARPS * 32>(p, wp.n_domains, smem_raw);
   __syncthreads();
 
   unsigned char *const wbase = smem_raw + wp.warp_off + warp * kMiscBytes;
@@ -352,11 +160,8 @@ __global__ void __launch_bounds__(WARPS * 32, WARPS > 16 ? 1 : 32 / WARPS) k_dec
   bool tma_pending = false;
 
   // ---- this warp's tiles: an even split of the launch's tile range over all warps
-  const uint64_t n_all = p.tile_end - p.tile_begin;
-  const uint64_t nwarps = (uint64_t)gridDim.x * WARPS;
-  const uint64_t gw = (uint64_t)blockIdx.x * WARPS + warp;
-  const uint64_t tw0 = p.tile_begin + n_all * gw / nwarps;
-  const uint64_t tw1 = p.tile_begin + n_all * (gw + 1) / nwarps;
+  uint64_t tw0, tw1;
+  unit_tiles(p, (uint64_t)blockIdx.x * WARPS + warp, (uint64_t)gridDim.x * WARPS, tw0, tw1);
   if (tw0 >= tw1) return;
 
   // prologue: records of tw0, then its first words
@@ -384,61 +189,14 @@ __global__ void __launch_bounds__(WARPS * 32, WARPS > 16 ? 1 : 32 / WARPS) k_dec
     if (g1 < tw1) fetch_records(p, g1, lane, rec);  // consumed after the decode
 
     const SegDev &sg = p.segs[cur.seg];
-    const uint32_t dom = sg.domain;
-    const DomW dd = dw[dom];
+    const DomW dd = dw[sg.domain];
     const uint64_t win0 = (g - sg.tile_base) * kT;
     const uint64_t left = sg.n_windows - win0;
     const uint32_t nwin = left < (uint64_t)kT ? (uint32_t)left : (uint32_t)kT;
 
-    // ---- 1. SymLen decode into the staging entries
+    // ---- 1. SymLen decode into the level bytes
     if (cur.ok) {
-      const uint16_t *lut = reinterpret_cast<const uint16_t *>(smem_raw + dd.lut_off);
-      int32_t base = -(int32_t)cur.skip;
-      uint32_t bad = 0;
-      for (uint32_t c0 = 0; c0 < cur.nw; c0 += kPassWords) {
-        uint64_t xw[kWPL];
-        uint32_t xn[kWPL];
-        if (c0 + kPassWords < cur.nw) {
-          load_pass(p, cur, c0 + kPassWords, lane, xw, xn);
-        } else {
-#pragma unroll
-          for (int u = 0; u < kWPL; ++u) {
-            xw[u] = 0;
-            xn[u] = 0;
-          }
-        }
-        uint32_t tot = 0;
-#pragma unroll
-        for (int u = 0; u < kWPL; ++u) tot += n[u];
-        uint32_t x = tot;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-          if (lane >= (uint32_t)o) x += y;
-        }
-        const uint32_t total = __shfl_sync(0xffffffffu, x, 31);
-        uint8_t *dst = stage + base + (int32_t)(x - tot);
-        if (dd.complete) {
-#pragma unroll
-          for (int u = 0; u < kWPL; ++u) {
-            bad |= decode_word<false>(w[u], n[u], dst, lut, dd.shift);
-            dst += n[u];
-          }
-        } else {
-#pragma unroll
-          for (int u = 0; u < kWPL; ++u) {
-            bad |= decode_word<true>(w[u], n[u], dst, lut, dd.shift);
-            dst += n[u];
-          }
-        }
-        base += (int32_t)total;
-#pragma unroll
-        for (int u = 0; u < kWPL; ++u) {
-          w[u] = xw[u];
-          n[u] = xn[u];
-        }
-      }
-      bad = __reduce_or_sync(0xffffffffu, bad);
+      const uint32_t bad = decode_tile(p, cur, dd, smem_raw, stage, lane, w, n);
       if (bad && lane == 0) flag_bad(p.status, bad, sg.caller_index);
     }
 
@@ -455,7 +213,6 @@ __global__ void __launch_bounds__(WARPS * 32, WARPS > 16 ? 1 : 32 / WARPS) k_dec
     // ---- 2./3. dequantization + inverse transform + reassembly, one window per lane
     if (cur.ok) {
       const float *deq = reinterpret_cast<const float *>(smem_raw + dd.deq_off);
-      const bool table1 = dd.zmask == kZmaskTable1;  // bins 0, 1 in zone 0, bins 2..15 in zone 1
       float *const out = p.out + sg.out_offset;
       const uint64_t S = sg.n_samples;
       const uint32_t aligned = sg.out_aligned;
@@ -464,35 +221,19 @@ __global__ void __launch_bounds__(WARPS * 32, WARPS > 16 ? 1 : 32 / WARPS) k_dec
       uint8_t *const lev = want_lev ? p.levels + sg.level_offset + win0 * kE : nullptr;
 #pragma unroll 1
       for (uint32_t w0 = 0; w0 < nwin; w0 += kStepWin) {
-        const uint32_t w = w0 + lane;
+        const uint32_t wi = w0 + lane;
         // all 32 windows of the step whole and inside the segment: one TMA store
         const bool tma_step = tma_seg && w0 + kStepWin <= nwin && (win0 + w0 + kStepWin) * kN <= S;
         if (tma_step && tma_pending) {
           if (lane == 0) tma_wait_read();  // the previous tile has left the staging buffer
           __syncwarp();
         }
-        if (w < nwin) {
-          const uint4 sv = *reinterpret_cast<const uint4 *>(stage + w * kE);
-          const uint32_t sw[4] = {sv.x, sv.y, sv.z, sv.w};
+        if (wi < nwin) {
+          const uint4 sv = *reinterpret_cast<const uint4 *>(stage + wi * kE);
           float c[16];
-          if (table1) {
-#pragma unroll
-            for (int k = 0; k < 16; ++k) c[k] = deq[(k < 2 ? 0 : kZStride) + ((sw[k >> 2] >> (8 * (k & 3))) & 0xffu)];
-          } else {
-#pragma unroll
-            for (int k = 0; k < 16; ++k)
-              c[k] = deq[((dd.zmask >> (2 * k)) & 3u) * kZStride + ((sw[k >> 2] >> (8 * (k & 3))) & 0xffu)];
-          }
-          if (want_lev) {
-            uint8_t *dl = lev + w * kE;
-            if ((reinterpret_cast<uintptr_t>(dl) & 15u) == 0) {
-              *reinterpret_cast<uint4 *>(dl) = sv;
-            } else {
-#pragma unroll
-              for (int j = 0; j < 16; ++j) dl[j] = (uint8_t)(sw[j >> 2] >> (8 * (j & 3)));
-            }
-          }
-          const uint64_t s0 = (win0 + w) * kN;
+          window_coefs(sv, deq, dd.zmask, c);
+          if (want_lev) put_levels(lev + wi * kE, sv);
+          const uint64_t s0 = (win0 + wi) * kN;
           float *const dst = out + s0;
           if (tma_step) {
             // row `lane` of the staging tile, 16-byte chunk c at c ^ (lane & 7)
@@ -516,7 +257,7 @@ __global__ void __launch_bounds__(WARPS * 32, WARPS > 16 ? 1 : 32 / WARPS) k_dec
         }
       }
     }
-    __syncwarp();  // the staging entries are rewritten by the next tile
+    __syncwarp();  // the level bytes are rewritten by the next tile
   }
   if (tma_pending && lane == 0) tma_wait_all();
 }

@@ -117,17 +117,15 @@ struct WarpParams {
   uint32_t tab_off[kWarpMaxDomains];  // bytes
 };
 
-// Shared-memory layout of the tensor-core kernel (decode_tc.cu), bytes.
+// Shared-memory layout of the tensor-core kernel (decode_tc.cu), bytes; the
+// tables and per-warp buffers are laid out as for the warp-tile kernel.
 struct TcParams {
-  uint32_t a_off, a_bytes;        // per-warpgroup A operands (two buffers)
-  uint32_t a_buf;                 // bytes of one A buffer
-  uint32_t b_off;                 // B operands
-  uint32_t coef_off, coef_bytes;  // per-warp coefficient buffers
-  uint32_t misc_off;              // mbarriers, tensor-memory address
-  uint32_t dom_off;               // per-domain descriptors
-  uint32_t tab_first;             // first per-domain table
-  uint32_t n_domains;
-  uint32_t pad[2];
+  uint32_t a_off;      // per-warpgroup A operands (two buffers of a_buf bytes each)
+  uint32_t a_buf;
+  uint32_t b_off;      // B operand(s)
+  uint32_t misc_off;   // mbarriers [warpgroups][2], tensor-memory address
+  uint32_t tiles_off;  // output staging tiles start at the next 1024-byte boundary
+  uint32_t pad[3];
 };
 
 struct BackwardParams {
@@ -168,12 +166,13 @@ bool encode_out_map(CUtensorMap *map, float *out, uint64_t extent);
 
 // tensor-core kernel for N = 32, E = 16 (decode_tc.cu); mode = fptc_idct (not FP32)
 uint32_t tc_tile_windows();
-size_t tc_smem_layout(uint32_t mode, uint32_t threads, const uint32_t *lmax, uint32_t n_domains, TcParams *tp);
+size_t tc_smem_layout(uint32_t mode, uint32_t threads, const uint32_t *lmax, uint32_t n_domains, WarpParams *wp,
+                      TcParams *tp);
 cudaError_t tc_smem_config(uint32_t mode, uint32_t threads, size_t smem);
 cudaError_t tc_occupancy(uint32_t mode, uint32_t threads, size_t smem, int *ctas_per_sm);
 cudaError_t tc_attributes(uint32_t mode, uint32_t threads, cudaFuncAttributes *attr);
-cudaError_t launch_tc(const DecodeParams &p, const TcParams &tp, uint32_t mode, uint32_t threads, uint32_t grid,
-                      size_t smem, cudaStream_t stream);
+cudaError_t launch_tc(const DecodeParams &p, const WarpParams &wp, const TcParams &tp, const CUtensorMap &out_map,
+                      uint32_t mode, uint32_t threads, uint32_t grid, size_t smem, cudaStream_t stream);
 
 cudaError_t launch_backward(const BackwardParams &p, uint32_t threads, uint32_t grid, size_t smem,
                             cudaStream_t stream);

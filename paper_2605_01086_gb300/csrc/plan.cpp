@@ -154,9 +154,11 @@ fptc_status configure_launch(fptc_plan *p) {
       }
   }
   const bool t_ok = threads == 128 || threads == 256 || threads == 512 ||
-                    ((threads == 768 || threads == 1024) && p->kind == FPTC_KERNEL_WARP_TILE);
+                    ((threads == 768 || threads == 1024) && p->kind == FPTC_KERNEL_WARP_TILE) ||
+                    (threads == 384 && p->kind == FPTC_KERNEL_TENSOR);
   if (!t_ok) {
-    set_error("threads must be 128, 256 or 512 (768 and 1024 also for the warp-tile kernel; got %u)", threads);
+    set_error("threads must be 128, 256 or 512 (768 and 1024 also for the warp-tile kernel, 384 for the "
+              "tensor-core kernel; got %u)", threads);
     return FPTC_ERR_INVALID_ARGUMENT;
   }
   p->threads = threads;
@@ -170,7 +172,22 @@ fptc_status configure_launch(fptc_plan *p) {
   } else if (p->kind == FPTC_KERNEL_TENSOR) {
     std::vector<uint32_t> lm;
     for (const auto &d : p->domains) lm.push_back(d.lmax);
-    p->smem = tc_smem_layout(p->opts.idct, threads, lm.data(), (uint32_t)lm.size(), &p->tp);
+    if (p->opts.threads == 0) {
+      // as many warpgroups as one CTA's shared memory allows (4 at most)
+      int dev = 0, optin = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+      WarpParams pw{};
+      TcParams pt{};
+      threads = 128;
+      for (uint32_t t : {512u, 384u, 256u})
+        if (tc_smem_layout(p->opts.idct, t, lm.data(), (uint32_t)lm.size(), &pw, &pt) <= (size_t)optin) {
+          threads = t;
+          break;
+        }
+      p->threads = threads;
+    }
+    p->smem = tc_smem_layout(p->opts.idct, threads, lm.data(), (uint32_t)lm.size(), &p->wp, &p->tp);
     e = tc_smem_config(p->opts.idct, threads, p->smem);
     if (e != cudaSuccess) return cuda_fail(e, "decode shared-memory size");
     e = tc_occupancy(p->opts.idct, threads, p->smem, &occ);
@@ -205,7 +222,7 @@ fptc_status configure_launch(fptc_plan *p) {
   const uint64_t full = (uint64_t)p->sm_count * p->ctas_per_sm;
   p->grid = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(full, p->n_tiles));
   // backward
-  p->b_threads = threads > 512 ? 256u : threads;
+  p->b_threads = (threads == 128 || threads == 256 || threads == 512) ? threads : 256u;  // backward variants
   p->b_smem = backward_smem_bytes(p->b_threads, p->lut_cap, p->coef_cap, p->gx_cap, p->basis_cap);
   e = backward_smem_config(p->b_threads, p->b_smem);
   if (e != cudaSuccess) return cuda_fail(e, "backward shared-memory size");
@@ -316,7 +333,13 @@ cudaError_t run_range(const fptc_plan *p, const IndexParams &ip0, const DecodePa
     wp.out_tma = encode_out_map(&map, dp.out, p->out_extent) ? 1u : 0u;
     return launch_warp(dp, wp, map, p->threads, grid, p->smem, st);
   }
-  if (p->kind == FPTC_KERNEL_TENSOR) return launch_tc(dp, p->tp, p->opts.idct, p->threads, grid, p->smem, st);
+  if (p->kind == FPTC_KERNEL_TENSOR) {
+    WarpParams wp = p->wp;
+    CUtensorMap map;
+    std::memset(&map, 0, sizeof(map));
+    wp.out_tma = encode_out_map(&map, dp.out, p->out_extent) ? 1u : 0u;
+    return launch_tc(dp, wp, p->tp, map, p->opts.idct, p->threads, grid, p->smem, st);
+  }
   return launch_decode(dp, p->kind, p->threads, grid, p->smem, st);
 }
 
