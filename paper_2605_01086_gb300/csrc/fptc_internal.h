@@ -174,6 +174,12 @@ cudaError_t tc_attributes(uint32_t mode, uint32_t threads, cudaFuncAttributes *a
 cudaError_t launch_tc(const DecodeParams &p, const WarpParams &wp, const TcParams &tp, const CUtensorMap &out_map,
                       uint32_t mode, uint32_t threads, uint32_t grid, size_t smem, cudaStream_t stream);
 
+// adjoint for N = 32, E = 16 plans on the warp-tile machinery (backward_warp.cu)
+size_t backward_warp_smem_layout(uint32_t threads, const uint32_t *lmax, uint32_t n_domains, WarpParams *wp);
+cudaError_t backward_warp_smem_config(uint32_t threads, size_t smem);
+cudaError_t launch_backward_warp(const BackwardParams &p, const WarpParams &wp, const CUtensorMap &gx_map,
+                                 uint32_t threads, uint32_t grid, size_t smem, cudaStream_t stream);
+
 cudaError_t launch_backward(const BackwardParams &p, uint32_t threads, uint32_t grid, size_t smem,
                             cudaStream_t stream);
 size_t backward_smem_bytes(uint32_t threads, uint32_t lut_cap, uint32_t coef_cap, uint32_t gx_cap,

@@ -52,6 +52,8 @@ struct fptc_plan {
   uint32_t lut_cap = 0, coef_cap = 0, gx_cap = 0, basis_cap = 0;
   uint32_t b_threads = 256, b_grid = 0;
   size_t b_smem = 0;
+  bool b_warp = false;    // backward on the warp-tile adjoint kernel
+  WarpParams b_wp{};
   cudaStream_t aux = nullptr;
   cudaEvent_t ev[2] = {nullptr, nullptr};
 };
@@ -222,6 +224,27 @@ fptc_status configure_launch(fptc_plan *p) {
   const uint64_t full = (uint64_t)p->sm_count * p->ctas_per_sm;
   p->grid = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(full, p->n_tiles));
   // backward
+  if (p->kind == FPTC_KERNEL_WARP_TILE || p->kind == FPTC_KERNEL_TENSOR) {
+    // the warp-tile adjoint: 16 warps if their buffers fit, else 8
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    std::vector<uint32_t> lm;
+    for (const auto &d : p->domains) lm.push_back(d.lmax);
+    p->b_warp = false;
+    for (uint32_t t : {512u, 256u}) {
+      const size_t need = backward_warp_smem_layout(t, lm.data(), (uint32_t)lm.size(), &p->b_wp);
+      if (need <= (size_t)optin) {
+        e = backward_warp_smem_config(t, need);
+        if (e != cudaSuccess) return cuda_fail(e, "backward shared-memory size");
+        p->b_warp = true;
+        p->b_threads = t;
+        p->b_smem = need;
+        p->b_grid = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>((uint64_t)p->sm_count, p->n_tiles));
+        return FPTC_OK;
+      }
+    }
+  }
   p->b_threads = (threads == 128 || threads == 256 || threads == 512) ? threads : 256u;  // backward variants
   p->b_smem = backward_smem_bytes(p->b_threads, p->lut_cap, p->coef_cap, p->gx_cap, p->basis_cap);
   e = backward_smem_config(p->b_threads, p->b_smem);
@@ -772,7 +795,15 @@ fptc_status fptc_decode_backward(fptc_plan *p, const uint64_t *d_words, const ui
   bp.grad_scale = d_grad_scale;
   bp.gx_cap = p->gx_cap;
   bp.basis_cap = p->basis_cap;
-  e = launch_backward(bp, p->b_threads, p->b_grid, p->b_smem, s);
+  if (p->b_warp) {
+    WarpParams wp = p->b_wp;
+    CUtensorMap map;
+    std::memset(&map, 0, sizeof(map));
+    wp.out_tma = encode_out_map(&map, const_cast<float *>(d_grad_out), p->out_extent) ? 1u : 0u;
+    e = launch_backward_warp(bp, wp, map, p->b_threads, p->b_grid, p->b_smem, s);
+  } else {
+    e = launch_backward(bp, p->b_threads, p->b_grid, p->b_smem, s);
+  }
   if (e != cudaSuccess) return cuda_fail(e, "backward launch");
   return FPTC_OK;
 }
