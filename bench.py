@@ -269,7 +269,8 @@ def run(args):
     in_bytes = 9 * int(batch.segments["n_words"].sum())
 
     t0 = time.perf_counter()
-    plan = Plan(doms, batch.segments, device=local, kernel=args.kernel or "auto", threads=args.threads)
+    plan = Plan(doms, batch.segments, device=local, kernel=args.kernel or "auto", threads=args.threads,
+                idct=args.idct)
     if args.kernel:
         args.no_autotune = True
     t_plan = time.perf_counter() - t0
@@ -348,7 +349,7 @@ def run(args):
     peak, peak_kind = measured_peaks()
     dec_avg = statistics.mean(dec_ms)
     kernel_names = {1: "k_decode (generic)", 2: "k_decode_fixed (block tile)", 3: "k_decode_warp (warp tile)",
-                    4: "k_decode_tc (tensor core)"}
+                    4: "k_decode_tc (tensor core, %s)" % args.idct}
     kname = kernel_names.get(plan.info["kernel"], "?")
     traffic = args.traffic if args.traffic is not None else measured_traffic(plan.info["kernel"], n_samples)
     achieved = (out_bytes + in_bytes) / (dec_avg / 1e3) / 1e9
@@ -359,7 +360,8 @@ def run(args):
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "vs_baseline": None, "dtype": "f32" if args.idct == "fp32" else "f32 (%s products)" % args.idct,
+            "data": "synthetic",
             "config": {"workload": wl.name, "n_streams": wl.n_streams, "n_samples": n_samples,
                        "out_bytes": out_bytes, "compressed_bytes": in_bytes, "params": PARAMS,
                        "domains": "eeg,seismic,power,met", "schedule": "persistent, CUDA graph",
@@ -372,6 +374,7 @@ def run(args):
             "prd_percent_sample": prd}
 
     # tensor-core forms of the inverse transform on the same streams: throughput
+    # (index + decode per step, and the decode kernel alone against the roofline)
     # and relative L2 distance to the FP32 output (the FP64 comparison is in the tests)
     if not args.no_forms and rank == 0:
         forms = {}
@@ -383,15 +386,51 @@ def run(args):
                 fplan.autotune(w, s, out3, trials=2, stream=stream)
                 fplan.decode(w, s, out=out3, stream=stream)
                 fms = time_steps(lambda: fplan.decode(w, s, out=out3, stream=stream), 5, stream, torch)
+                kms = time_steps(lambda: fplan.decode_stages(w, s, out3, STAGE_DECODE, stream=stream), 5, stream,
+                                 torch)
             torch.cuda.synchronize()
             rel = float(torch.linalg.vector_norm((out3 - ref).double()) / torch.linalg.vector_norm(ref.double()))
+            ka = (out_bytes + in_bytes) / (statistics.median(kms) / 1e3) / 1e9
             forms[idct] = {"value": out_bytes / (statistics.median(fms) / 1e3) / 1e9, "unit": UNIT,
                            "ms_per_step": statistics.median(fms), "rel_l2_vs_fp32": rel,
-                           "threads": fplan.info["threads"]}
+                           "threads": fplan.info["threads"],
+                           "roofline": {"bound": "hbm", "achieved": ka, "peak": peak, "unit": "GB/s",
+                                        "frac": ka / peak, "launch_ms": statistics.median(kms),
+                                        "kernel": "k_decode_tc (tcgen05)"}}
             fplan.close()
             del out3
         line["forms"] = forms
         del ref
+
+    # differentiable form: forward keeping the levels, then the hand-written
+    # adjoint (dL/dA_z with an FP64 reduction, and dL/dC for every coefficient)
+    # for dL/dx = x_hat - x0 with x0 = 0 (the decoded samples themselves)
+    if not args.no_forms and rank == 0:
+        n_lev = plan.info["n_levels_total"]
+        lv = torch.empty(max(1, n_lev), dtype=torch.uint8, device=dev)
+        gco = torch.empty(max(1, n_lev), dtype=torch.float32, device=dev)
+        sc = torch.tensor([[float(x) for x in d.scale] for d in doms], dtype=torch.float32, device=dev)
+        with torch.cuda.stream(stream):
+            plan.decode(w, s, out=out, levels=lv, scale=sc, stream=stream)
+            fw = time_steps(lambda: plan.decode(w, s, out=out, levels=lv, scale=sc, stream=stream), 5, stream,
+                            torch)
+            plan.backward(out, levels=lv, scale=sc, grad_coeffs=gco, stream=stream)
+            bw = time_steps(lambda: plan.backward(out, levels=lv, scale=sc, grad_coeffs=gco, stream=stream), 5,
+                            stream, torch)
+        torch.cuda.synchronize()
+        gsc, _ = plan.backward(out, levels=lv, scale=sc, grad_coeffs=gco, stream=stream)
+        torch.cuda.synchronize()
+        fwd_ms, bwd_ms = statistics.median(fw), statistics.median(bw)
+        # adjoint bytes: dL/dx read (4 B / sample), levels read (1 B / coefficient), dL/dC written (4 B / coefficient)
+        b_bytes = 4 * n_samples + 5 * n_lev
+        line["differentiable"] = {
+            "forward_ms": fwd_ms, "backward_ms": bwd_ms,
+            "value": out_bytes / ((fwd_ms + bwd_ms) / 1e3) / 1e9, "unit": UNIT,
+            "grad_scale_finite": bool(torch.isfinite(gsc).all()),
+            "roofline": {"bound": "hbm", "achieved": b_bytes / (bwd_ms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
+                         "frac": b_bytes / (bwd_ms / 1e3) / 1e9 / peak, "algorithmic_bytes_per_launch": b_bytes,
+                         "kernel": "k_backward_warp (adjoint)"}}
+        del lv, gco, sc
 
     # plain baseline: one set of launches per stream, same streams, same output
     if not args.no_plain and rank == 0:
@@ -466,6 +505,8 @@ def main():
     ap.add_argument("--no-forms", action="store_true")
     ap.add_argument("--kernel", default=None, help="fix the decode kernel (no autotuning): warp_tile, block_tile, generic")
     ap.add_argument("--threads", type=int, default=0)
+    ap.add_argument("--idct", default="fp32", choices=["fp32", "tf32", "bf16x3", "tf32x3"],
+                    help="inverse-transform form of the timed plan (tensor-core forms use the tcgen05 kernel)")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
