@@ -54,8 +54,10 @@ struct fptc_plan {
   size_t b_smem = 0;
   bool b_warp = false;    // backward on the warp-tile adjoint kernel
   WarpParams b_wp{};
-  cudaStream_t aux = nullptr;
-  cudaEvent_t ev[2] = {nullptr, nullptr};
+  static constexpr int kAux = 4;        // copy-back streams of the end-to-end decode
+  static constexpr int kPieces = 16;    // decode pieces of the end-to-end decode
+  cudaStream_t aux[kAux] = {};
+  cudaEvent_t ev[kPieces] = {};
 };
 
 namespace {
@@ -97,7 +99,8 @@ void free_device(fptc_plan *p) {
   cudaFree(p->d_seg_bad);
   cudaFree(p->d_tiles);
   cudaFree(p->d_status);
-  if (p->aux) cudaStreamDestroy(p->aux);
+  for (auto &a : p->aux)
+    if (a) cudaStreamDestroy(a);
   for (auto &e : p->ev)
     if (e) cudaEventDestroy(e);
 }
@@ -657,9 +660,11 @@ fptc_status fptc_plan_create(fptc_plan **out, int device, const fptc_domain *dom
     if (st == FPTC_OK) st = upload_layout(p);
     if (st == FPTC_OK) st = configure_launch(p);
     if (st == FPTC_OK) {
-      if ((e = cudaStreamCreateWithFlags(&p->aux, cudaStreamNonBlocking)) != cudaSuccess ||
-          (e = cudaEventCreateWithFlags(&p->ev[0], cudaEventDisableTiming)) != cudaSuccess ||
-          (e = cudaEventCreateWithFlags(&p->ev[1], cudaEventDisableTiming)) != cudaSuccess)
+      for (auto &a : p->aux)
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&a, cudaStreamNonBlocking);
+      for (auto &v : p->ev)
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&v, cudaEventDisableTiming);
+      if (e != cudaSuccess)
         st = cuda_fail(e, "plan streams");
     }
     if (st != FPTC_OK) {
@@ -835,9 +840,10 @@ fptc_status fptc_decode_host(fptc_plan *p, const uint64_t *h_words, const uint8_
   const DecodeParams dp = decode_params(p, d_words, d_symlen, d_out, nullptr, nullptr);
   e = launch_index(ip, s);
   if (e != cudaSuccess) return cuda_fail(e, "index launch");
-  // decode in pieces of about equal output, copy each piece back while the next one decodes
+  // decode in pieces of about equal output; each piece is copied back on one of
+  // several streams (several copy engines) while the next pieces decode
   const uint32_t n = (uint32_t)p->segs.size();
-  const uint32_t pieces = std::min<uint32_t>(8u, n);
+  const uint32_t pieces = std::min<uint32_t>((uint32_t)fptc_plan::kPieces, n);
   const uint64_t per = (p->n_samples + pieces - 1) / pieces;
   uint32_t s0 = 0;
   int k = 0;
@@ -845,20 +851,22 @@ fptc_status fptc_decode_host(fptc_plan *p, const uint64_t *h_words, const uint8_
     uint32_t s1 = s0;
     uint64_t acc = 0;
     while (s1 < n && (acc < per || s1 == s0)) acc += p->segs[s1++].n_samples;
+    if (k == fptc_plan::kPieces - 1) s1 = n;  // the last piece takes the rest
     e = run_range(p, ip, dp, s0, s1, false, s);
     if (e != cudaSuccess) break;
     const uint64_t o0 = p->segs[s0].out_offset;
     uint64_t o1 = o0;
     for (uint32_t i = s0; i < s1; ++i) o1 = std::max(o1, p->segs[i].out_offset + p->segs[i].n_samples);
-    cudaEvent_t ev = p->ev[k & 1];
+    cudaEvent_t ev = p->ev[k];
+    cudaStream_t a = p->aux[k % fptc_plan::kAux];
     if ((e = cudaEventRecord(ev, s)) != cudaSuccess) break;
-    if ((e = cudaStreamWaitEvent(p->aux, ev, 0)) != cudaSuccess) break;
-    if (o1 > o0) e = cudaMemcpyAsync(h_out + o0, d_out + o0, (o1 - o0) * 4, cudaMemcpyDeviceToHost, p->aux);
-    // the next piece may reuse this event only after the copy above was queued
+    if ((e = cudaStreamWaitEvent(a, ev, 0)) != cudaSuccess) break;
+    if (o1 > o0) e = cudaMemcpyAsync(h_out + o0, d_out + o0, (o1 - o0) * 4, cudaMemcpyDeviceToHost, a);
     s0 = s1;
     ++k;
   }
-  if (e == cudaSuccess) e = cudaStreamSynchronize(p->aux);
+  for (auto &a : p->aux)
+    if (e == cudaSuccess) e = cudaStreamSynchronize(a);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(e, "end-to-end decode");
   return FPTC_OK;

@@ -295,3 +295,26 @@ def test_graph_capture_replay():
     g.replay()
     torch.cuda.synchronize()
     compare_with_oracle(plan, b, out, lv)
+
+
+@pytest.mark.parametrize("idct", ["fp32", "bf16x3"])
+def test_decode_host_buffers(idct):
+    """fptc_decode_host: compressed streams from pinned host memory, samples back
+    to host memory (pieces copied back on several streams while later pieces
+    decode); equal to the device-buffer decode and within the oracle bound."""
+    wl = siggen.mixed_10000_logu(n=60, lo=1, hi=300000)
+    b = encode_workload(wl)
+    plan = make_plan(b, idct=idct, out_align=32)
+    w, s, out, lv = gpu_decode(plan, b)
+    h_w = torch.from_numpy(b.words.view(np.int64)).pin_memory()
+    h_s = torch.from_numpy(b.symlen).pin_memory()
+    h_o = torch.full((plan.info["out_extent"],), float("nan"), dtype=torch.float32).pin_memory()
+    d_w, d_s = torch.zeros_like(w), torch.zeros_like(s)
+    d_o = torch.zeros_like(out)
+    plan.decode_host(h_w, h_s, h_o, d_w, d_s, d_o)
+    assert plan.device_status()[0] == 0
+    ref = out.cpu()
+    for seg in plan.segments:
+        o, n = int(seg["out_offset"]), int(seg["n_samples"])
+        assert torch.equal(h_o[o:o + n], ref[o:o + n])
+    compare_with_oracle(plan, b, h_o, None, tol=FP32_REL_L2 if idct == "fp32" else 2e-5)
