@@ -8,11 +8,14 @@
 // with B[k][n] = cos(pi/N (n + 1/2) k) (B[0][n] = 1/2), one product per
 // transform step of a warpgroup: its four warps each contribute 32 windows
 // (one step of their own current tile) as rows 32 q .. 32 q + 31 of the A
-// operand, one thread issues tcgen05.mma (M = 128, N = 32) with A and B in
-// shared memory and D in tensor memory, tcgen05.commit signals an mbarrier,
-// and warp q reads rows 32 q .. 32 q + 31 of D with tcgen05.ld 32x32b (lane i
-// = one window: the layout the TMA output staging expects).  The readback of
-// step k overlaps the product of step k + 1 (two A and two D buffers).
+// operand, which lane i of warp q writes straight into tensor-memory lane
+// 32 q + i (tcgen05.st: no shared-memory operand, so 24 warps fit); one thread
+// issues tcgen05.mma (M = 128, N = 32) with A and D in tensor memory and B in
+// shared memory, tcgen05.commit signals an mbarrier, and warp q reads rows
+// 32 q .. 32 q + 31 of D with tcgen05.ld 32x32b (lane i = one window: the
+// layout the TMA output staging expects).  The A rows of step k + 1 are
+// written while product k runs (two A buffers); D is read back before the
+// next product is issued.
 //
 // Precision forms (the integer decode is exact in every form):
 //   TF32    one product, operands rounded to TF32 (10-bit mantissa);
@@ -21,10 +24,11 @@
 //   BF16X3  the same split with BF16 halves, C_hi B_hi + C_lo B_hi + C_hi B_lo.
 // All accumulate in FP32.
 //
-// Operand layout: K-major, no swizzle.  A core matrix is 8 rows x 16 bytes
-// stored contiguously; LBO = byte distance between core matrices adjacent in K,
-// SBO = between core matrices adjacent in M (or N).  A kernel that uses tensor
-// memory runs one CTA per SM.  Every wait on an mbarrier is bounded; on
+// Operands: A in tensor memory, one row per lane, K packed along 32-bit
+// columns (two BF16 or one TF32 per column).  B in shared memory, K-major, no
+// swizzle: a core matrix is 8 rows x 16 bytes stored contiguously; LBO = byte
+// distance between core matrices adjacent in K, SBO = between core matrices
+// adjacent in N.  A kernel that uses tensor memory runs one CTA per SM.  Every wait on an mbarrier is bounded; on
 // expiry the kernel flags FPTC_FLAG_TIMEOUT and the warpgroup stops.
 #include <cuda_bf16.h>
 
@@ -54,13 +58,15 @@ __device__ __forceinline__ bool bar_any_c(bool v) {
   return r != 0;
 }
 
-// Barrier over the 128 threads of warpgroup wg (ids 1..4), returning the OR of v.
+// Barrier over the 128 threads of warpgroup wg (ids 1..6), returning the OR of v.
 __device__ __forceinline__ bool wg_barrier_any(uint32_t wg, bool v) {
   switch (wg) {
     case 0: return bar_any_c<1>(v);
     case 1: return bar_any_c<2>(v);
     case 2: return bar_any_c<3>(v);
-    default: return bar_any_c<4>(v);
+    case 3: return bar_any_c<4>(v);
+    case 4: return bar_any_c<5>(v);
+    default: return bar_any_c<6>(v);
   }
 }
 
@@ -95,21 +101,39 @@ __host__ __device__ constexpr uint32_t instr_desc(uint32_t ab_format, uint32_t m
 }
 constexpr uint32_t kFmtBF16 = 1, kFmtTF32 = 2;
 
-__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint32_t a_tmem, uint64_t b, uint32_t idesc,
+                                         uint32_t acc) {
   asm volatile(
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
-      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      " tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "r"(a_tmem), "l"(b), "r"(idesc), "r"(acc)
       : "memory");
 }
 
-__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint32_t a_tmem, uint64_t b, uint32_t idesc, uint32_t acc) {
   asm volatile(
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
-      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "r"(a_tmem), "l"(b), "r"(idesc), "r"(acc)
       : "memory");
 }
+
+// Thread i of the warp writes 8 or 16 consecutive 32-bit columns of lane
+// (taddr lane) + i.
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t (&r)[8]) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(taddr),
+               "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7])
+               : "memory");
+}
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15, %16};" ::"r"(taddr),
+      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]), "r"(r[9]),
+      "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
+      : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
 __device__ __forceinline__ void mma_commit(uint32_t mbar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
@@ -141,18 +165,24 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
 }
 
 // ---- operand layouts ---------------------------------------------------------
-// TF32 (4 bytes): row r, bin k -> (r/8)*512 + (k/4)*128 + (r%8)*16 + (k%4)*4; LBO 128, SBO 512.
-// BF16 (2 bytes): row r, bin k -> (r/8)*256 + (k/8)*128 + (r%8)*16 + (k%8)*2; LBO 128, SBO 256.
-__device__ __forceinline__ uint32_t off_tf32_chunk(uint32_t r, uint32_t j) {
-  return (r >> 3) * 512u + j * 128u + (r & 7u) * 16u;
+// B in shared memory.  TF32 (4 bytes): row n, bin k -> (n/8)*512 + (k/4)*128 + (n%8)*16 + (k%4)*4;
+// LBO 128, SBO 512.  BF16 (2 bytes): row n, bin k -> (n/8)*256 + (k/8)*128 + (n%8)*16 + (k%8)*2;
+// LBO 128, SBO 256.
+// A in tensor memory: columns per A set (one step's operands).
+template <int MODE>
+__host__ __device__ constexpr uint32_t a_cols() {
+  return MODE == FPTC_IDCT_TF32X3 ? 32u : 16u;  // BF16X3: hi 8 + lo 8; TF32: 16; TF32X3: big 16 + small 16
 }
-__device__ __forceinline__ uint32_t off_bf16_chunk(uint32_t r, uint32_t j) {
-  return (r >> 3) * 256u + j * 128u + (r & 7u) * 16u;
+// Tensor-memory columns per warpgroup: one 32-column D and two A sets.
+template <int MODE>
+__host__ __device__ constexpr uint32_t wg_cols() {
+  return 32u + 2u * a_cols<MODE>();
 }
 
-// Row r of the A operand(s) from one window's 16 coefficients.
+// This lane's row of the A operand(s) from one window's 16 coefficients; a
+// points at lane 32 q + i of the A set (all 32 lanes of the warp take part).
 template <int MODE>
-__device__ __forceinline__ void put_a_row(unsigned char *a, uint32_t r, const float (&c)[16]) {
+__device__ __forceinline__ void put_a_row(uint32_t a, const float (&c)[16]) {
   if (MODE == FPTC_IDCT_BF16X3) {
     uint32_t h[8], l[8];
 #pragma unroll
@@ -162,43 +192,38 @@ __device__ __forceinline__ void put_a_row(unsigned char *a, uint32_t r, const fl
       const float h0 = __uint_as_float(h[j] << 16), h1 = __uint_as_float(h[j] & 0xffff0000u);
       l[j] = pack_bf16(x0 - h0, x1 - h1);
     }
-#pragma unroll
-    for (int j = 0; j < 2; ++j) {
-      *reinterpret_cast<uint4 *>(a + off_bf16_chunk(r, j)) = make_uint4(h[4 * j], h[4 * j + 1], h[4 * j + 2], h[4 * j + 3]);
-      *reinterpret_cast<uint4 *>(a + 4096 + off_bf16_chunk(r, j)) =
-          make_uint4(l[4 * j], l[4 * j + 1], l[4 * j + 2], l[4 * j + 3]);
-    }
+    tmem_st8(a, h);
+    tmem_st8(a + 8, l);
   } else {
+    uint32_t big[16];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const float4 big = make_float4(tf32_round(c[4 * j]), tf32_round(c[4 * j + 1]), tf32_round(c[4 * j + 2]),
-                                     tf32_round(c[4 * j + 3]));
-      *reinterpret_cast<float4 *>(a + off_tf32_chunk(r, j)) = big;
-      if (MODE == FPTC_IDCT_TF32X3) {
-        const float4 sm = make_float4(tf32_round(c[4 * j] - big.x), tf32_round(c[4 * j + 1] - big.y),
-                                      tf32_round(c[4 * j + 2] - big.z), tf32_round(c[4 * j + 3] - big.w));
-        *reinterpret_cast<float4 *>(a + 8192 + off_tf32_chunk(r, j)) = sm;
-      }
+    for (int j = 0; j < 16; ++j) big[j] = __float_as_uint(tf32_round(c[j]));
+    tmem_st16(a, big);
+    if (MODE == FPTC_IDCT_TF32X3) {
+      uint32_t sm[16];
+#pragma unroll
+      for (int j = 0; j < 16; ++j) sm[j] = __float_as_uint(tf32_round(c[j] - __uint_as_float(big[j])));
+      tmem_st16(a + 16, sm);
     }
   }
 }
 
-// The products of one step: A buffer at a, B at b, accumulator d.
+// The products of one step: A set at tensor-memory column a, B at b, accumulator d.
 template <int MODE>
 __device__ __forceinline__ void issue_products(uint32_t a, uint32_t b, uint32_t d) {
   if (MODE == FPTC_IDCT_BF16X3) {
     constexpr uint32_t id = instr_desc(kFmtBF16, kRows, kN);
-    mma_f16(d, smem_desc(a, 128, 256), smem_desc(b, 128, 256), id, 0);          // hi * hi
-    mma_f16(d, smem_desc(a + 4096, 128, 256), smem_desc(b, 128, 256), id, 1);   // lo * hi
-    mma_f16(d, smem_desc(a, 128, 256), smem_desc(b + 1024, 128, 256), id, 1);   // hi * lo
+    mma_f16(d, a, smem_desc(b, 128, 256), id, 0);            // hi * hi
+    mma_f16(d, a + 8, smem_desc(b, 128, 256), id, 1);        // lo * hi
+    mma_f16(d, a, smem_desc(b + 1024, 128, 256), id, 1);     // hi * lo
   } else {
     constexpr uint32_t id = instr_desc(kFmtTF32, kRows, kN);
 #pragma unroll
     for (uint32_t h = 0; h < 2; ++h) {  // bins 0..7, 8..15
-      mma_tf32(d, smem_desc(a + 256 * h, 128, 512), smem_desc(b + 256 * h, 128, 512), id, h);
+      mma_tf32(d, a + 8 * h, smem_desc(b + 256 * h, 128, 512), id, h);
       if (MODE == FPTC_IDCT_TF32X3) {
-        mma_tf32(d, smem_desc(a + 256 * h, 128, 512), smem_desc(b + 2048 + 256 * h, 128, 512), id, 1);
-        mma_tf32(d, smem_desc(a + 8192 + 256 * h, 128, 512), smem_desc(b + 256 * h, 128, 512), id, 1);
+        mma_tf32(d, a + 8 * h, smem_desc(b + 2048 + 256 * h, 128, 512), id, 1);
+        mma_tf32(d, a + 16 + 8 * h, smem_desc(b + 256 * h, 128, 512), id, 1);
       }
     }
   }
@@ -214,21 +239,12 @@ struct StepOut {
   uint32_t flags;     // bit 0: 16-byte stores, bit 1: 32-byte stores, bit 2: TMA
 };
 
-// A operand buffers per warpgroup: two (the next step's rows are written while
-// the product reads the current ones), or one where two do not fit (TF32X3 with
-// three or four warpgroups: the rows of step k + 1 wait for product k).
-template <int MODE, int NWG>
-__host__ __device__ constexpr int a_buffers() {
-  return (MODE == FPTC_IDCT_TF32X3 && NWG >= 3) ? 1 : 2;
-}
-
 template <int MODE, int NWG>
 __global__ void __launch_bounds__(NWG * 128, 1) k_decode_tc(const DecodeParams p, const WarpParams wp,
                                                             const TcParams tp,
                                                             const __grid_constant__ CUtensorMap out_map) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr int WARPS = NWG * 4;
-  constexpr int ABUF = a_buffers<MODE, NWG>();
   const DomW *const dw = reinterpret_cast<const DomW *>(smem_raw);
   const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t wg = warp >> 2, wq = warp & 3;
@@ -255,13 +271,16 @@ __global__ void __launch_bounds__(NWG * 128, 1) k_decode_tc(const DecodeParams p
       }
     }
   }
-  uint64_t *const mbar = reinterpret_cast<uint64_t *>(smem_raw + tp.misc_off);  // [NWG][2]
-  uint32_t *const tmem_slot = reinterpret_cast<uint32_t *>(smem_raw + tp.misc_off + 16 * NWG);
+  uint64_t *const mbar = reinterpret_cast<uint64_t *>(smem_raw + tp.misc_off);  // [NWG]
+  uint32_t *const tmem_slot = reinterpret_cast<uint32_t *>(smem_raw + tp.misc_off + 8 * NWG);
   if (threadIdx.x == 0) {
-    for (int i = 0; i < 2 * NWG; ++i) mbar_init(smem_addr(mbar + i), 1);
+    for (int i = 0; i < NWG; ++i) mbar_init(smem_addr(mbar + i), 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  constexpr uint32_t kCols = NWG <= 2 ? 128u : 256u;  // two 32-column D per warpgroup, a power of two
+  // tensor memory: per warpgroup one D and two A sets, rounded up to a power of two
+  constexpr uint32_t kNeed = NWG * wg_cols<MODE>();
+  constexpr uint32_t kCols = kNeed <= 32 ? 32u : kNeed <= 64 ? 64u : kNeed <= 128 ? 128u : kNeed <= 256 ? 256u : 512u;
+  static_assert(kNeed <= 512, "tensor memory holds 512 columns");
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(tmem_slot)),
                  "r"(kCols)
@@ -273,14 +292,14 @@ __global__ void __launch_bounds__(NWG * 128, 1) k_decode_tc(const DecodeParams p
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
-  const uint32_t d_tmem = tmem + wg * 64u;               // this warpgroup's two 32-column D buffers
-  const uint32_t my_tmem = d_tmem + ((wq * 32u) << 16);  // lanes 32 wq .. 32 wq + 31
+  const uint32_t d_tmem = tmem + wg * wg_cols<MODE>();    // this warpgroup's D, then its two A sets
+  const uint32_t a_tmem = d_tmem + 32u;
+  const uint32_t lane_off = (wq * 32u) << 16;              // lanes 32 wq .. 32 wq + 31
 
   unsigned char *const wbase = smem_raw + wp.warp_off + warp * kMiscBytes;
   uint64_t *const wbuf = reinterpret_cast<uint64_t *>(wbase);
   TileRec *const rec = reinterpret_cast<TileRec *>(wbase + kPassWords * 8);
   uint8_t *const stage = wbase + kPassWords * 8 + 32 + kGuard;
-  unsigned char *const a_base = smem_raw + tp.a_off + wg * ABUF * tp.a_buf;
   const uintptr_t tiles0 = (reinterpret_cast<uintptr_t>(smem_raw + tp.tiles_off) + 1023) & ~uintptr_t(1023);
   unsigned char *const otile = reinterpret_cast<unsigned char *>(tiles0) + warp * kOutTile;
   const bool want_lev = p.levels != nullptr;
@@ -301,31 +320,31 @@ __global__ void __launch_bounds__(NWG * 128, 1) k_decode_tc(const DecodeParams p
     pn = fetch_pass0(p, make_ctx(p, t0 + wq, s, rec[0], rec[1]), lane, wbuf);
   }
 
-  uint32_t phase[2] = {0u, 0u};
+  uint32_t phase = 0u;
   bool timeout = false;  // this warp saw an expired wait
   bool stop = false;     // some warp of the warpgroup did (decided at a warpgroup barrier: uniform)
   bool tma_pending = false;
   StepOut prev{0, nullptr, 0, 0, 0};
   uint64_t k = 0;  // steps issued by this warpgroup
 
-  // Reads back step k - 1's product (D buffer (k - 1) & 1) and stores its windows.
-  auto drain = [&](const StepOut &o, uint32_t buf) {
+  // Reads back the product in D (step k - 1) and stores its windows.
+  auto drain = [&](const StepOut &o) {
     {
       uint32_t it = 0;
       bool late = false;
-      while (!mbar_try_wait(smem_addr(mbar + 2 * wg + buf), phase[buf])) {
+      while (!mbar_try_wait(smem_addr(mbar + wg), phase)) {
         if (++it >= kWaitLimit) {
           late = true;
           break;
         }
       }
-      phase[buf] ^= 1u;
+      phase ^= 1u;
       timeout = timeout || __any_sync(0xffffffffu, late);  // one decision for the warp
     }
     if (timeout) return;
     tc_fence_after();
     uint32_t v[32];
-    tmem_ld32(my_tmem + buf * 32u, v);
+    tmem_ld32(d_tmem + lane_off, v);
     if (o.nwin == 0) return;
     const bool tma = (o.flags & 4u) && o.nwin == kStepWin && (uint64_t)kStepWin * kN <= o.left;
     if (tma) {
@@ -410,31 +429,29 @@ __global__ void __launch_bounds__(NWG * 128, 1) k_decode_tc(const DecodeParams p
     const float *deq = reinterpret_cast<const float *>(smem_raw + dd.deq_off);
     uint8_t *const lev = (want_lev && nwin) ? p.levels + sg.level_offset + win0 * kE : nullptr;
     for (uint32_t w0 = 0; w0 < (uint32_t)kT; w0 += kStepWin) {
-      const uint32_t buf = (uint32_t)(k & 1);
-      unsigned char *const a = a_base + (ABUF == 2 ? buf : 0u) * tp.a_buf;
-      if (ABUF == 1 && k > 0) {
-        drain(prev, buf ^ 1u);  // product k - 1 has left the single A buffer
-        prev.nwin = 0;
-      }
+      const uint32_t a_set = a_tmem + (uint32_t)(k & 1) * a_cols<MODE>();
       const uint32_t wi = w0 + lane;
+      float c[16];
       if (wi < nwin) {
         const uint4 sv = *reinterpret_cast<const uint4 *>(stage + wi * kE);
-        float c[16];
         window_coefs(sv, deq, dd.zmask, c);
         if (lev) put_levels(lev + wi * kE, sv);
-        put_a_row<MODE>(a, wq * 32u + lane, c);
+      } else {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) c[j] = 0.0f;
       }
-      fence_async_shared();
+      put_a_row<MODE>(a_set + lane_off, c);  // product k - 1 reads the other A set
+      tmem_wait_st();
+      if (k > 0) drain(prev);                // D is free for product k once every warp has read it
       tc_fence_before();
-      // every row of A[buf] written; the readback of step k - 2 (same buffers) done
       if (wg_barrier_any(wg, timeout)) {
         stop = true;
         break;
       }
       tc_fence_after();
       if (wq == 0 && lane == 0) {
-        issue_products<MODE>(smem_addr(a), smem_addr(b_base), d_tmem + buf * 32u);
-        mma_commit(smem_addr(mbar + 2 * wg + buf));
+        issue_products<MODE>(a_set, smem_addr(b_base), d_tmem);
+        mma_commit(smem_addr(mbar + wg));
       }
       StepOut cur_out{0, nullptr, 0, 0, 0};
       if (w0 < nwin) {
@@ -446,13 +463,12 @@ __global__ void __launch_bounds__(NWG * 128, 1) k_decode_tc(const DecodeParams p
         cur_out.flags = (sg.out_aligned & 1u) | ((sg.out_aligned & 2u) && vec32_base ? 2u : 0u) |
                         (wp.out_tma && (sg.out_aligned & 4u) ? 4u : 0u);
       }
-      if (ABUF == 2 && k > 0) drain(prev, buf ^ 1u);  // an expiry here stops the warpgroup at the next barrier
       prev = cur_out;
       ++k;
     }
     __syncwarp();  // the level bytes are rewritten by the next tile
   }
-  if (!stop && !timeout && k > 0) drain(prev, (uint32_t)((k - 1) & 1));
+  if (!stop && !timeout && k > 0) drain(prev);
   if ((stop || timeout) && lane == 0) atomicOr(&p.status->flags, kFlagTimeout);
   if (tma_pending && lane == 0) tma_wait_all();
 
@@ -467,7 +483,10 @@ __global__ void __launch_bounds__(NWG * 128, 1) k_decode_tc(const DecodeParams p
 
 template <int MODE, int NWG>
 void *tcptr() {
-  return reinterpret_cast<void *>(&k_decode_tc<MODE, NWG>);
+  if constexpr (NWG * wg_cols<MODE>() <= 512u)
+    return reinterpret_cast<void *>(&k_decode_tc<MODE, NWG>);
+  else
+    return nullptr;
 }
 
 template <int MODE>
@@ -477,6 +496,8 @@ void *tcpick_mode(uint32_t nwg) {
     case 2: return tcptr<MODE, 2>();
     case 3: return tcptr<MODE, 3>();
     case 4: return tcptr<MODE, 4>();
+    case 5: return tcptr<MODE, 5>();
+    case 6: return MODE == FPTC_IDCT_TF32X3 ? nullptr : tcptr<MODE, 6>();
     default: return nullptr;
   }
 }
@@ -514,15 +535,14 @@ size_t tc_smem_layout(uint32_t mode, uint32_t threads, const uint32_t *lmax, uin
   wp->out_tma = 0;
   o += (size_t)warps * kMiscBytes;
   tp->b_off = (uint32_t)align16(o);
-  o = tp->b_off + 4096;  // up to two 32 x 64-byte operands
-  // one A buffer: 128 x 64 B (TF32, or BF16 hi + lo), twice that for TF32X3 (big, small)
-  tp->a_buf = mode == FPTC_IDCT_TF32X3 ? 16384u : 8192u;
-  const uint32_t abufs = (mode == FPTC_IDCT_TF32X3 && nwg >= 3) ? 1u : 2u;  // a_buffers<MODE, NWG>()
-  tp->a_off = (uint32_t)align16(o);
-  o = tp->a_off + (size_t)nwg * abufs * tp->a_buf;
+  o = tp->b_off + 4096;  // up to two 32 x 64-byte B operands
+  tp->a_off = 0;         // A lives in tensor memory
+  tp->a_buf = 0;
   tp->misc_off = (uint32_t)align16(o);
-  o = tp->misc_off + 16 * nwg + 16;
+  o = tp->misc_off + 8 * nwg + 16;
   tp->tiles_off = (uint32_t)align16(o);
+  const uint32_t cols = (mode == FPTC_IDCT_TF32X3 ? 96u : 64u) * nwg;  // wg_cols per warpgroup
+  if (cols > 512u) return ~size_t(0);                                   // does not fit tensor memory
   return tp->tiles_off + 1023 + (size_t)warps * kOutTile;
 }
 

@@ -160,10 +160,10 @@ fptc_status configure_launch(fptc_plan *p) {
   }
   const bool t_ok = threads == 128 || threads == 256 || threads == 512 ||
                     ((threads == 768 || threads == 1024) && p->kind == FPTC_KERNEL_WARP_TILE) ||
-                    (threads == 384 && p->kind == FPTC_KERNEL_TENSOR);
+                    ((threads == 384 || threads == 640 || threads == 768) && p->kind == FPTC_KERNEL_TENSOR);
   if (!t_ok) {
-    set_error("threads must be 128, 256 or 512 (768 and 1024 also for the warp-tile kernel, 384 for the "
-              "tensor-core kernel; got %u)", threads);
+    set_error("threads must be 128, 256 or 512 (768 and 1024 also for the warp-tile kernel, 384, 640 and 768 "
+              "for the tensor-core kernel; got %u)", threads);
     return FPTC_ERR_INVALID_ARGUMENT;
   }
   p->threads = threads;
@@ -185,7 +185,7 @@ fptc_status configure_launch(fptc_plan *p) {
       WarpParams pw{};
       TcParams pt{};
       threads = 128;
-      for (uint32_t t : {512u, 384u, 256u})
+      for (uint32_t t : {768u, 640u, 512u, 384u, 256u})
         if (tc_smem_layout(p->opts.idct, t, lm.data(), (uint32_t)lm.size(), &pw, &pt) <= (size_t)optin) {
           threads = t;
           break;
@@ -196,15 +196,14 @@ fptc_status configure_launch(fptc_plan *p) {
     e = tc_smem_config(p->opts.idct, threads, p->smem);
     if (e != cudaSuccess) return cuda_fail(e, "decode shared-memory size");
     e = tc_occupancy(p->opts.idct, threads, p->smem, &occ);
-    // tensor memory: 2 x 32 columns per warpgroup (a power of two per CTA), 512 per SM
-    const uint32_t nwg = threads / 128, cols = nwg <= 1 ? 64u : (nwg == 2 ? 128u : 256u);
+    // one CTA per SM (tensor memory)
     if (std::getenv("FPTC_DEBUG")) {
       cudaFuncAttributes fa{};
       tc_attributes(p->opts.idct, threads, &fa);
       std::fprintf(stderr, "fptc: tensor kernel threads %u regs %d static smem %zu max dyn smem %d dyn %zu occupancy %d\n",
                    threads, fa.numRegs, fa.sharedSizeBytes, fa.maxDynamicSharedSizeBytes, p->smem, occ);
     }
-    if (e == cudaSuccess) occ = std::min<int>(occ, (int)(512u / cols));
+    if (e == cudaSuccess) occ = std::min<int>(occ, 1);
   } else if (p->kind == FPTC_KERNEL_WARP_TILE) {
     std::vector<uint32_t> lm;
     for (const auto &d : p->domains) lm.push_back(d.lmax);
@@ -912,13 +911,13 @@ fptc_status fptc_plan_autotune(fptc_plan *p, const uint64_t *d_words, const uint
   };
   std::vector<Cand> cands;
   for (uint32_t th : {128u, 256u, 512u, 768u, 1024u}) {
-    if (th > 512) {
-      if (keep.idct == FPTC_IDCT_FP32 && fixed && p->domains.size() <= kWarpMaxDomains)
-        cands.push_back({FPTC_KERNEL_WARP_TILE, warp_tile_windows() * 32, th});
+    if (keep.idct != FPTC_IDCT_FP32) {
+      if (th <= 768) cands.push_back({FPTC_KERNEL_TENSOR, tc_tile_windows() * 32, th});
       continue;
     }
-    if (keep.idct != FPTC_IDCT_FP32) {
-      cands.push_back({FPTC_KERNEL_TENSOR, tc_tile_windows() * 32, th});
+    if (th > 512) {
+      if (fixed && p->domains.size() <= kWarpMaxDomains)
+        cands.push_back({FPTC_KERNEL_WARP_TILE, warp_tile_windows() * 32, th});
       continue;
     }
     if (fixed && p->domains.size() <= kWarpMaxDomains) cands.push_back({FPTC_KERNEL_WARP_TILE, warp_tile_windows() * 32, th});
