@@ -910,11 +910,10 @@ fptc_status fptc_plan_autotune(fptc_plan *p, const uint64_t *d_words, const uint
     uint32_t kernel, tile_samples, threads;
   };
   std::vector<Cand> cands;
+  if (keep.idct != FPTC_IDCT_FP32)
+    for (uint32_t th : {256u, 384u, 512u, 640u, 768u}) cands.push_back({FPTC_KERNEL_TENSOR, tc_tile_windows() * 32, th});
   for (uint32_t th : {128u, 256u, 512u, 768u, 1024u}) {
-    if (keep.idct != FPTC_IDCT_FP32) {
-      if (th <= 768) cands.push_back({FPTC_KERNEL_TENSOR, tc_tile_windows() * 32, th});
-      continue;
-    }
+    if (keep.idct != FPTC_IDCT_FP32) continue;
     if (th > 512) {
       if (fixed && p->domains.size() <= kWarpMaxDomains)
         cands.push_back({FPTC_KERNEL_WARP_TILE, warp_tile_windows() * 32, th});
