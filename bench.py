@@ -154,17 +154,23 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
+KERNEL_SOURCES = {1: ["decode.cu"], 2: ["decode_fixed.cu"], 3: ["decode_warp.cu", "warp_tile.cuh"],
+                  4: ["decode_tc.cu", "warp_tile.cuh"], 5: ["backward_warp.cu", "warp_tile.cuh"]}
+
+
 def _kernel_source_hash(kind: int):
     import hashlib
-    files = {1: "decode.cu", 2: "decode_fixed.cu", 3: "decode_warp.cu", 4: "decode_tc.cu"}
-    f = os.path.join(ROOT, "paper_2605_01086_gb300", "csrc", files.get(kind, "decode.cu"))
-    with open(f, "rb") as fh:
-        return hashlib.sha1(fh.read()).hexdigest()[:12]
+    h = hashlib.sha1()
+    for f in KERNEL_SOURCES.get(kind, ["decode.cu"]):
+        with open(os.path.join(ROOT, "paper_2605_01086_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:12]
 
 
 def measured_traffic(kind: int, n_samples: int):
     """DRAM bytes per launch from the committed ncu summary (profiles/dram_traffic.txt:
-    'kind sha1 bytes_per_sample'), scaled to this launch; None if the kernel changed since."""
+    'kind sha1 bytes_per_sample'), scaled to this launch; None if the kernel changed since.
+    Kinds: 1-4 the decode kernels (fptc_kernel), 5 the warp-tile adjoint."""
     p = os.path.join(ROOT, "profiles", "dram_traffic.txt")
     if not os.path.exists(p):
         return None
@@ -396,6 +402,8 @@ def run(args):
                            "threads": fplan.info["threads"],
                            "roofline": {"bound": "hbm", "achieved": ka, "peak": peak, "unit": "GB/s",
                                         "frac": ka / peak, "launch_ms": statistics.median(kms),
+                                        "traffic": measured_traffic(4, n_samples) if fplan.info["kernel"] == 4
+                                        else None,
                                         "kernel": "k_decode_tc (tcgen05)"}}
             fplan.close()
             del out3
@@ -429,6 +437,7 @@ def run(args):
             "grad_scale_finite": bool(torch.isfinite(gsc).all()),
             "roofline": {"bound": "hbm", "achieved": b_bytes / (bwd_ms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
                          "frac": b_bytes / (bwd_ms / 1e3) / 1e9 / peak, "algorithmic_bytes_per_launch": b_bytes,
+                         "traffic": measured_traffic(5, n_samples) if plan.info["kernel"] in (3, 4) else None,
                          "kernel": "k_backward_warp (adjoint)"}}
         del lv, gco, sc
 
