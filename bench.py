@@ -441,6 +441,26 @@ def run(args):
                          "kernel": "k_backward_warp (adjoint)"}}
         del lv, gco, sc
 
+    # the paper's three-kernel GPU design on the same streams (global per-word offsets and
+    # level array, one thread per output sample), for comparison with the fused kernels
+    if not args.no_plain and rank == 0:
+        tplan = Plan(doms, batch.segments, device=local, schedule="three_kernel")
+        out4 = torch.zeros_like(out)
+        with torch.cuda.stream(stream):
+            tplan.decode(w, s, out=out4, stream=stream)
+            tms = time_steps(lambda: tplan.decode(w, s, out=out4, stream=stream), 3, stream, torch)
+            tix = time_steps(lambda: tplan.decode_stages(w, s, out4, STAGE_INDEX, stream=stream), 3, stream, torch)
+            tdc = time_steps(lambda: tplan.decode_stages(w, s, out4, STAGE_DECODE, stream=stream), 3, stream, torch)
+        torch.cuda.synchronize()
+        rel = float(torch.linalg.vector_norm((out4 - out).double()) / torch.linalg.vector_norm(out.double()))
+        tv = out_bytes / (statistics.median(tms) / 1e3) / 1e9
+        line["three_kernel"] = {"value": tv, "unit": UNIT, "ms_per_step": statistics.median(tms),
+                                "index_ms": statistics.median(tix), "decode_ms": statistics.median(tdc),
+                                "launches_per_step": tplan.launches_per_decode, "rel_l2_vs_fused": rel,
+                                "fused_over_three_kernel": value / world / tv}
+        tplan.close()
+        del out4
+
     # plain baseline: one set of launches per stream, same streams, same output
     if not args.no_plain and rank == 0:
         pplan = Plan(doms, batch.segments, device=local, schedule="per_segment")

@@ -100,7 +100,12 @@ typedef enum fptc_idct {
 
 typedef enum fptc_schedule {
   FPTC_SCHEDULE_PERSISTENT = 0,  /* one persistent launch over every tile of the batch */
-  FPTC_SCHEDULE_PER_SEGMENT = 1  /* plain: one set of launches per segment */
+  FPTC_SCHEDULE_PER_SEGMENT = 1, /* plain: one set of launches per segment */
+  FPTC_SCHEDULE_THREE_KERNEL = 2 /* the GPU design of Sec. 4.2, for comparison: per-word offsets in a
+                                    global array, one thread per word writing the levels to a global
+                                    byte array, one thread per output sample for dequantization and
+                                    inverse DCT.  The plan owns a 4-byte-per-word offset array and a
+                                    level array (unless levels are passed); FP32 transform only */
 } fptc_schedule;
 
 typedef enum fptc_kernel {

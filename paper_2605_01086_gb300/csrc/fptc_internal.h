@@ -140,6 +140,11 @@ struct BackwardParams {
 
 // Launch wrappers (index.cu, decode.cu, backward.cu).
 cudaError_t launch_index(const IndexParams &p, cudaStream_t stream);
+// per-word symbol offsets (index.cu) and the lossless / lossy kernels (decode_paper.cu) of the
+// three-kernel schedule
+cudaError_t launch_word_offsets(const IndexParams &p, uint32_t *word_off, cudaStream_t stream);
+cudaError_t launch_three_kernel(const DecodeParams &p, const uint32_t *word_off, uint8_t *levels,
+                                uint64_t chunk_begin, uint64_t chunk_end, cudaStream_t stream);
 // generic kernel (any N, E)
 cudaError_t launch_decode(const DecodeParams &p, int kind, uint32_t threads, uint32_t grid, size_t smem,
                           cudaStream_t stream);

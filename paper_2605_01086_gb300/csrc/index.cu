@@ -213,6 +213,38 @@ __global__ void __launch_bounds__(256) k_tile_index(IndexParams p) {
   }
 }
 
+// Symbol offset (in the segment) of every word, for the three-kernel schedule
+// (Sec. 4.2.1 as the paper runs it: a global array of per-word offsets).
+__global__ void __launch_bounds__(256) k_word_offsets(IndexParams p, uint32_t *word_off) {
+  const uint32_t lane = threadIdx.x & 31;
+  uint64_t c0, c1;
+  warp_chunks(p, c0, c1);
+  if (c0 >= c1) return;
+  uint32_t s = chunk_segment(p.segs, p.seg_begin, p.seg_end, c0);
+  for (uint64_t c = c0; c < c1; ++c) {
+    while (c >= p.segs[s].chunk_base + p.segs[s].n_chunks) ++s;
+    const SegDev &sg = p.segs[s];
+    const LaneBlock b = load_block(p.symlen, sg, c - sg.chunk_base, lane);
+    const uint32_t tsum = block_sum(b.v);
+    uint32_t x = tsum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= (uint32_t)o) x += y;
+    }
+    if (p.seg_bad[s] != 0) continue;  // uniform over the warp
+    uint32_t off = (uint32_t)p.chunk_off[c] + (x - tsum);
+    const uint32_t wv[4] = {b.v.x, b.v.y, b.v.z, b.v.w};
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      const uint64_t word = b.word0 + j;
+      // inside the segment (block -1 wraps below word_offset and fails the test)
+      if (word - sg.word_offset < sg.n_words && lane < 31) word_off[word] = off;
+      off += (wv[j >> 2] >> (8 * (j & 3))) & 0xffu;
+    }
+  }
+}
+
 }  // namespace
 
 cudaError_t launch_index(const IndexParams &p, cudaStream_t stream) {
@@ -229,4 +261,15 @@ cudaError_t launch_index(const IndexParams &p, cudaStream_t stream) {
   return cudaGetLastError();
 }
 
+}  // namespace fptc
+
+namespace fptc {
+cudaError_t launch_word_offsets(const IndexParams &p, uint32_t *word_off, cudaStream_t stream) {
+  const uint64_t n_chunks = p.chunk_end - p.chunk_begin;
+  if (n_chunks == 0 || p.seg_end <= p.seg_begin) return cudaSuccess;
+  const uint64_t want = (n_chunks + 7) / 8;
+  const uint32_t grid = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(p.grid ? p.grid : 1024u, want));
+  k_word_offsets<<<grid, 256, 0, stream>>>(p, word_off);
+  return cudaGetLastError();
+}
 }  // namespace fptc

@@ -39,6 +39,8 @@ struct fptc_plan {
   uint32_t *d_chunk_sum = nullptr;
   uint64_t *d_chunk_off = nullptr;
   uint32_t *d_seg_bad = nullptr;
+  uint32_t *d_word_off = nullptr;   // three-kernel schedule: symbol offset of every word
+  uint8_t *d_lev_scratch = nullptr; // three-kernel schedule: the level array
   TileRec *d_tiles = nullptr;
   uint64_t tiles_capacity = 0;
   DevStatus *d_status = nullptr;
@@ -97,6 +99,8 @@ void free_device(fptc_plan *p) {
   cudaFree(p->d_chunk_sum);
   cudaFree(p->d_chunk_off);
   cudaFree(p->d_seg_bad);
+  cudaFree(p->d_word_off);
+  cudaFree(p->d_lev_scratch);
   cudaFree(p->d_tiles);
   cudaFree(p->d_status);
   for (auto &a : p->aux)
@@ -340,6 +344,7 @@ cudaError_t run_range(const fptc_plan *p, const IndexParams &ip0, const DecodePa
     ip.chunk_begin = a.chunk_base;
     ip.chunk_end = b.chunk_base + b.n_chunks;
     cudaError_t e = launch_index(ip, st);
+    if (e == cudaSuccess && p->opts.schedule == FPTC_SCHEDULE_THREE_KERNEL) e = launch_word_offsets(ip, p->d_word_off, st);
     if (e != cudaSuccess) return e;
   }
   if (!decode) return cudaSuccess;
@@ -348,6 +353,9 @@ cudaError_t run_range(const fptc_plan *p, const IndexParams &ip0, const DecodePa
   dp.seg_end = s1;
   dp.tile_begin = a.tile_base;
   dp.tile_end = b.tile_base + b.n_tiles;
+  if (p->opts.schedule == FPTC_SCHEDULE_THREE_KERNEL)
+    return launch_three_kernel(dp, p->d_word_off, dp.levels ? dp.levels : p->d_lev_scratch, a.chunk_base,
+                               b.chunk_base + b.n_chunks, st);
   const uint64_t tiles = dp.tile_end - dp.tile_begin;
   const uint32_t grid = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(p->grid, tiles));
   if (p->kind == FPTC_KERNEL_BLOCK_TILE) return launch_fixed(dp, p->threads, grid, p->smem, st);
@@ -440,7 +448,8 @@ fptc_status fptc_plan_create(fptc_plan **out, int device, const fptc_domain *dom
   o.idct = FPTC_IDCT_FP32;
   o.schedule = FPTC_SCHEDULE_PERSISTENT;
   if (opts) o = *opts;
-  if (o.idct > FPTC_IDCT_TF32X3 || o.schedule > FPTC_SCHEDULE_PER_SEGMENT || o.reserved[0] || o.reserved[1]) {
+  if (o.idct > FPTC_IDCT_TF32X3 || o.schedule > FPTC_SCHEDULE_THREE_KERNEL || o.reserved[0] || o.reserved[1] ||
+      (o.schedule == FPTC_SCHEDULE_THREE_KERNEL && o.idct != FPTC_IDCT_FP32)) {
     set_error("invalid plan options");
     return FPTC_ERR_INVALID_ARGUMENT;
   }
@@ -652,6 +661,11 @@ fptc_status fptc_plan_create(fptc_plan **out, int device, const fptc_domain *dom
         DevStatus s0{0u, 0u, ~0ull};
         e = cudaMemcpy(p->d_status, &s0, sizeof(s0), cudaMemcpyHostToDevice);
         if (e == cudaSuccess) e = cudaMemset(p->d_seg_bad, 0, ns * 4);
+        if (e == cudaSuccess && o.schedule == FPTC_SCHEDULE_THREE_KERNEL) {
+          e = cudaMalloc(&p->d_word_off, std::max<uint64_t>(p->words_extent, 1) * 4);
+          if (e == cudaSuccess) e = cudaMalloc(&p->d_lev_scratch, std::max<uint64_t>(p->n_levels, 1));
+          if (e == cudaSuccess) b += std::max<uint64_t>(p->words_extent, 1) * 4 + std::max<uint64_t>(p->n_levels, 1);
+        }
         if (e != cudaSuccess) st = cuda_fail(e, "plan scratch init");
       }
     }
@@ -725,6 +739,7 @@ uint32_t fptc_plan_launches_per_decode(const fptc_plan *p) {
   if (!p) return 0;
   if (p->segs.empty()) return 0;
   if (p->opts.schedule == FPTC_SCHEDULE_PERSISTENT) return (p->n_chunks ? 3u : 1u) + 1u;
+  if (p->opts.schedule == FPTC_SCHEDULE_THREE_KERNEL) return (p->n_chunks ? 4u : 1u) + (p->n_chunks ? 2u : 1u);
   uint32_t n = 0;
   for (const auto &s : p->segs) n += (s.n_chunks ? 3u : 1u) + 1u;
   return n;
@@ -752,7 +767,7 @@ fptc_status fptc_decode_stages(fptc_plan *p, const uint64_t *d_words, const uint
   const IndexParams ip = index_params(p, d_symlen);
   const DecodeParams dp = decode_params(p, d_words, d_symlen, d_out, d_levels, d_scale);
   cudaError_t e = cudaSuccess;
-  if (p->opts.schedule == FPTC_SCHEDULE_PERSISTENT) {
+  if (p->opts.schedule != FPTC_SCHEDULE_PER_SEGMENT) {
     e = run_range(p, ip, dp, 0, (uint32_t)p->segs.size(), idx, s, dec);
   } else {
     for (uint32_t i = 0; i < p->segs.size() && e == cudaSuccess; ++i) e = run_range(p, ip, dp, i, i + 1, idx, s, dec);
@@ -838,6 +853,7 @@ fptc_status fptc_decode_host(fptc_plan *p, const uint64_t *h_words, const uint8_
   const IndexParams ip = index_params(p, d_symlen);
   const DecodeParams dp = decode_params(p, d_words, d_symlen, d_out, nullptr, nullptr);
   e = launch_index(ip, s);
+  if (e == cudaSuccess && p->opts.schedule == FPTC_SCHEDULE_THREE_KERNEL) e = launch_word_offsets(ip, p->d_word_off, s);
   if (e != cudaSuccess) return cuda_fail(e, "index launch");
   // decode in pieces of about equal output; each piece is copied back on one of
   // several streams (several copy engines) while the next pieces decode
