@@ -154,8 +154,10 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-KERNEL_SOURCES = {1: ["decode.cu"], 2: ["decode_fixed.cu"], 3: ["decode_warp.cu", "warp_tile.cuh"],
-                  4: ["decode_tc.cu", "warp_tile.cuh"], 5: ["backward_warp.cu", "warp_tile.cuh"]}
+KERNEL_SOURCES = {1: ["decode.cu"], 2: ["decode_fixed.cu"],
+                  3: ["decode_warp.cu", "warp_tile.cuh", "symlen_chunks.cuh"],
+                  4: ["decode_tc.cu", "warp_tile.cuh", "symlen_chunks.cuh"],
+                  5: ["backward_warp.cu", "warp_tile.cuh", "symlen_chunks.cuh"]}
 
 
 def _kernel_source_hash(kind: int):
@@ -516,6 +518,55 @@ def run(args):
     return 0
 
 
+SWEEP_SHAPES = [(16, 8), (32, 8), (32, 16), (32, 32), (64, 16), (64, 32), (128, 32), (128, 64)]
+
+
+def run_sweep(args):
+    """Throughput over the window size N and kept bins E (Table 1 ranges; the paper's Fig. 14
+    trend): 512 EEG-like signals of 65,536 samples per shape, tables trained per shape,
+    index + decode per step on the plan's default kernel."""
+    import torch
+
+    from paper_2605_01086_gb300 import Plan, codec
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    wl = siggen.eeg_2048x1m()
+    n, S = 512, 65536
+    seeds = wl.seeds[:n]
+    doms_d = np.zeros(n, np.int32)
+    lengths = np.full(n, S, np.uint64)
+    flat, offs = siggen.signals(doms_d, seeds, lengths)
+    ts = siggen.training_set(0)
+    tflat, toffs = siggen.signals(ts.domains, ts.seeds, ts.lengths)
+    rows = []
+    stream = torch.cuda.Stream(dev)
+    for N, E in SWEEP_SHAPES:
+        d = codec.train_domain(tflat, toffs, ts.lengths, N, E, min(2, E), E, 50.0, 0.004, 12, 99.9)
+        b = codec.encode_batch([d], flat, offs, lengths, np.zeros(n, np.uint32))
+        plan = Plan([d], b.segments, device=0)
+        w, s = plan.to_device(b.words, b.symlen)
+        out = plan.empty_out()
+        with torch.cuda.stream(stream):
+            plan.decode(w, s, out=out, stream=stream)
+            for _ in range(args.warmup):
+                plan.decode(w, s, out=out, stream=stream)
+            ms = time_steps(lambda: plan.decode(w, s, out=out, stream=stream), args.steps, stream, torch)
+        torch.cuda.synchronize()
+        x = flat.astype(np.float64)
+        xh = out[:n * S].double().cpu().numpy()
+        prd = 100.0 * float(np.sqrt(np.sum((x - xh) ** 2) / np.sum(x ** 2)))
+        out_b = 4 * n * S
+        rows.append({"N": N, "E": E, "kernel": plan.info["kernel"], "ms": statistics.median(ms),
+                     "GBps": out_b / (statistics.median(ms) / 1e3) / 1e9,
+                     "compression_ratio": out_b / (9.0 * b.words.size), "prd_percent": prd})
+        plan.close()
+        del w, s, out
+    print(json.dumps({"sweep": "N x E, 512 EEG-like signals x 65536 samples, index + decode per step",
+                      "unit": UNIT, "rows": rows}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -534,6 +585,7 @@ def main():
     ap.add_argument("--no-forms", action="store_true")
     ap.add_argument("--kernel", default=None, help="fix the decode kernel (no autotuning): warp_tile, block_tile, generic")
     ap.add_argument("--threads", type=int, default=0)
+    ap.add_argument("--sweep", action="store_true", help="throughput over window size N and kept bins E instead")
     ap.add_argument("--idct", default="fp32", choices=["fp32", "tf32", "bf16x3", "tf32x3"],
                     help="inverse-transform form of the timed plan (tensor-core forms use the tcgen05 kernel)")
     args = ap.parse_args()
@@ -541,6 +593,8 @@ def main():
         raise SystemExit("--warmup must be >= 3")
     if args.impl == "reference":
         return run_reference(args)
+    if args.sweep:
+        return run_sweep(args)
     return run(args)
 
 

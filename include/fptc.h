@@ -133,7 +133,7 @@ typedef struct fptc_plan fptc_plan;
 typedef struct fptc_plan_info {
   uint64_t n_segments;
   uint64_t n_tiles;
-  uint64_t n_chunks;            /* index work units (2048 words each) */
+  uint64_t n_chunks;            /* index work units (chunks of at most 496 words) */
   uint64_t words_extent;        /* max(word_offset + n_words): minimum word/symlen buffer length */
   uint64_t out_extent;          /* max(out_offset + n_samples): minimum output length in floats */
   uint64_t n_samples_total;

@@ -157,8 +157,7 @@ __global__ void __launch_bounds__(WARPS * 32, 1) k_backward_warp(const BackwardP
 
   unsigned char *const wbase = smem_raw + wp.warp_off + warp * kMiscBytes;
   uint64_t *const wbuf = reinterpret_cast<uint64_t *>(wbase);
-  TileRec *const rec = reinterpret_cast<TileRec *>(wbase + kPassWords * 8);
-  uint8_t *const stage = wbase + kPassWords * 8 + 32 + kGuard;
+  uint8_t *const stage = wbase + kPassWords * 8 + kGuard;
   uint64_t *const mbar = reinterpret_cast<uint64_t *>(smem_raw + wp.warp_off + WARPS * kMiscBytes) + 2 * warp;
   const uintptr_t tiles0 =
       (reinterpret_cast<uintptr_t>(smem_raw + wp.warp_off + WARPS * kMiscBytes + WARPS * 16) + 1023) &
@@ -178,11 +177,10 @@ __global__ void __launch_bounds__(WARPS * 32, 1) k_backward_warp(const BackwardP
 
   uint32_t s = find_segment(p.segs, p.seg_begin, p.seg_end, tw0);
   uint32_t pn = 0;
-  if (redecode) {
-    fetch_records(p, tw0, lane, rec);
-    cp_async_wait_all();
-    __syncwarp();
-    pn = fetch_pass0(p, make_ctx(p, tw0, s, rec[0], rec[1]), lane, wbuf);
+  Ctx nxt{0, 0, 0, s, 0};
+  if (redecode) {  // where tile tw0 starts, then its first words
+    nxt = first_ctx(p, s, tw0, lane);
+    pn = fetch_pass0(p, nxt, lane, wbuf);
   }
 
   uint32_t phase[2] = {0u, 0u};
@@ -211,14 +209,17 @@ __global__ void __launch_bounds__(WARPS * 32, 1) k_backward_warp(const BackwardP
     if (redecode) {
       cp_async_wait_all();
       __syncwarp();
-      cur = make_ctx(p, g, s, rec[0], rec[1]);
+      cur = nxt;
 #pragma unroll
       for (int u = 0; u < kWPL; ++u) {
         w[u] = wbuf[kWPL * lane + u];
         n[u] = (pn >> (8 * u)) & 0xffu;
       }
       __syncwarp();
-      if (g + 1 < tw1) fetch_records(p, g + 1, lane, rec);
+      if (!cur.ok && g + 1 < tw1) {  // skipped tile: the next one is located without it
+        nxt = next_ctx(p, g, s, cur, TileEnd{0u, 0u, 0u});
+        pn = fetch_pass0(p, nxt, lane, wbuf);
+      }
     }
     const SegDev &sg = p.segs[s];
     if (!cur.ok) continue;  // a segment the index flagged (only when decoding again)
@@ -257,14 +258,11 @@ __global__ void __launch_bounds__(WARPS * 32, 1) k_backward_warp(const BackwardP
     issue(si);
 
     if (redecode) {
-      const uint32_t bad = decode_tile(p, cur, dd, smem_raw, stage, lane, w, n);
-      if (bad && lane == 0) flag_bad(p.status, bad, sg.caller_index);
-      if (g + 1 < tw1) {
-        cp_async_wait_all();
-        __syncwarp();
-        uint32_t s1 = s;
-        while (g + 1 >= p.segs[s1].tile_base + p.segs[s1].n_tiles) ++s1;
-        pn = fetch_pass0(p, make_ctx(p, g + 1, s1, rec[0], rec[1]), lane, wbuf);
+      const TileEnd te = decode_tile(p, cur, nwin * kE, dd, smem_raw, stage, lane, w, n);
+      if (te.bad && lane == 0) flag_bad(p.status, te.bad, sg.caller_index);
+      if (g + 1 < tw1) {  // tile g + 1 starts where tile g ended
+        nxt = next_ctx(p, g, s, cur, te);
+        pn = fetch_pass0(p, nxt, lane, wbuf);
       }
       __syncwarp();
     }

@@ -3,7 +3,8 @@
 //
 // The SymLen decode, the level staging, the dequantization and the output path
 // are those of the warp-tile kernel (warp_tile.cuh): each warp decodes whole
-// tiles of 128 windows into level bytes.  The inverse transform of Eq. 1 is
+// tiles of 128 windows into level bytes, over a contiguous tile range of its
+// own.  The inverse transform of Eq. 1 is
 //      D[128 windows x 32 samples] = C[128 x 16 bins] * B[16 x 32]
 // with B[k][n] = cos(pi/N (n + 1/2) k) (B[0][n] = 1/2), one product per
 // transform step of a warpgroup: its four warps each contribute 32 windows
@@ -298,26 +299,31 @@ __global__ void __launch_bounds__(NWG * 128, 1) k_decode_tc(const DecodeParams p
 
   unsigned char *const wbase = smem_raw + wp.warp_off + warp * kMiscBytes;
   uint64_t *const wbuf = reinterpret_cast<uint64_t *>(wbase);
-  TileRec *const rec = reinterpret_cast<TileRec *>(wbase + kPassWords * 8);
-  uint8_t *const stage = wbase + kPassWords * 8 + 32 + kGuard;
+  uint8_t *const stage = wbase + kPassWords * 8 + kGuard;
   const uintptr_t tiles0 = (reinterpret_cast<uintptr_t>(smem_raw + tp.tiles_off) + 1023) & ~uintptr_t(1023);
   unsigned char *const otile = reinterpret_cast<unsigned char *>(tiles0) + warp * kOutTile;
   const bool want_lev = p.levels != nullptr;
   const bool vec32_base = (reinterpret_cast<uintptr_t>(p.out) & 31u) == 0;
 
-  // ---- this warpgroup's tiles; warp q takes tiles t0 + 4 r + q in round r
+  // ---- this warp's tiles: an even split of the launch's tile range over all
+  // warps; the warpgroup runs as many rounds as its longest range (the four
+  // differ by at most one tile), a warp past its range contributing zero rows
+  const uint64_t units = (uint64_t)gridDim.x * NWG * 4, u0 = ((uint64_t)blockIdx.x * NWG + wg) * 4;
   uint64_t t0, t1;
-  unit_tiles(p, (uint64_t)blockIdx.x * NWG + wg, (uint64_t)gridDim.x * NWG, t0, t1);
-  const uint64_t rounds = (t1 - t0 + 3) / 4;  // the same for the four warps
+  unit_tiles(p, u0 + wq, units, t0, t1);
+  uint64_t rounds = 0;
+  for (uint32_t q = 0; q < 4; ++q) {
+    uint64_t a, b;
+    unit_tiles(p, u0 + q, units, a, b);
+    rounds = b - a > rounds ? b - a : rounds;
+  }
 
   uint32_t s = find_segment(p.segs, p.seg_begin, p.seg_end, t0 < t1 ? t0 : p.tile_begin);
   uint32_t pn = 0;
-  if (t0 + wq < t1) {
-    fetch_records(p, t0 + wq, lane, rec);
-    cp_async_wait_all();
-    __syncwarp();
-    while (t0 + wq >= p.segs[s].tile_base + p.segs[s].n_tiles) ++s;
-    pn = fetch_pass0(p, make_ctx(p, t0 + wq, s, rec[0], rec[1]), lane, wbuf);
+  Ctx nxt{0, 0, 0, s, 0};
+  if (t0 < t1) {  // where tile t0 starts, then its first words
+    nxt = first_ctx(p, s, t0, lane);
+    pn = fetch_pass0(p, nxt, lane, wbuf);
   }
 
   uint32_t phase = 0u;
@@ -389,7 +395,7 @@ __global__ void __launch_bounds__(NWG * 128, 1) k_decode_tc(const DecodeParams p
   };
 
   for (uint64_t r = 0; r < rounds && !stop; ++r) {
-    const uint64_t g = t0 + 4 * r + wq;
+    const uint64_t g = t0 + r;
     const bool have = g < t1;
     Ctx cur{0, 0, 0, s, 0};
     uint64_t w[kWPL] = {0, 0};
@@ -397,15 +403,14 @@ __global__ void __launch_bounds__(NWG * 128, 1) k_decode_tc(const DecodeParams p
     if (have) {
       cp_async_wait_all();
       __syncwarp();
-      while (g >= p.segs[s].tile_base + p.segs[s].n_tiles) ++s;
-      cur = make_ctx(p, g, s, rec[0], rec[1]);
+      cur = nxt;
+      s = cur.seg;
 #pragma unroll
       for (int u = 0; u < kWPL; ++u) {
         w[u] = wbuf[kWPL * lane + u];
         n[u] = (pn >> (8 * u)) & 0xffu;
       }
       __syncwarp();
-      if (g + 4 < t1) fetch_records(p, g + 4, lane, rec);
     }
     const SegDev &sg = p.segs[cur.seg];
     const DomW dd = dw[sg.domain];
@@ -413,16 +418,14 @@ __global__ void __launch_bounds__(NWG * 128, 1) k_decode_tc(const DecodeParams p
     const uint64_t left = sg.n_windows - win0;
     const uint32_t nwin = !(have && cur.ok) ? 0u : (left < (uint64_t)kT ? (uint32_t)left : (uint32_t)kT);
 
+    TileEnd te{0u, 0u, 0u};
     if (nwin) {
-      const uint32_t bad = decode_tile(p, cur, dd, smem_raw, stage, lane, w, n);
-      if (bad && lane == 0) flag_bad(p.status, bad, sg.caller_index);
+      te = decode_tile(p, cur, nwin * kE, dd, smem_raw, stage, lane, w, n);
+      if (te.bad && lane == 0) flag_bad(p.status, te.bad, sg.caller_index);
     }
-    if (g + 4 < t1) {
-      cp_async_wait_all();
-      __syncwarp();
-      uint32_t s1 = s;
-      while (g + 4 >= p.segs[s1].tile_base + p.segs[s1].n_tiles) ++s1;
-      pn = fetch_pass0(p, make_ctx(p, g + 4, s1, rec[0], rec[1]), lane, wbuf);
+    if (g + 1 < t1) {  // tile g + 1 starts where tile g ended
+      nxt = next_ctx(p, g, s, cur, te);
+      pn = fetch_pass0(p, nxt, lane, wbuf);
     }
     __syncwarp();
 

@@ -27,9 +27,10 @@
 //     with a TMA tensor store (the output viewed as rows of 32 floats), so the
 //     output never passes through the L1 load/store pipe.  Other windows use
 //     32-byte (or 16-byte, or scalar) streaming stores.
-//  The tile records of tile g+1 are loaded when tile g starts, the first words
-//  of tile g+1 when tile g's decode ends (hidden by its transform), and the
-//  words of a tile's next decode pass before the current pass.
+//  The warp locates the first tile of its range from the index's chunk
+//  offsets; tile g+1 starts at the word where tile g's decode ended, and its
+//  first words are loaded then (hidden by tile g's transform); the words of a
+//  tile's next decode pass load while the current pass decodes.
 // The decode tables, dequantization rows and basis of every domain stay in
 // shared memory for the whole kernel.
 #include <cuda.h>
@@ -150,8 +151,7 @@ __global__ void __launch_bounds__(WARPS * 32, WARPS > 16 ? 1 : 32 / WARPS) k_dec
 
   unsigned char *const wbase = smem_raw + wp.warp_off + warp * kMiscBytes;
   uint64_t *const wbuf = reinterpret_cast<uint64_t *>(wbase);                       // first-pass words
-  TileRec *const rec = reinterpret_cast<TileRec *>(wbase + kPassWords * 8);          // records g, g + 1
-  uint8_t *const stage = wbase + kPassWords * 8 + 32 + kGuard;                      // tile position 0
+  uint8_t *const stage = wbase + kPassWords * 8 + kGuard;                           // tile position 0
   // output staging tile: 1024-byte aligned (the period of the 128-byte swizzle)
   const uintptr_t tiles0 = (reinterpret_cast<uintptr_t>(smem_raw + wp.warp_off + WARPS * kMiscBytes) + 1023) &
                            ~uintptr_t(1023);
@@ -164,19 +164,15 @@ __global__ void __launch_bounds__(WARPS * 32, WARPS > 16 ? 1 : 32 / WARPS) k_dec
   unit_tiles(p, (uint64_t)blockIdx.x * WARPS + warp, (uint64_t)gridDim.x * WARPS, tw0, tw1);
   if (tw0 >= tw1) return;
 
-  // prologue: records of tw0, then its first words
-  uint32_t s = find_segment(p.segs, p.seg_begin, p.seg_end, tw0);
-  fetch_records(p, tw0, lane, rec);
-  cp_async_wait_all();
-  __syncwarp();
-  uint32_t pn = fetch_pass0(p, make_ctx(p, tw0, s, rec[0], rec[1]), lane, wbuf);
+  // prologue: where tile tw0 starts, then its first words
+  Ctx nxt = first_ctx(p, find_segment(p.segs, p.seg_begin, p.seg_end, tw0), tw0, lane);
+  uint32_t pn = fetch_pass0(p, nxt, lane, wbuf);
 
   for (uint64_t g = tw0; g < tw1; ++g) {
-    // ---- tile g: its records and first words have been requested
+    // ---- tile g: its first words have been requested
     cp_async_wait_all();
     __syncwarp();
-    while (g >= p.segs[s].tile_base + p.segs[s].n_tiles) ++s;
-    const Ctx cur = make_ctx(p, g, s, rec[0], rec[1]);
+    const Ctx cur = nxt;
     uint64_t w[kWPL];
     uint32_t n[kWPL];
 #pragma unroll
@@ -186,7 +182,6 @@ __global__ void __launch_bounds__(WARPS * 32, WARPS > 16 ? 1 : 32 / WARPS) k_dec
     }
     __syncwarp();
     const uint64_t g1 = g + 1;
-    if (g1 < tw1) fetch_records(p, g1, lane, rec);  // consumed after the decode
 
     const SegDev &sg = p.segs[cur.seg];
     const DomW dd = dw[sg.domain];
@@ -195,18 +190,16 @@ __global__ void __launch_bounds__(WARPS * 32, WARPS > 16 ? 1 : 32 / WARPS) k_dec
     const uint32_t nwin = left < (uint64_t)kT ? (uint32_t)left : (uint32_t)kT;
 
     // ---- 1. SymLen decode into the level bytes
+    TileEnd te{0u, 0u, 0u};
     if (cur.ok) {
-      const uint32_t bad = decode_tile(p, cur, dd, smem_raw, stage, lane, w, n);
-      if (bad && lane == 0) flag_bad(p.status, bad, sg.caller_index);
+      te = decode_tile(p, cur, nwin * kE, dd, smem_raw, stage, lane, w, n);
+      if (te.bad && lane == 0) flag_bad(p.status, te.bad, sg.caller_index);
     }
 
     // ---- first words of tile g + 1 (in flight during the transform)
     if (g1 < tw1) {
-      cp_async_wait_all();
-      __syncwarp();
-      uint32_t s1 = s;
-      while (g1 >= p.segs[s1].tile_base + p.segs[s1].n_tiles) ++s1;
-      pn = fetch_pass0(p, make_ctx(p, g1, s1, rec[0], rec[1]), lane, wbuf);
+      nxt = next_ctx(p, g, cur.seg, cur, te);
+      pn = fetch_pass0(p, nxt, lane, wbuf);
     }
     __syncwarp();
 

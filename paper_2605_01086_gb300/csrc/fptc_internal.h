@@ -84,7 +84,7 @@ struct IndexParams {
   uint64_t chunk_begin, chunk_end;  // chunk range of this launch
   uint32_t seg_begin, seg_end;      // segment range of this launch
   uint32_t grid;                    // CTAs of the chunk kernels (0: a default)
-  uint32_t pad;
+  uint32_t records;                 // 1: write a TileRec per tile (the kernels that read one)
 };
 
 struct DecodeParams {
@@ -98,6 +98,7 @@ struct DecodeParams {
   const uint16_t *luts;
   const float *basis;
   const TileRec *tiles;
+  const uint64_t *chunk_off;      // index chunk offsets (the warp-tile kernels locate their first tile)
   const uint32_t *seg_bad;
   DevStatus *status;
   uint64_t tile_begin, tile_end;  // tile range of this launch

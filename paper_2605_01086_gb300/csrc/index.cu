@@ -13,20 +13,15 @@
 //
 // Kernels 1 and 3 run one warp per chunk over a contiguous chunk range per
 // warp (the segment cursor advances with the chunk index, so no per-chunk
-// table is read).  A segment's symlen bytes are cut at 16-byte boundaries of
-// the address space: with A the first boundary at or after the segment's
-// first byte, block b covers [A + 16 b, A + 16 b + 16), b >= -1, and chunk k
-// is blocks 31 k - 1 .. 31 k + 29, one per lane (lane 31 idles).  Every block
-// but the segment's first and last lies inside the segment and is read with
-// one 16-byte load; those two are read byte by byte, so nothing outside the
-// segment is read.  The next chunk's block is loaded while the current one is
-// reduced.
-#include "fptc_internal.h"
+// table is read), with the next chunks' blocks loaded while the current ones
+// are reduced; the chunk geometry is that of symlen_chunks.cuh.  Kernel 3 runs
+// only for the kernels that read a record per tile: the warp-tile kernels
+// locate the first tile of their range from the chunk offsets
+// (symbol_word) and every later one from the tile decoded before it.
+#include "symlen_chunks.cuh"
 
 namespace fptc {
 namespace {
-
-static_assert(kChunkWords == 31 * 16, "a chunk is 31 blocks of 16 bytes");
 
 __device__ __forceinline__ void flag_bad(DevStatus *st, unsigned int flag, uint32_t caller_index) {
   atomicOr(&st->flags, flag);
@@ -45,48 +40,6 @@ __device__ __forceinline__ uint32_t chunk_segment(const SegDev *segs, uint32_t l
   return lo;
 }
 
-// A lane's view of one chunk: its 16 symlen bytes (zero outside the segment)
-// and the global word index of byte 0 of its block.
-struct LaneBlock {
-  uint4 v;
-  uint64_t word0;
-};
-
-// Block 31 k - 1 + lane of segment sg (lane < 31).
-__device__ __forceinline__ LaneBlock load_block(const uint8_t *symlen, const SegDev &sg, uint64_t k, uint32_t lane) {
-  LaneBlock r;
-  const uintptr_t a0 = reinterpret_cast<uintptr_t>(symlen + sg.word_offset);
-  const uintptr_t a1 = a0 + sg.n_words;
-  const uintptr_t blk = ((a0 + 15) & ~uintptr_t(15)) + 16 * (uintptr_t)(31 * k + lane) - 16;
-  r.word0 = sg.word_offset + (uint64_t)(blk - a0);  // wraps below word_offset for block -1 (masked bytes)
-  if (lane < 31 && blk >= a0 && blk + 16 <= a1) {
-    r.v = __ldg(reinterpret_cast<const uint4 *>(blk));
-  } else {
-    uint32_t w[4] = {0u, 0u, 0u, 0u};
-    if (lane < 31 && blk + 16 > a0 && blk < a1) {  // the segment's first or last block
-#pragma unroll
-      for (int j = 0; j < 16; ++j) {
-        const uintptr_t a = blk + j;
-        if (a >= a0 && a < a1) w[j >> 2] |= (uint32_t)__ldg(reinterpret_cast<const uint8_t *>(a)) << (8 * (j & 3));
-      }
-    }
-    r.v = make_uint4(w[0], w[1], w[2], w[3]);
-  }
-  return r;
-}
-
-__device__ __forceinline__ uint32_t block_sum(const uint4 &v) {
-  uint32_t s = __dp4a(v.x, 0x01010101u, 0u);
-  s = __dp4a(v.y, 0x01010101u, s);
-  s = __dp4a(v.z, 0x01010101u, s);
-  return __dp4a(v.w, 0x01010101u, s);
-}
-
-__device__ __forceinline__ bool block_over64(const uint4 &v) {
-  const uint32_t t = 0x40404040u;
-  return (__vcmpgtu4(v.x, t) | __vcmpgtu4(v.y, t) | __vcmpgtu4(v.z, t) | __vcmpgtu4(v.w, t)) != 0u;
-}
-
 // This warp's chunk range [c0, c1) of the launch.
 __device__ __forceinline__ void warp_chunks(const IndexParams &p, uint64_t &c0, uint64_t &c1) {
   const uint64_t gw = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -96,23 +49,51 @@ __device__ __forceinline__ void warp_chunks(const IndexParams &p, uint64_t &c0, 
   c1 = p.chunk_begin + n * (gw + 1) / nw;
 }
 
-__global__ void __launch_bounds__(256) k_chunk_count(IndexParams p) {
+// Chunks in flight per warp: the loads of the next group of chunks are issued
+// before the current group is reduced (four for the chunk sums, two for the
+// tile index, whose group holds more state).
+
+// Symlen blocks of chunks c .. c + P - 1 (clipped to c1) with their segments;
+// the segment cursor s advances monotonically.
+template <int P>
+struct ChunkGroup {
+  uint4 v[P];
+  uint32_t seg[P];
+};
+template <int P>
+__device__ __forceinline__ void load_group(const IndexParams &p, uint64_t c, uint64_t c1, uint32_t lane, uint32_t &s,
+                                           ChunkGroup<P> &g) {
+#pragma unroll
+  for (int i = 0; i < P; ++i) {
+    g.v[i] = make_uint4(0u, 0u, 0u, 0u);
+    g.seg[i] = s;
+    if (c + i < c1) {
+      while (c + i >= p.segs[s].chunk_base + p.segs[s].n_chunks) ++s;
+      g.seg[i] = s;
+      g.v[i] = load_block(p.symlen, p.segs[s], c + i - p.segs[s].chunk_base, lane).v;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256, 4) k_chunk_count(IndexParams p) {
   const uint32_t lane = threadIdx.x & 31;
   uint64_t c0, c1;
   warp_chunks(p, c0, c1);
   if (c0 >= c1) return;
   uint32_t s = chunk_segment(p.segs, p.seg_begin, p.seg_end, c0);
-  while (c0 >= p.segs[s].chunk_base + p.segs[s].n_chunks) ++s;
-  LaneBlock cur = load_block(p.symlen, p.segs[s], c0 - p.segs[s].chunk_base, lane);
-  for (uint64_t c = c0; c < c1; ++c) {
-    LaneBlock nxt{make_uint4(0u, 0u, 0u, 0u), 0};
-    if (c + 1 < c1) {
-      while (c + 1 >= p.segs[s].chunk_base + p.segs[s].n_chunks) ++s;
-      nxt = load_block(p.symlen, p.segs[s], c + 1 - p.segs[s].chunk_base, lane);
+  constexpr int kPipe = 4;
+  ChunkGroup<kPipe> cur;
+  load_group(p, c0, c1, lane, s, cur);
+  for (uint64_t c = c0; c < c1; c += kPipe) {
+    ChunkGroup<kPipe> nxt;
+    load_group(p, c + kPipe, c1, lane, s, nxt);
+#pragma unroll
+    for (int i = 0; i < kPipe; ++i) {
+      if (c + i >= c1) break;
+      const uint32_t sum = __reduce_add_sync(0xffffffffu, block_sum(cur.v[i]));
+      const uint32_t bad = __reduce_or_sync(0xffffffffu, block_over64(cur.v[i]) ? 1u : 0u);
+      if (lane == 0) p.chunk_sum[c + i] = bad ? kChunkBad : sum;
     }
-    const uint32_t sum = __reduce_add_sync(0xffffffffu, block_sum(cur.v));
-    const uint32_t bad = __reduce_or_sync(0xffffffffu, block_over64(cur.v) ? 1u : 0u);
-    if (lane == 0) p.chunk_sum[c] = bad ? kChunkBad : sum;
     cur = nxt;
   }
 }
@@ -151,65 +132,72 @@ __global__ void __launch_bounds__(256) k_segment_scan(IndexParams p) {
   }
 }
 
-__global__ void __launch_bounds__(256) k_tile_index(IndexParams p) {
+__global__ void __launch_bounds__(256, 3) k_tile_index(IndexParams p) {
   const uint32_t lane = threadIdx.x & 31;
   uint64_t c0, c1;
   warp_chunks(p, c0, c1);
   if (c0 >= c1) return;
   uint32_t s = chunk_segment(p.segs, p.seg_begin, p.seg_end, c0);
-  while (c0 >= p.segs[s].chunk_base + p.segs[s].n_chunks) ++s;
-  LaneBlock cur = load_block(p.symlen, p.segs[s], c0 - p.segs[s].chunk_base, lane);
-  uint64_t off_cur = p.chunk_off[c0];
-  uint32_t scur = s;
-  for (uint64_t c = c0; c < c1; ++c) {
-    LaneBlock nxt{make_uint4(0u, 0u, 0u, 0u), 0};
-    uint64_t off_nxt = 0;
-    uint32_t snxt = s;
-    if (c + 1 < c1) {
-      while (c + 1 >= p.segs[s].chunk_base + p.segs[s].n_chunks) ++s;
-      snxt = s;
-      nxt = load_block(p.symlen, p.segs[s], c + 1 - p.segs[s].chunk_base, lane);
-      off_nxt = p.chunk_off[c + 1];
-    }
-    if (p.seg_bad[scur] == 0) {  // uniform over the warp
-      const SegDev &sg = p.segs[scur];
+  constexpr int kPipe = 2;
+  ChunkGroup<kPipe> cur;
+  load_group(p, c0, c1, lane, s, cur);
+  uint64_t off_cur[kPipe];
+#pragma unroll
+  for (int i = 0; i < kPipe; ++i) off_cur[i] = c0 + i < c1 ? p.chunk_off[c0 + i] : 0;
+  for (uint64_t c = c0; c < c1; c += kPipe) {
+    ChunkGroup<kPipe> nxt;
+    load_group(p, c + kPipe, c1, lane, s, nxt);
+    uint64_t off_nxt[kPipe];
+#pragma unroll
+    for (int i = 0; i < kPipe; ++i) off_nxt[i] = c + kPipe + i < c1 ? p.chunk_off[c + kPipe + i] : 0;
+#pragma unroll
+    for (int i = 0; i < kPipe; ++i) {
+      if (c + i >= c1) break;
+      const uint32_t si = cur.seg[i];
+      if (p.seg_bad[si] != 0) continue;  // uniform over the warp
+      const SegDev &sg = p.segs[si];
       const DomainDev &dm = p.domains[sg.domain];
       const uint64_t te = (uint64_t)dm.tile_windows * dm.E;  // symbols per tile
-      const uint32_t tsum = block_sum(cur.v);
+      const uint4 bv = cur.v[i];
+      const uint32_t tsum = block_sum(bv);
       uint32_t x = tsum;
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
         const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
         if (lane >= (uint32_t)o) x += y;
       }
-      if (tsum) {
-        uint64_t off = off_cur + (x - tsum);  // symbol offset (in the segment) of the block's first word
-        // first tile whose start is >= off
-        uint64_t tn = off < 0xFFFFFFFFull && te < 0xFFFFFFFFull ? ((uint32_t)off + (uint32_t)te - 1u) / (uint32_t)te
-                                                                  : (off + te - 1) / te;
-        uint64_t ns = tn * te;
-        const uint32_t wv[4] = {cur.v.x, cur.v.y, cur.v.z, cur.v.w};
+      if (tsum == 0) continue;
+      uint64_t off = off_cur[i] + (x - tsum);  // symbol offset (in the segment) of the block's first word
+      // first tile whose start is >= off
+      uint64_t tn = off < 0xFFFFFFFFull && te < 0xFFFFFFFFull ? ((uint32_t)off + (uint32_t)te - 1u) / (uint32_t)te
+                                                                : (off + te - 1) / te;
+      uint64_t ns = tn * te;
+      if (ns >= off + tsum) continue;  // most blocks hold no tile start (a tile is thousands of symbols)
+      const uint32_t wv[4] = {bv.x, bv.y, bv.z, bv.w};
+      // global word index of byte 0 of this lane's block (as load_block computes it)
+      const uintptr_t a0 = reinterpret_cast<uintptr_t>(p.symlen + sg.word_offset);
+      const uint64_t word0 = sg.word_offset + (uint64_t)(((a0 + 15) & ~uintptr_t(15)) +
+                                                         16 * (uintptr_t)(31 * (c + i - sg.chunk_base) + lane) - 16 - a0);
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          const uint64_t end = off + ((wv[j >> 2] >> (8 * (j & 3))) & 0xffu);
-          while (ns < end) {
-            if (tn < sg.n_tiles) {
-              TileRec r;
-              r.first_word = cur.word0 + j;
-              r.skip = (uint32_t)(ns - off);
-              r.pad = 0;
-              p.tiles[sg.tile_base + tn] = r;
-            }
-            ++tn;
-            ns += te;
+      for (int j = 0; j < 16; ++j) {
+        const uint64_t end = off + ((wv[j >> 2] >> (8 * (j & 3))) & 0xffu);
+        while (ns < end) {
+          if (tn < sg.n_tiles) {
+            TileRec r;
+            r.first_word = word0 + j;
+            r.skip = (uint32_t)(ns - off);
+            r.pad = 0;
+            p.tiles[sg.tile_base + tn] = r;
           }
-          off = end;
+          ++tn;
+          ns += te;
         }
+        off = end;
       }
     }
     cur = nxt;
-    off_cur = off_nxt;
-    scur = snxt;
+#pragma unroll
+    for (int i = 0; i < kPipe; ++i) off_cur[i] = off_nxt[i];
   }
 }
 
@@ -257,7 +245,7 @@ cudaError_t launch_index(const IndexParams &p, cudaStream_t stream) {
   if (n_chunks > 0) k_chunk_count<<<grid, 256, 0, stream>>>(p);
   const uint64_t warps_threads = (uint64_t)n_segs * 32;
   k_segment_scan<<<(unsigned)((warps_threads + 255) / 256), 256, 0, stream>>>(p);
-  if (n_chunks > 0) k_tile_index<<<grid, 256, 0, stream>>>(p);
+  if (n_chunks > 0 && p.records) k_tile_index<<<grid, 256, 0, stream>>>(p);
   return cudaGetLastError();
 }
 

@@ -207,6 +207,7 @@ extern "C" fptc_status fptc_decode_stream_noalloc(const fptc_domain *domain, con
   ip.seg_begin = 0;
   ip.seg_end = 1;
   ip.grid = 0;
+  ip.records = 1;
   e = launch_index(ip, s);
   if (e != cudaSuccess) {
     set_error("allocation-free index launch: %s", cudaGetErrorString(e));
@@ -223,6 +224,7 @@ extern "C" fptc_status fptc_decode_stream_noalloc(const fptc_domain *domain, con
   dp.luts = reinterpret_cast<const uint16_t *>(scr + kOffLut);
   dp.basis = reinterpret_cast<const float *>(scr + kOffBasis);
   dp.tiles = ip.tiles;
+  dp.chunk_off = ip.chunk_off;
   dp.seg_bad = ip.seg_bad;
   dp.status = ip.status;
   dp.tile_begin = 0;

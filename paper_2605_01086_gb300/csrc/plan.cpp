@@ -289,8 +289,11 @@ fptc_status upload_layout(fptc_plan *p) {
   return FPTC_OK;
 }
 
-IndexParams index_params(const fptc_plan *p, const uint8_t *d_symlen) {
+// records: a TileRec per tile for kernels that read one (the warp-tile kernels
+// locate their tiles from the chunk offsets and need none).
+IndexParams index_params(const fptc_plan *p, const uint8_t *d_symlen, bool records) {
   IndexParams ip{};
+  ip.records = records ? 1u : 0u;
   ip.symlen = d_symlen;
   ip.segs = p->d_segs;
   ip.domains = p->d_domains;
@@ -307,6 +310,12 @@ IndexParams index_params(const fptc_plan *p, const uint8_t *d_symlen) {
   return ip;
 }
 
+// Whether the plan's forward decode reads a record per tile.
+bool needs_records(const fptc_plan *p) {
+  return !(p->kind == FPTC_KERNEL_WARP_TILE || p->kind == FPTC_KERNEL_TENSOR) ||
+         p->opts.schedule == FPTC_SCHEDULE_THREE_KERNEL;
+}
+
 DecodeParams decode_params(const fptc_plan *p, const uint64_t *d_words, const uint8_t *d_symlen, float *d_out,
                            uint8_t *d_levels, const float *d_scale) {
   DecodeParams dp{};
@@ -320,6 +329,7 @@ DecodeParams decode_params(const fptc_plan *p, const uint64_t *d_words, const ui
   dp.luts = p->d_luts;
   dp.basis = p->d_basis;
   dp.tiles = p->d_tiles;
+  dp.chunk_off = p->d_chunk_off;
   dp.seg_bad = p->d_seg_bad;
   dp.status = p->d_status;
   dp.tile_begin = 0;
@@ -764,7 +774,7 @@ fptc_status fptc_decode_stages(fptc_plan *p, const uint64_t *d_words, const uint
   DeviceGuard g(p->device);
   if (!g.ok) return cuda_fail(cudaGetLastError(), "set device");
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  const IndexParams ip = index_params(p, d_symlen);
+  const IndexParams ip = index_params(p, d_symlen, needs_records(p));
   const DecodeParams dp = decode_params(p, d_words, d_symlen, d_out, d_levels, d_scale);
   cudaError_t e = cudaSuccess;
   if (p->opts.schedule != FPTC_SCHEDULE_PER_SEGMENT) {
@@ -803,7 +813,7 @@ fptc_status fptc_decode_backward(fptc_plan *p, const uint64_t *d_words, const ui
   if (e != cudaSuccess) return cuda_fail(e, "zero grad_scale");
   if (p->segs.empty()) return FPTC_OK;
   if (redecode) {
-    e = launch_index(index_params(p, d_symlen), s);
+    e = launch_index(index_params(p, d_symlen, !p->b_warp), s);
     if (e != cudaSuccess) return cuda_fail(e, "index launch");
   }
   BackwardParams bp{};
@@ -850,7 +860,7 @@ fptc_status fptc_decode_host(fptc_plan *p, const uint64_t *h_words, const uint8_
     if (e == cudaSuccess) e = cudaMemcpyAsync(d_symlen, h_symlen, p->words_extent, cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return cuda_fail(e, "copy to device");
   }
-  const IndexParams ip = index_params(p, d_symlen);
+  const IndexParams ip = index_params(p, d_symlen, needs_records(p));
   const DecodeParams dp = decode_params(p, d_words, d_symlen, d_out, nullptr, nullptr);
   e = launch_index(ip, s);
   if (e == cudaSuccess && p->opts.schedule == FPTC_SCHEDULE_THREE_KERNEL) e = launch_word_offsets(ip, p->d_word_off, s);

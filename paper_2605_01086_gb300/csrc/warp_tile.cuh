@@ -3,12 +3,17 @@
 // N = 32, E = 16: tile constants, per-domain tables in shared memory, the
 // SymLen word decoder, tile contexts and their asynchronous prefetch, the
 // per-window dequantization, and the TMA store of 32-window output tiles.
-// Included inside an anonymous namespace by each kernel file.
+//
+// Each warp decodes a contiguous range of tiles.  The first tile of the range
+// is located from the index's chunk offsets (symbol_word); every later tile of
+// a segment starts at the word where the tile before it ended, which the SymLen
+// decode of that tile finds anyway, so no record per tile is read.
 #pragma once
 
 #include <cuda.h>
 
 #include "device_util.cuh"
+#include "symlen_chunks.cuh"
 
 namespace fptc {
 namespace wt {
@@ -24,7 +29,7 @@ constexpr int kWPL = 2;                    // consecutive words per lane per dec
 constexpr int kPassWords = 32 * kWPL;
 constexpr int kStepWin = 32;               // windows per transform step (one per lane)
 constexpr int kOutTile = kStepWin * kN * 4;  // bytes of a step's output (TMA box 32 x 32 floats)
-constexpr int kMiscBytes = kPassWords * 8 + 32 + kStage;  // per warp: first-pass words, records, levels
+constexpr int kMiscBytes = kPassWords * 8 + kStage;  // per warp: first-pass words, level bytes
 // zone mask of Table 1 (B1 = 2, B2 = 16): bins 0, 1 in zone 0, the rest in zone 1
 constexpr uint32_t kZmaskTable1 = 0x55555550u;
 
@@ -91,8 +96,8 @@ __device__ __forceinline__ uint32_t decode_word(uint64_t w, uint32_t n, uint8_t 
   return ((hi | lo | mk) == 0u ? kFlagBitOverrun : 0u) | ((CHECKED && low == 0u) ? kFlagInvalidCode : 0u);
 }
 
-// Where a tile's words are (first word, count, codewords of the first word
-// that belong to the previous tile) and its segment.
+// Where a tile's words are (first word, words that may belong to it, codewords
+// of the first word that belong to the previous tile) and its segment.
 struct Ctx {
   uint64_t fw;
   uint32_t nw;
@@ -101,22 +106,48 @@ struct Ctx {
   uint32_t ok;  // 0: segment flagged by the index, or no tile
 };
 
-__device__ __forceinline__ Ctx make_ctx(const DecodeParams &p, uint64_t g, uint32_t s, const TileRec &r,
-                                        const TileRec &rn) {
-  Ctx c{0, 0, 0, s, 0};
-  const SegDev &sg = p.segs[s];
+// Context of a tile of segment s starting at word fw after `skip` symbols.  A
+// tile holds at most kTS symbols and every word of a valid stream at least
+// one, so it spans at most kTS + 1 words (fewer at the segment's end).
+__device__ __forceinline__ Ctx make_ctx(const DecodeParams &p, uint32_t s, uint64_t fw, uint32_t skip) {
+  Ctx c{fw, 0, skip, s, 0};
   if (p.seg_bad[s] != 0) return c;
-  const uint64_t tin = g - sg.tile_base;
-  c.fw = r.first_word;
-  c.skip = r.skip;
-  uint64_t lw;
-  if (tin + 1 < sg.n_tiles)
-    lw = rn.first_word - (rn.skip == 0 ? 1u : 0u);
-  else
-    lw = sg.word_offset + sg.n_words - 1;
-  c.nw = lw >= c.fw ? (uint32_t)(lw - c.fw + 1) : 0u;
+  const SegDev &sg = p.segs[s];
+  const uint64_t end = sg.word_offset + sg.n_words;
+  c.nw = fw < end ? (uint32_t)min(end - fw, (uint64_t)kTS + 1u) : 0u;
   c.ok = 1;
   return c;
+}
+
+// Context of tile g of segment s located from the index (warp-collective).
+__device__ __forceinline__ Ctx first_ctx(const DecodeParams &p, uint32_t s, uint64_t g, uint32_t lane) {
+  const SegDev &sg = p.segs[s];
+  if (p.seg_bad[s] != 0) return Ctx{0, 0, 0, s, 0};
+  const uint64_t tin = g - sg.tile_base;
+  if (tin == 0) return make_ctx(p, s, sg.word_offset, 0u);
+  const TileRec r = symbol_word(p.symlen, p.chunk_off, sg, tin * (uint64_t)kTS, lane);
+  if (r.pad != 0) return Ctx{0, 0, 0, s, 0};
+  return make_ctx(p, s, r.first_word, r.skip);
+}
+
+// Where a decoded tile ended: the word (from the tile's first word) holding
+// the next tile's first symbol and the symbols of it that were this tile's.
+struct TileEnd {
+  uint32_t bad;  // error flags (OR over the warp)
+  uint32_t word;
+  uint32_t skip;
+};
+
+// Context of tile g + 1 after tile g (segment s, context cur) ended at e.
+__device__ __forceinline__ Ctx next_ctx(const DecodeParams &p, uint64_t g, uint32_t s, const Ctx &cur,
+                                        const TileEnd &e) {
+  if (g + 1 < p.segs[s].tile_base + p.segs[s].n_tiles) {
+    if (!cur.ok) return Ctx{0, 0, 0, s, 0};
+    return make_ctx(p, s, cur.fw + e.word, e.skip);
+  }
+  uint32_t s1 = s + 1;
+  while (g + 1 >= p.segs[s1].tile_base + p.segs[s1].n_tiles) ++s1;  // segments without tiles
+  return make_ctx(p, s1, p.segs[s1].word_offset, 0u);
 }
 
 // Words i0 + kWPL lane + u (u < kWPL) of a tile (zero beyond its word count).
@@ -147,12 +178,6 @@ __device__ __forceinline__ void cp_async16(void *dst, const void *src) {
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
-
-// Records of tiles g and g + 1 into rec[0..1] (lanes 0 and 1).
-__device__ __forceinline__ void fetch_records(const DecodeParams &p, uint64_t g, uint32_t lane, TileRec *rec) {
-  if (lane < 2 && g + lane < p.tile_end) cp_async16(rec + lane, p.tiles + g + lane);
-  cp_async_commit();
-}
 
 // First pass of a tile: words kWPL lane + u into wbuf (copies), their symbol
 // counts packed one per byte into a register (zero beyond the tile's words).
@@ -216,30 +241,22 @@ __device__ __forceinline__ uint32_t load_domain_tables(const DecodeParams &p, ui
   return off;
 }
 
-// SymLen decode of one tile (Sec. 4.2.1) into the level bytes at stage[0..):
-// passes of two consecutive words per lane, a warp scan of their symbol
-// counts, the codewords of each word at their tile positions (those of the
-// previous tile, and after the tile's last symbol, go to the guards).  w/n
-// hold the first pass's words; later passes are loaded one pass ahead.
-// Returns the OR of the error flags over the warp.
-__device__ __forceinline__ uint32_t decode_tile(const DecodeParams &p, const Ctx &cur, const DomW &dd,
-                                                const unsigned char *smem, uint8_t *stage, uint32_t lane,
-                                                uint64_t (&w)[kWPL], uint32_t (&n)[kWPL]) {
+// SymLen decode of one tile of `te` symbols (Sec. 4.2.1) into the level bytes
+// at stage[0..): passes of two consecutive words per lane, a warp scan of their
+// symbol counts, the codewords of each word at their tile positions (those of
+// the previous tile go to the guard before the tile, those after the tile's
+// last symbol to the guard after it).  The pass whose scan reaches te is the
+// last: its words that start at or after te are left to the next tile, and the
+// word holding symbol te is where the next tile starts.  w/n hold the first
+// pass's words; each later pass is loaded while the one before it decodes.
+__device__ __forceinline__ TileEnd decode_tile(const DecodeParams &p, const Ctx &cur, uint32_t te, const DomW &dd,
+                                               const unsigned char *smem, uint8_t *stage, uint32_t lane,
+                                               uint64_t (&w)[kWPL], uint32_t (&n)[kWPL]) {
   const uint16_t *lut = reinterpret_cast<const uint16_t *>(smem + dd.lut_off);
   int32_t base = -(int32_t)cur.skip;
   uint32_t bad = 0;
+  TileEnd r{0u, 0u, 0u};
   for (uint32_t c0 = 0; c0 < cur.nw; c0 += kPassWords) {
-    uint64_t xw[kWPL];
-    uint32_t xn[kWPL];
-    if (c0 + kPassWords < cur.nw) {
-      load_pass(p, cur, c0 + kPassWords, lane, xw, xn);
-    } else {
-#pragma unroll
-      for (int u = 0; u < kWPL; ++u) {
-        xw[u] = 0;
-        xn[u] = 0;
-      }
-    }
     uint32_t tot = 0;
 #pragma unroll
     for (int u = 0; u < kWPL; ++u) tot += n[u];
@@ -250,7 +267,44 @@ __device__ __forceinline__ uint32_t decode_tile(const DecodeParams &p, const Ctx
       if (lane >= (uint32_t)o) x += y;
     }
     const uint32_t total = __shfl_sync(0xffffffffu, x, 31);
-    uint8_t *dst = stage + base + (int32_t)(x - tot);
+    const int32_t p0 = base + (int32_t)(x - tot);  // tile position of this lane's first symbol
+    const bool last = base + (int32_t)total >= (int32_t)te;
+    uint64_t xw[kWPL];
+    uint32_t xn[kWPL];
+    if (!last && c0 + kPassWords < cur.nw) {
+      load_pass(p, cur, c0 + kPassWords, lane, xw, xn);
+    } else {
+#pragma unroll
+      for (int u = 0; u < kWPL; ++u) {
+        xw[u] = 0;
+        xn[u] = 0;
+      }
+    }
+    if (last) {
+      uint32_t hit = 0u, hw = 0u, hs = 0u;
+      int32_t q = p0;
+#pragma unroll
+      for (int u = 0; u < kWPL; ++u) {
+        const int32_t qe = q + (int32_t)n[u];
+        if (!hit && q <= (int32_t)te && (int32_t)te < qe) {
+          hit = 1u;
+          hw = c0 + kWPL * lane + u;
+          hs = (uint32_t)((int32_t)te - q);
+        }
+        if (q >= (int32_t)te) n[u] = 0u;
+        q = qe;
+      }
+      const uint32_t m = __ballot_sync(0xffffffffu, hit);
+      if (m) {
+        const uint32_t src = (uint32_t)(__ffs(m) - 1);
+        r.word = __shfl_sync(0xffffffffu, hw, src);
+        r.skip = __shfl_sync(0xffffffffu, hs, src);
+      } else {  // the tile ends with this pass's last word
+        r.word = c0 + kPassWords;
+        r.skip = 0u;
+      }
+    }
+    uint8_t *dst = stage + p0;
     if (dd.complete) {
 #pragma unroll
       for (int u = 0; u < kWPL; ++u) {
@@ -264,6 +318,7 @@ __device__ __forceinline__ uint32_t decode_tile(const DecodeParams &p, const Ctx
         dst += n[u];
       }
     }
+    if (last) break;
     base += (int32_t)total;
 #pragma unroll
     for (int u = 0; u < kWPL; ++u) {
@@ -271,7 +326,8 @@ __device__ __forceinline__ uint32_t decode_tile(const DecodeParams &p, const Ctx
       n[u] = xn[u];
     }
   }
-  return __reduce_or_sync(0xffffffffu, bad);
+  r.bad = __reduce_or_sync(0xffffffffu, bad);
+  return r;
 }
 
 // The 16 coefficients A_z * unit_z(level) of a window from its 16 level bytes

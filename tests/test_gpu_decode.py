@@ -255,6 +255,47 @@ def test_corrupt_segment_is_flagged_and_confined(case, kernel):
     assert plan.device_status()[0] == 0
 
 
+@pytest.mark.parametrize("form", ["warp_tile", "tensor"])
+def test_tile_chain_across_rejected_segment(form):
+    """Every warp decodes a run of consecutive tiles, each starting where the one
+    before it ended; a segment the index rejects inside such a run is skipped and
+    the tiles after it still start at the right words."""
+    from paper_2605_01086_gb300 import _lib
+    b = encode_workload(siggen.mixed_10000_logu(n=48, lo=100000, hi=200000))
+    bad = 20
+    b.symlen[int(b.word_off[bad]) + 7] -= 1
+    opts = dict(kernel="warp_tile") if form == "warp_tile" else dict(idct="bf16x3")
+    plan = make_plan(b, threads=128, ctas_per_sm=1, **opts)
+    warps = plan.info["grid"] * 4
+    assert plan.info["n_tiles"] >= 2 * warps
+    w, s = plan.to_device(b.words, b.symlen)
+    out = plan.empty_out().fill_(float("nan"))
+    lv = torch.empty(plan.info["n_levels_total"], dtype=torch.uint8, device=plan.device)
+    plan.decode(w, s, out=out, levels=lv)
+    st, flags, first = plan.device_status()
+    assert st == _lib.CORRUPT_STREAM and flags & _lib.FLAG_SYMBOL_COUNT and first == bad
+    good = [i for i in range(b.n_streams) if i != bad]
+    compare_with_oracle(plan, b, out, lv, idx=good, tol=FP32_REL_L2 if form == "warp_tile" else 2e-5)
+
+
+def test_adjoint_redecode_chains_tiles():
+    """The adjoint decoding the levels again, several tiles per warp: the same
+    coefficient gradients as from the saved levels."""
+    b = encode_workload(siggen.power_1024x65536(n=320, S=65536))
+    plan = make_plan(b)
+    w, s, out, lv = gpu_decode(plan, b)
+    gx = torch.randn(out.numel(), generator=torch.Generator().manual_seed(5)).to(plan.device) * 1e-3
+    gco = torch.empty(plan.info["n_levels_total"], dtype=torch.float32, device=plan.device)
+    gco2 = torch.empty_like(gco)
+    gsc, _ = plan.backward(gx, levels=lv, grad_coeffs=gco)
+    gsc2, _ = plan.backward(gx, words=w, symlen=s, grad_coeffs=gco2)
+    torch.cuda.synchronize()
+    assert plan.info["n_tiles"] >= 2 * plan.info["sm_count"] * 16
+    assert torch.equal(gco, gco2)
+    assert torch.allclose(gsc, gsc2, rtol=1e-12, atol=0)
+    assert plan.device_status()[0] == 0
+
+
 def test_invalid_code_is_flagged():
     from paper_2605_01086_gb300 import _lib
     cl = np.zeros(256, np.uint8)
