@@ -122,20 +122,27 @@ __device__ __forceinline__ void idct32(const float (&c)[16], Put put) {
   }
 }
 
-// A window whose output is not 32-byte aligned or that ends the segment
-// (m < 32 samples): 16-byte or scalar stores.  Kept out of line.
-__device__ __noinline__ void idct32_store_slow(const float (&c)[16], float *dst, uint32_t m, uint32_t vec16) {
-  if (m == kN && vec16) {
-    idct32(c, [&](int b, const float(&v)[8]) {
-      __stcs(reinterpret_cast<float4 *>(dst + 8 * b), make_float4(v[0], v[1], v[2], v[3]));
-      __stcs(reinterpret_cast<float4 *>(dst + 8 * b) + 1, make_float4(v[4], v[5], v[6], v[7]));
-    });
-  } else {
-    idct32(c, [&](int b, const float(&v)[8]) {
+// One window's 32 samples from row `lane` of the staging tile (16-byte chunk
+// c at c ^ (lane & 7)) to dst: m samples, 32-byte or 16-byte streaming stores
+// where the alignment allows.
+__device__ __forceinline__ void store_row(const unsigned char *row, uint32_t sx, float *dst, uint32_t m, bool vec32,
+                                          bool vec16) {
+  if (m == kN && (vec32 || vec16)) {
 #pragma unroll
-      for (int i = 0; i < 8; ++i)
-        if ((uint32_t)(8 * b + i) < m) dst[8 * b + i] = v[i];
-    });
+    for (int b = 0; b < 4; ++b) {
+      const float4 u = *reinterpret_cast<const float4 *>(row + (((2 * b) ^ sx) << 4));
+      const float4 v = *reinterpret_cast<const float4 *>(row + (((2 * b + 1) ^ sx) << 4));
+      if (vec32) {
+        const float x[8] = {u.x, u.y, u.z, u.w, v.x, v.y, v.z, v.w};
+        st_cs_v8(dst + 8 * b, x);
+      } else {
+        __stcs(reinterpret_cast<float4 *>(dst + 8 * b), u);
+        __stcs(reinterpret_cast<float4 *>(dst + 8 * b) + 1, v);
+      }
+    }
+  } else {
+    for (uint32_t n = 0; n < m; ++n)
+      dst[n] = *reinterpret_cast<const float *>(row + ((((n >> 2) ^ sx) << 4) | ((n & 3u) << 2)));
   }
 }
 
@@ -217,36 +224,32 @@ __global__ void __launch_bounds__(WARPS * 32, WARPS > 16 ? 1 : 32 / WARPS) k_dec
         const uint32_t wi = w0 + lane;
         // all 32 windows of the step whole and inside the segment: one TMA store
         const bool tma_step = tma_seg && w0 + kStepWin <= nwin && (win0 + w0 + kStepWin) * kN <= S;
-        if (tma_step && tma_pending) {
-          if (lane == 0) tma_wait_read();  // the previous tile has left the staging buffer
+        if (tma_pending) {
+          if (lane == 0) tma_wait_read();  // the previous step has left the staging tile
           __syncwarp();
+          tma_pending = false;
         }
+        // row `lane` of the staging tile, 16-byte chunk c at c ^ (lane & 7)
+        unsigned char *const row = otile + lane * (kN * 4);
+        const uint32_t sx = lane & 7u;
         if (wi < nwin) {
           const uint4 sv = *reinterpret_cast<const uint4 *>(stage + wi * kE);
           float c[16];
           window_coefs(sv, deq, dd.zmask, c);
           if (want_lev) put_levels(lev + wi * kE, sv);
-          const uint64_t s0 = (win0 + wi) * kN;
-          float *const dst = out + s0;
-          if (tma_step) {
-            // row `lane` of the staging tile, 16-byte chunk c at c ^ (lane & 7)
-            unsigned char *const row = otile + lane * (kN * 4);
-            const uint32_t sx = lane & 7u;
-            idct32(c, [&](int b, const float(&v)[8]) {
-              *reinterpret_cast<float4 *>(row + (((2 * b) ^ sx) << 4)) = make_float4(v[0], v[1], v[2], v[3]);
-              *reinterpret_cast<float4 *>(row + (((2 * b + 1) ^ sx) << 4)) = make_float4(v[4], v[5], v[6], v[7]);
-            });
-          } else if (s0 + kN <= S && vec32) {
-            idct32(c, [&](int b, const float(&v)[8]) { st_cs_v8(dst + 8 * b, v); });
-          } else {
-            idct32_store_slow(c, dst, s0 + kN <= S ? kN : (uint32_t)(S - s0), aligned & 1u);
-          }
+          idct32(c, [&](int b, const float(&v)[8]) {
+            *reinterpret_cast<float4 *>(row + (((2 * b) ^ sx) << 4)) = make_float4(v[0], v[1], v[2], v[3]);
+            *reinterpret_cast<float4 *>(row + (((2 * b + 1) ^ sx) << 4)) = make_float4(v[4], v[5], v[6], v[7]);
+          });
         }
         if (tma_step) {
           fence_async_shared();
           __syncwarp();
           if (lane == 0) tma_store_rows(&out_map, otile, (int32_t)((sg.out_offset >> 5) + win0 + w0));
           tma_pending = true;
+        } else if (wi < nwin) {  // each lane stores its own row
+          const uint64_t s0 = (win0 + wi) * kN;
+          store_row(row, sx, out + s0, s0 + kN <= S ? kN : (uint32_t)(S - s0), vec32, aligned & 1u);
         }
       }
     }
