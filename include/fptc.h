@@ -186,9 +186,11 @@ fptc_status fptc_decode_batch(fptc_plan *plan, const uint64_t *d_words, const ui
                               uint8_t *d_levels, const float *d_scale, fptc_stream stream);
 
 /* The stages of fptc_decode_batch run separately, for per-stage timing:
- * FPTC_STAGE_INDEX runs the SymLen index kernels (symlen scan, tile starts),
- * FPTC_STAGE_DECODE the fused decode kernel, which reads the tile starts the
- * last index stage of this plan wrote (so d_symlen must be unchanged since).
+ * FPTC_STAGE_INDEX runs the SymLen index kernels (symlen scan into chunk
+ * offsets, symbol-count check, and for the block-tile and generic kernels the
+ * start of every tile), FPTC_STAGE_DECODE the fused decode kernel, which reads
+ * what the last index stage of this plan wrote (so d_symlen must be unchanged
+ * since).
  * stages = FPTC_STAGE_INDEX | FPTC_STAGE_DECODE is fptc_decode_batch. */
 #define FPTC_STAGE_INDEX 1u
 #define FPTC_STAGE_DECODE 2u
@@ -211,10 +213,14 @@ fptc_status fptc_decode_backward(fptc_plan *plan, const uint64_t *d_words, const
 
 /* End-to-end decode from host memory: copies h_words / h_symlen (words_extent
  * entries each) into the caller's device buffers, decodes, and copies the
- * samples of every segment back into h_out (out_extent floats).  The copies
- * are split in pieces and overlapped with decoding on `stream` and one
- * internal stream.  Host buffers should be page-locked for full speed.
- * Returns after h_out holds the result (it synchronizes). */
+ * samples of every segment back into h_out (out_extent floats).  The work is
+ * split in up to 16 pieces of about equal output in output order: a piece's
+ * words are uploaded on an internal stream, indexed and decoded on `stream`,
+ * and copied back on one of four internal streams, so uploads, decoding and
+ * copies back of different pieces overlap (when the words are not laid out in
+ * output order, every word is uploaded before the first piece decodes).  Host
+ * buffers should be page-locked for full speed.  Returns after h_out holds the
+ * result (it synchronizes). */
 fptc_status fptc_decode_host(fptc_plan *plan, const uint64_t *h_words, const uint8_t *h_symlen, float *h_out,
                              uint64_t *d_words, uint8_t *d_symlen, float *d_out, fptc_stream stream);
 

@@ -59,7 +59,10 @@ struct fptc_plan {
   static constexpr int kAux = 4;        // copy-back streams of the end-to-end decode
   static constexpr int kPieces = 16;    // decode pieces of the end-to-end decode
   cudaStream_t aux[kAux] = {};
-  cudaEvent_t ev[kPieces] = {};
+  cudaStream_t up = nullptr;            // upload stream of the end-to-end decode
+  cudaEvent_t ev[kPieces] = {};         // piece k decoded
+  cudaEvent_t evh[kPieces] = {};        // piece k's words uploaded
+  cudaEvent_t ev_start = nullptr;       // the caller's stream reached the end-to-end decode
 };
 
 namespace {
@@ -105,8 +108,12 @@ void free_device(fptc_plan *p) {
   cudaFree(p->d_status);
   for (auto &a : p->aux)
     if (a) cudaStreamDestroy(a);
+  if (p->up) cudaStreamDestroy(p->up);
   for (auto &e : p->ev)
     if (e) cudaEventDestroy(e);
+  for (auto &e : p->evh)
+    if (e) cudaEventDestroy(e);
+  if (p->ev_start) cudaEventDestroy(p->ev_start);
 }
 
 // Reconstruction at A_z = 1 (the inverse zone maps of Sec. 3.2), FP64 then FP32.
@@ -685,8 +692,12 @@ fptc_status fptc_plan_create(fptc_plan **out, int device, const fptc_domain *dom
     if (st == FPTC_OK) {
       for (auto &a : p->aux)
         if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&a, cudaStreamNonBlocking);
+      if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->up, cudaStreamNonBlocking);
       for (auto &v : p->ev)
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&v, cudaEventDisableTiming);
+      for (auto &v : p->evh)
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&v, cudaEventDisableTiming);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_start, cudaEventDisableTiming);
       if (e != cudaSuccess)
         st = cuda_fail(e, "plan streams");
     }
@@ -854,42 +865,78 @@ fptc_status fptc_decode_host(fptc_plan *p, const uint64_t *h_words, const uint8_
   DeviceGuard g(p->device);
   if (!g.ok) return cuda_fail(cudaGetLastError(), "set device");
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  cudaError_t e = cudaSuccess;
-  if (any_words) {
-    e = cudaMemcpyAsync(d_words, h_words, p->words_extent * 8, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(d_symlen, h_symlen, p->words_extent, cudaMemcpyHostToDevice, s);
-    if (e != cudaSuccess) return cuda_fail(e, "copy to device");
+  // Pieces of about equal output in queue (output) order.  Piece k's words go
+  // up on the upload stream, it is indexed and decoded on `stream` once they
+  // are there, and its samples go back on one of the copy-back streams, so
+  // uploads, decoding and copies back of different pieces overlap.
+  struct Piece {
+    uint32_t s0, s1;
+    uint64_t w0, w1;  // hull of the piece's words
+    uint64_t o0, o1;  // hull of its output
+  };
+  std::vector<Piece> pieces;
+  {
+    const uint32_t n = (uint32_t)p->segs.size();
+    const uint64_t per = (p->n_samples + fptc_plan::kPieces - 1) / fptc_plan::kPieces;
+    uint32_t s0 = 0;
+    while (s0 < n) {
+      uint32_t s1 = s0;
+      uint64_t acc = 0;
+      while (s1 < n && (acc < per || s1 == s0)) acc += p->segs[s1++].n_samples;
+      if (pieces.size() == fptc_plan::kPieces - 1) s1 = n;  // the last piece takes the rest
+      Piece pc{s0, s1, UINT64_MAX, 0, UINT64_MAX, 0};
+      for (uint32_t i = s0; i < s1; ++i) {
+        const SegDev &sg = p->segs[i];
+        if (sg.n_words) {
+          pc.w0 = std::min(pc.w0, sg.word_offset);
+          pc.w1 = std::max(pc.w1, sg.word_offset + sg.n_words);
+        }
+        if (sg.n_samples) {
+          pc.o0 = std::min(pc.o0, sg.out_offset);
+          pc.o1 = std::max(pc.o1, sg.out_offset + sg.n_samples);
+        }
+      }
+      pieces.push_back(pc);
+      s0 = s1;
+    }
   }
+  // uploads per piece only where the pieces' word hulls are disjoint and ascending
+  // (words laid out in output order); otherwise every word goes up first
+  bool split_up = true;
+  {
+    uint64_t end = 0;
+    for (const Piece &pc : pieces)
+      if (pc.w1 > pc.w0) {
+        split_up = split_up && pc.w0 >= end;
+        end = pc.w1;
+      }
+  }
+  auto upload = [&](uint64_t w0, uint64_t w1) -> cudaError_t {
+    if (w1 <= w0) return cudaSuccess;
+    cudaError_t r = cudaMemcpyAsync(d_words + w0, h_words + w0, (w1 - w0) * 8, cudaMemcpyHostToDevice, p->up);
+    if (r == cudaSuccess) r = cudaMemcpyAsync(d_symlen + w0, h_symlen + w0, w1 - w0, cudaMemcpyHostToDevice, p->up);
+    return r;
+  };
+  // the device buffers are the caller's: uploads start after the work already on `stream`
+  cudaError_t e = cudaEventRecord(p->ev_start, s);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(p->up, p->ev_start, 0);
+  if (e == cudaSuccess && any_words && !split_up) e = upload(0, p->words_extent);
+  if (e != cudaSuccess) return cuda_fail(e, "copy to device");
   const IndexParams ip = index_params(p, d_symlen, needs_records(p));
   const DecodeParams dp = decode_params(p, d_words, d_symlen, d_out, nullptr, nullptr);
-  e = launch_index(ip, s);
-  if (e == cudaSuccess && p->opts.schedule == FPTC_SCHEDULE_THREE_KERNEL) e = launch_word_offsets(ip, p->d_word_off, s);
-  if (e != cudaSuccess) return cuda_fail(e, "index launch");
-  // decode in pieces of about equal output; each piece is copied back on one of
-  // several streams (several copy engines) while the next pieces decode
-  const uint32_t n = (uint32_t)p->segs.size();
-  const uint32_t pieces = std::min<uint32_t>((uint32_t)fptc_plan::kPieces, n);
-  const uint64_t per = (p->n_samples + pieces - 1) / pieces;
-  uint32_t s0 = 0;
-  int k = 0;
-  while (s0 < n && e == cudaSuccess) {
-    uint32_t s1 = s0;
-    uint64_t acc = 0;
-    while (s1 < n && (acc < per || s1 == s0)) acc += p->segs[s1++].n_samples;
-    if (k == fptc_plan::kPieces - 1) s1 = n;  // the last piece takes the rest
-    e = run_range(p, ip, dp, s0, s1, false, s);
+  for (size_t k = 0; k < pieces.size() && e == cudaSuccess; ++k) {
+    const Piece &pc = pieces[k];
+    if (split_up) e = upload(pc.w0, pc.w1);
+    if (e == cudaSuccess) e = cudaEventRecord(p->evh[k], p->up);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, p->evh[k], 0);
+    if (e == cudaSuccess) e = run_range(p, ip, dp, pc.s0, pc.s1, true, s);
     if (e != cudaSuccess) break;
-    const uint64_t o0 = p->segs[s0].out_offset;
-    uint64_t o1 = o0;
-    for (uint32_t i = s0; i < s1; ++i) o1 = std::max(o1, p->segs[i].out_offset + p->segs[i].n_samples);
-    cudaEvent_t ev = p->ev[k];
     cudaStream_t a = p->aux[k % fptc_plan::kAux];
-    if ((e = cudaEventRecord(ev, s)) != cudaSuccess) break;
-    if ((e = cudaStreamWaitEvent(a, ev, 0)) != cudaSuccess) break;
-    if (o1 > o0) e = cudaMemcpyAsync(h_out + o0, d_out + o0, (o1 - o0) * 4, cudaMemcpyDeviceToHost, a);
-    s0 = s1;
-    ++k;
+    if ((e = cudaEventRecord(p->ev[k], s)) != cudaSuccess) break;
+    if ((e = cudaStreamWaitEvent(a, p->ev[k], 0)) != cudaSuccess) break;
+    if (pc.o1 > pc.o0) e = cudaMemcpyAsync(h_out + pc.o0, d_out + pc.o0, (pc.o1 - pc.o0) * 4, cudaMemcpyDeviceToHost, a);
   }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(p->up);
   for (auto &a : p->aux)
     if (e == cudaSuccess) e = cudaStreamSynchronize(a);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);

@@ -338,13 +338,31 @@ def test_graph_capture_replay():
     compare_with_oracle(plan, b, out, lv)
 
 
-@pytest.mark.parametrize("idct", ["fp32", "bf16x3"])
-def test_decode_host_buffers(idct):
+def _words_reversed(b):
+    """The same batch with the streams' words stored in reverse stream order."""
+    order = np.arange(b.n_streams)[::-1]
+    words, symlen, off = [], [], np.zeros(b.n_streams, np.uint64)
+    pos = 0
+    for i in order:
+        a, n = int(b.word_off[i]), int(b.n_words[i])
+        words.append(b.words[a:a + n])
+        symlen.append(b.symlen[a:a + n])
+        off[i] = pos
+        pos += n
+    return oracle.EncodedBatch(np.concatenate(words), np.concatenate(symlen), off, b.n_words.copy(),
+                               b.lengths.copy(), b.domain_idx.copy(), b.domains)
+
+
+@pytest.mark.parametrize("idct,layout", [("fp32", "ordered"), ("bf16x3", "ordered"), ("fp32", "words_reversed")])
+def test_decode_host_buffers(idct, layout):
     """fptc_decode_host: compressed streams from pinned host memory, samples back
-    to host memory (pieces copied back on several streams while later pieces
-    decode); equal to the device-buffer decode and within the oracle bound."""
+    to host memory (a piece's words go up and its samples come back while other
+    pieces decode; with the words out of output order everything goes up first);
+    equal to the device-buffer decode and within the oracle bound."""
     wl = siggen.mixed_10000_logu(n=60, lo=1, hi=300000)
     b = encode_workload(wl)
+    if layout == "words_reversed":
+        b = _words_reversed(b)
     plan = make_plan(b, idct=idct, out_align=32)
     w, s, out, lv = gpu_decode(plan, b)
     h_w = torch.from_numpy(b.words.view(np.int64)).pin_memory()
