@@ -122,30 +122,6 @@ __device__ __forceinline__ void idct32(const float (&c)[16], Put put) {
   }
 }
 
-// One window's 32 samples from row `lane` of the staging tile (16-byte chunk
-// c at c ^ (lane & 7)) to dst: m samples, 32-byte or 16-byte streaming stores
-// where the alignment allows.
-__device__ __forceinline__ void store_row(const unsigned char *row, uint32_t sx, float *dst, uint32_t m, bool vec32,
-                                          bool vec16) {
-  if (m == kN && (vec32 || vec16)) {
-#pragma unroll
-    for (int b = 0; b < 4; ++b) {
-      const float4 u = *reinterpret_cast<const float4 *>(row + (((2 * b) ^ sx) << 4));
-      const float4 v = *reinterpret_cast<const float4 *>(row + (((2 * b + 1) ^ sx) << 4));
-      if (vec32) {
-        const float x[8] = {u.x, u.y, u.z, u.w, v.x, v.y, v.z, v.w};
-        st_cs_v8(dst + 8 * b, x);
-      } else {
-        __stcs(reinterpret_cast<float4 *>(dst + 8 * b), u);
-        __stcs(reinterpret_cast<float4 *>(dst + 8 * b) + 1, v);
-      }
-    }
-  } else {
-    for (uint32_t n = 0; n < m; ++n)
-      dst[n] = *reinterpret_cast<const float *>(row + ((((n >> 2) ^ sx) << 4) | ((n & 3u) << 2)));
-  }
-}
-
 template <int WARPS>
 __global__ void __launch_bounds__(WARPS * 32, WARPS > 16 ? 1 : 32 / WARPS) k_decode_warp(
     const DecodeParams p, const WarpParams wp, const __grid_constant__ CUtensorMap out_map) {

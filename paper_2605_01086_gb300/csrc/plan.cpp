@@ -47,6 +47,8 @@ struct fptc_plan {
   size_t device_bytes = 0;
   // launch settings
   int kind = FPTC_KERNEL_GENERIC;   // fptc_kernel in use
+  uint32_t shape_n = 0;   // every domain shares this N and the warp-tile kernel of decode_shape.cu serves it
+                          // (0: not such a plan; N = 32, E = 16 plans use decode_warp.cu)
   WarpParams wp{};
   TcParams tp{};
   uint32_t threads = 256, grid = 0, ctas_per_sm = 0;
@@ -137,8 +139,9 @@ void unit_tables(const fptc_domain &d, float unit[2][256]) {
 void layout_tiles(fptc_plan *p, uint32_t tile_samples) {
   p->coef_cap = 0;
   p->gx_cap = 0;
+  const bool shape = p->kind == FPTC_KERNEL_WARP_TILE && p->shape_n != 0;
   for (auto &dd : p->dom_dev) {
-    dd.tile_windows = std::max<uint32_t>(1u, tile_samples / dd.N);
+    dd.tile_windows = shape ? shape_windows_per_tile(dd.N, dd.E) : std::max<uint32_t>(1u, tile_samples / dd.N);
     p->coef_cap = std::max(p->coef_cap, dd.tile_windows * dd.E);
     p->gx_cap = std::max(p->gx_cap, dd.tile_windows * dd.N);
   }
@@ -154,27 +157,42 @@ void layout_tiles(fptc_plan *p, uint32_t tile_samples) {
 
 fptc_status configure_launch(fptc_plan *p) {
   uint32_t threads = p->opts.threads ? p->opts.threads : (p->kind == FPTC_KERNEL_TENSOR ? 512u : 256u);
+  const bool shape = p->kind == FPTC_KERNEL_WARP_TILE && p->shape_n != 0;
+  std::vector<uint32_t> lm, es;
+  for (const auto &d : p->domains) {
+    lm.push_back(d.lmax);
+    es.push_back(d.E);
+  }
   if (p->kind == FPTC_KERNEL_WARP_TILE && p->opts.threads == 0) {
-    // as many warps per SM as one CTA's shared memory allows (32 at most)
+    // as many warps per SM as one CTA's shared memory allows (32 at most; 16
+    // for other shapes, whose transform wants more registers per thread)
     int dev = 0, optin = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    std::vector<uint32_t> lm;
-    for (const auto &d : p->domains) lm.push_back(d.lmax);
     WarpParams probe{};
     threads = 128;
-    for (uint32_t t : {1024u, 768u, 512u, 256u})
-      if (warp_smem_layout(t, lm.data(), (uint32_t)lm.size(), &probe) <= (size_t)optin) {
-        threads = t;
-        break;
-      }
+    if (shape) {
+      for (uint32_t t : {512u, 256u})
+        if (shape_smem_layout(p->shape_n, t, lm.data(), es.data(), (uint32_t)lm.size(), &probe) <= (size_t)optin) {
+          threads = t;
+          break;
+        }
+    } else {
+      for (uint32_t t : {1024u, 768u, 512u, 256u})
+        if (warp_smem_layout(t, lm.data(), (uint32_t)lm.size(), &probe) <= (size_t)optin) {
+          threads = t;
+          break;
+        }
+    }
   }
-  const bool t_ok = threads == 128 || threads == 256 || threads == 512 ||
-                    ((threads == 768 || threads == 1024) && p->kind == FPTC_KERNEL_WARP_TILE) ||
-                    ((threads == 384 || threads == 640 || threads == 768) && p->kind == FPTC_KERNEL_TENSOR);
+  const bool t_ok = shape ? (threads == 256 || threads == 512 || threads == 768)
+                          : (threads == 128 || threads == 256 || threads == 512 ||
+                             ((threads == 768 || threads == 1024) && p->kind == FPTC_KERNEL_WARP_TILE) ||
+                             ((threads == 384 || threads == 640 || threads == 768) && p->kind == FPTC_KERNEL_TENSOR));
   if (!t_ok) {
     set_error("threads must be 128, 256 or 512 (768 and 1024 also for the warp-tile kernel, 384, 640 and 768 "
-              "for the tensor-core kernel; got %u)", threads);
+              "for the tensor-core kernel; 256, 512 or 768 for the warp-tile kernel of other shapes; got %u)",
+              threads);
     return FPTC_ERR_INVALID_ARGUMENT;
   }
   p->threads = threads;
@@ -186,8 +204,6 @@ fptc_status configure_launch(fptc_plan *p) {
     if (e != cudaSuccess) return cuda_fail(e, "decode shared-memory size");
     e = fixed_occupancy(threads, p->smem, &occ);
   } else if (p->kind == FPTC_KERNEL_TENSOR) {
-    std::vector<uint32_t> lm;
-    for (const auto &d : p->domains) lm.push_back(d.lmax);
     if (p->opts.threads == 0) {
       // as many warpgroups as one CTA's shared memory allows (4 at most)
       int dev = 0, optin = 0;
@@ -215,9 +231,12 @@ fptc_status configure_launch(fptc_plan *p) {
                    threads, fa.numRegs, fa.sharedSizeBytes, fa.maxDynamicSharedSizeBytes, p->smem, occ);
     }
     if (e == cudaSuccess) occ = std::min<int>(occ, 1);
+  } else if (shape) {
+    p->smem = shape_smem_layout(p->shape_n, threads, lm.data(), es.data(), (uint32_t)lm.size(), &p->wp);
+    e = shape_smem_config(p->shape_n, threads, p->smem);
+    if (e != cudaSuccess) return cuda_fail(e, "decode shared-memory size");
+    e = shape_occupancy(p->shape_n, threads, p->smem, &occ);
   } else if (p->kind == FPTC_KERNEL_WARP_TILE) {
-    std::vector<uint32_t> lm;
-    for (const auto &d : p->domains) lm.push_back(d.lmax);
     p->smem = warp_smem_layout(threads, lm.data(), (uint32_t)lm.size(), &p->wp);
     e = warp_smem_config(threads, p->smem);
     if (e != cudaSuccess) return cuda_fail(e, "decode shared-memory size");
@@ -236,14 +255,12 @@ fptc_status configure_launch(fptc_plan *p) {
   p->ctas_per_sm = p->opts.ctas_per_sm ? std::min<uint32_t>(p->opts.ctas_per_sm, (uint32_t)occ) : (uint32_t)occ;
   const uint64_t full = (uint64_t)p->sm_count * p->ctas_per_sm;
   p->grid = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(full, p->n_tiles));
-  // backward
-  if (p->kind == FPTC_KERNEL_WARP_TILE || p->kind == FPTC_KERNEL_TENSOR) {
+  // backward (the warp-tile adjoint serves N = 32, E = 16 plans)
+  if ((p->kind == FPTC_KERNEL_WARP_TILE && !shape) || p->kind == FPTC_KERNEL_TENSOR) {
     // the warp-tile adjoint: 16 warps if their buffers fit, else 8
     int dev = 0, optin = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    std::vector<uint32_t> lm;
-    for (const auto &d : p->domains) lm.push_back(d.lmax);
     p->b_warp = false;
     for (uint32_t t : {512u, 256u}) {
       const size_t need = backward_warp_smem_layout(t, lm.data(), (uint32_t)lm.size(), &p->b_wp);
@@ -381,6 +398,7 @@ cudaError_t run_range(const fptc_plan *p, const IndexParams &ip0, const DecodePa
     CUtensorMap map;
     std::memset(&map, 0, sizeof(map));
     wp.out_tma = encode_out_map(&map, dp.out, p->out_extent) ? 1u : 0u;
+    if (p->shape_n) return launch_shape(dp, wp, map, p->shape_n, p->threads, grid, p->smem, st);
     return launch_warp(dp, wp, map, p->threads, grid, p->smem, st);
   }
   if (p->kind == FPTC_KERNEL_TENSOR) {
@@ -474,16 +492,22 @@ fptc_status fptc_plan_create(fptc_plan **out, int device, const fptc_domain *dom
     set_error("unknown kernel %u", o.kernel);
     return FPTC_ERR_INVALID_ARGUMENT;
   }
-  bool all_fixed = true;
-  for (uint32_t d = 0; d < n_domains; ++d) all_fixed = all_fixed && domains[d].N == 32 && domains[d].E == 16;
-  const bool warp_ok = all_fixed && n_domains <= kWarpMaxDomains;
+  bool all_fixed = true, same_n = n_domains > 0;
+  for (uint32_t d = 0; d < n_domains; ++d) {
+    all_fixed = all_fixed && domains[d].N == 32 && domains[d].E == 16;
+    same_n = same_n && domains[d].N == domains[0].N;
+  }
+  const bool fixed_ok = all_fixed && n_domains <= kWarpMaxDomains;
+  // other shapes: one power-of-two N for every domain
+  const bool shape_ok = !all_fixed && same_n && shape_supported(domains[0].N) && n_domains <= kWarpMaxDomains;
+  const bool warp_ok = fixed_ok || shape_ok;
   if ((o.kernel == FPTC_KERNEL_BLOCK_TILE && !all_fixed) || (o.kernel == FPTC_KERNEL_WARP_TILE && !warp_ok)) {
-    set_error("the fixed-shape kernels need N = 32, E = 16 in every domain (and at most %u domains for the "
-              "warp-tile kernel)", kWarpMaxDomains);
+    set_error("the block-tile kernel needs N = 32, E = 16 in every domain; the warp-tile kernel that, or one "
+              "power-of-two N in [4, 128] shared by every domain (at most %u domains)", kWarpMaxDomains);
     return FPTC_ERR_UNSUPPORTED;
   }
   if (o.idct != FPTC_IDCT_FP32 || o.kernel == FPTC_KERNEL_TENSOR) {
-    if (!warp_ok || o.idct == FPTC_IDCT_FP32) {
+    if (!fixed_ok || o.idct == FPTC_IDCT_FP32) {
       set_error("the tensor-core transform needs N = 32, E = 16 in every domain (at most %u domains) and "
                 "idct = TF32, BF16X3 or TF32X3", kWarpMaxDomains);
       return FPTC_ERR_UNSUPPORTED;
@@ -500,11 +524,17 @@ fptc_status fptc_plan_create(fptc_plan **out, int device, const fptc_domain *dom
       WarpParams probe{};
       int optin = 0;
       if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device) != cudaSuccess) optin = 0;
-      fits = warp_smem_layout(128, lm.data(), n_domains, &probe) <= (size_t)optin;
+      if (fixed_ok) {
+        fits = warp_smem_layout(128, lm.data(), n_domains, &probe) <= (size_t)optin;
+      } else {
+        std::vector<uint32_t> es(n_domains);
+        for (uint32_t d = 0; d < n_domains; ++d) es[d] = domains[d].E;
+        fits = shape_smem_layout(domains[0].N, 256, lm.data(), es.data(), n_domains, &probe) <= (size_t)optin;
+      }
     }
     o.kernel = fits ? FPTC_KERNEL_WARP_TILE : (all_fixed ? FPTC_KERNEL_BLOCK_TILE : FPTC_KERNEL_GENERIC);
   }
-  if (o.kernel == FPTC_KERNEL_WARP_TILE) o.tile_samples = warp_tile_windows() * 32;
+  if (o.kernel == FPTC_KERNEL_WARP_TILE) o.tile_samples = shape_ok ? 0 : warp_tile_windows() * 32;
   if (o.kernel == FPTC_KERNEL_TENSOR) o.tile_samples = tc_tile_windows() * 32;
   if (o.tile_samples == 0) o.tile_samples = o.kernel == FPTC_KERNEL_BLOCK_TILE ? 8192 : 4096;
   if (o.tile_samples > 65536) {
@@ -605,6 +635,7 @@ fptc_status fptc_plan_create(fptc_plan **out, int device, const fptc_domain *dom
   }
   p->lut_cap = 1u << max_lmax;
   p->kind = (int)o.kernel;
+  p->shape_n = shape_ok ? domains[0].N : 0u;
 
   // ---- tile queue: segments ordered by output offset
   p->queue.resize(n_segments);
@@ -990,9 +1021,11 @@ fptc_status fptc_plan_autotune(fptc_plan *p, const uint64_t *d_words, const uint
     if (th > 512) {
       if (fixed && p->domains.size() <= kWarpMaxDomains)
         cands.push_back({FPTC_KERNEL_WARP_TILE, warp_tile_windows() * 32, th});
+      if (p->shape_n && th == 768) cands.push_back({FPTC_KERNEL_WARP_TILE, 4096, th});
       continue;
     }
     if (fixed && p->domains.size() <= kWarpMaxDomains) cands.push_back({FPTC_KERNEL_WARP_TILE, warp_tile_windows() * 32, th});
+    if (p->shape_n && th >= 256) cands.push_back({FPTC_KERNEL_WARP_TILE, 4096, th});
     if (fixed)
       for (uint32_t ts : {4096u, 8192u}) cands.push_back({FPTC_KERNEL_BLOCK_TILE, ts, th});
     else

@@ -119,13 +119,15 @@ __device__ __forceinline__ Ctx make_ctx(const DecodeParams &p, uint32_t s, uint6
   return c;
 }
 
-// Context of tile g of segment s located from the index (warp-collective).
-__device__ __forceinline__ Ctx first_ctx(const DecodeParams &p, uint32_t s, uint64_t g, uint32_t lane) {
+// Context of tile g of segment s (tiles of tile_syms symbols) located from the
+// index (warp-collective).
+__device__ __forceinline__ Ctx first_ctx(const DecodeParams &p, uint32_t s, uint64_t g, uint32_t lane,
+                                         uint64_t tile_syms = kTS) {
   const SegDev &sg = p.segs[s];
   if (p.seg_bad[s] != 0) return Ctx{0, 0, 0, s, 0};
   const uint64_t tin = g - sg.tile_base;
   if (tin == 0) return make_ctx(p, s, sg.word_offset, 0u);
-  const TileRec r = symbol_word(p.symlen, p.chunk_off, sg, tin * (uint64_t)kTS, lane);
+  const TileRec r = symbol_word(p.symlen, p.chunk_off, sg, tin * tile_syms, lane);
   if (r.pad != 0) return Ctx{0, 0, 0, s, 0};
   return make_ctx(p, s, r.first_word, r.skip);
 }
@@ -249,7 +251,9 @@ __device__ __forceinline__ uint32_t load_domain_tables(const DecodeParams &p, ui
 // last: its words that start at or after te are left to the next tile, and the
 // word holding symbol te is where the next tile starts.  w/n hold the first
 // pass's words; each later pass is loaded while the one before it decodes.
-__device__ __forceinline__ TileEnd decode_tile(const DecodeParams &p, const Ctx &cur, uint32_t te, const DomW &dd,
+// D: the domain's table view (lut_off, shift, complete).
+template <class D>
+__device__ __forceinline__ TileEnd decode_tile(const DecodeParams &p, const Ctx &cur, uint32_t te, const D &dd,
                                                const unsigned char *smem, uint8_t *stage, uint32_t lane,
                                                uint64_t (&w)[kWPL], uint32_t (&n)[kWPL]) {
   const uint16_t *lut = reinterpret_cast<const uint16_t *>(smem + dd.lut_off);
@@ -352,6 +356,30 @@ __device__ __forceinline__ void put_levels(uint8_t *dl, const uint4 &sv) {
     const uint32_t sw[4] = {sv.x, sv.y, sv.z, sv.w};
 #pragma unroll
     for (int j = 0; j < 16; ++j) dl[j] = (uint8_t)(sw[j >> 2] >> (8 * (j & 3)));
+  }
+}
+
+// A row of 32 samples from the staging tile (16-byte chunk c at c ^ (row & 7),
+// sx = row & 7) to dst: m samples, 32-byte or 16-byte streaming stores where
+// the alignment allows.
+__device__ __forceinline__ void store_row(const unsigned char *row, uint32_t sx, float *dst, uint32_t m, bool vec32,
+                                          bool vec16) {
+  if (m == 32 && (vec32 || vec16)) {
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const float4 u = *reinterpret_cast<const float4 *>(row + (((2 * b) ^ sx) << 4));
+      const float4 v = *reinterpret_cast<const float4 *>(row + (((2 * b + 1) ^ sx) << 4));
+      if (vec32) {
+        const float x[8] = {u.x, u.y, u.z, u.w, v.x, v.y, v.z, v.w};
+        st_cs_v8(dst + 8 * b, x);
+      } else {
+        __stcs(reinterpret_cast<float4 *>(dst + 8 * b), u);
+        __stcs(reinterpret_cast<float4 *>(dst + 8 * b) + 1, v);
+      }
+    }
+  } else {
+    for (uint32_t n = 0; n < m; ++n)
+      dst[n] = *reinterpret_cast<const float *>(row + ((((n >> 2) ^ sx) << 4) | ((n & 3u) << 2)));
   }
 }
 

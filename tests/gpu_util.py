@@ -93,3 +93,21 @@ def compare_with_oracle(plan, batch, out, lv, idx=None, tol=FP32_REL_L2, domains
             np.testing.assert_array_equal(lv_h[a:a + L], olv[int(lv_off[j]):int(lv_off[j]) + L],
                                           err_msg=f"levels of stream {i}")
     return worst
+
+
+def crafted_batch(domains, levels_list, lengths, dom_idx):
+    """Packs given level arrays with the oracle's Alg. 1 (no signal, no quantizer)."""
+    words, symlen, nw = [], [], []
+    for X, di in zip(levels_list, dom_idx):
+        d = domains[di]
+        codes = oracle.canonical_codes(d.code_len, d.lmax)
+        w, s = oracle.pack_symlen(X, codes, d.code_len)
+        words.append(w)
+        symlen.append(s)
+        nw.append(w.size)
+    nw = np.array(nw, np.uint64)
+    off = np.zeros(len(nw), np.uint64)
+    if len(nw) > 1:
+        off[1:] = np.cumsum(nw[:-1])
+    return oracle.EncodedBatch(np.concatenate(words), np.concatenate(symlen), off, nw,
+                               np.array(lengths, np.uint64), np.array(dom_idx, np.int32), list(domains))

@@ -12,8 +12,8 @@ import pytest
 import oracle
 import siggen
 
-from gpu_util import (FP32_REL_L2, compare_with_oracle, encode_workload, gpu_decode, make_plan, oracle_domains,
-                      product_domain, segments_of)
+from gpu_util import (FP32_REL_L2, compare_with_oracle, crafted_batch, encode_workload, gpu_decode, make_plan,
+                      oracle_domains, product_domain, segments_of)
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -25,24 +25,6 @@ def _built():
         pytest.skip("no CUDA device")
     from paper_2605_01086_gb300 import build
     build()
-
-
-def crafted_batch(domains, levels_list, lengths, dom_idx):
-    """Packs given level arrays with the oracle's Alg. 1 (no signal, no quantizer)."""
-    words, symlen, nw = [], [], []
-    for X, di in zip(levels_list, dom_idx):
-        d = domains[di]
-        codes = oracle.canonical_codes(d.code_len, d.lmax)
-        w, s = oracle.pack_symlen(X, codes, d.code_len)
-        words.append(w)
-        symlen.append(s)
-        nw.append(w.size)
-    nw = np.array(nw, np.uint64)
-    off = np.zeros(len(nw), np.uint64)
-    if len(nw) > 1:
-        off[1:] = np.cumsum(nw[:-1])
-    return oracle.EncodedBatch(np.concatenate(words), np.concatenate(symlen), off, nw,
-                               np.array(lengths, np.uint64), np.array(dom_idx, np.int32), list(domains))
 
 
 def test_eeg_single_stream():
@@ -151,15 +133,16 @@ def test_sixty_four_one_bit_codes_per_word():
     compare_with_oracle(plan, b, out, lv)
 
 
-def test_incomplete_code_and_one_symbol_windows():
+@pytest.mark.parametrize("kernel", ["generic", "warp_tile"])
+def test_incomplete_code_and_one_symbol_windows(kernel):
     cl = np.zeros(256, np.uint8)
     cl[128], cl[120], cl[140] = 1, 3, 3   # Kraft 3/4: incomplete
     o1 = oracle.Domain(4, 1, 1, 1, 20.0, 0.01, (5.0, 0.0, 0.0), 3, cl)  # E = 1: one symbol per window
     rng = np.random.default_rng(3)
     X = rng.choice(np.array([128, 120, 140], np.uint8), size=1000)
     b = crafted_batch([o1], [X, X[:1], X[:7]], [4000, 3, 27], [0, 0, 0])
-    plan = make_plan(b)
-    assert plan.info["kernel"] == KERNEL_IDS["generic"]
+    plan = make_plan(b, kernel=kernel)
+    assert plan.info["kernel"] == KERNEL_IDS[kernel]
     _, _, out, lv = gpu_decode(plan, b)
     compare_with_oracle(plan, b, out, lv)
 
