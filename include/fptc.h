@@ -109,10 +109,13 @@ typedef enum fptc_schedule {
 } fptc_schedule;
 
 typedef enum fptc_kernel {
-  FPTC_KERNEL_AUTO = 0,        /* warp-tile if every domain has N = 32, E = 16, else generic */
+  FPTC_KERNEL_AUTO = 0,        /* warp-tile if every domain has N = 32, E = 16, or if all domains share one
+                                  power-of-two N in [4, 128] (and their tables fit), else generic */
   FPTC_KERNEL_GENERIC = 1,     /* any N, E: one block per tile, basis through L1 */
   FPTC_KERNEL_BLOCK_TILE = 2,  /* N = 32, E = 16: one block per tile, pipelined */
-  FPTC_KERNEL_WARP_TILE = 3,   /* N = 32, E = 16: one warp per 64-window tile, no block barriers */
+  FPTC_KERNEL_WARP_TILE = 3,   /* one warp per tile, no block barriers: N = 32, E = 16 (128-window tiles),
+                                  or one power-of-two N in [4, 128] shared by every domain, any E <= N
+                                  (tiles of about 2048 symbols); at most 8 domains */
   FPTC_KERNEL_TENSOR = 4       /* N = 32, E = 16, tensor-core transform; chosen by idct != FPTC_IDCT_FP32 */
 } fptc_kernel;
 
@@ -121,8 +124,9 @@ typedef struct fptc_plan_options {
   uint32_t schedule;      /* fptc_schedule */
   uint32_t tile_samples;  /* target output samples per tile (whole windows); 0 = 8192 if every domain
                              has N = 32, E = 16, else 4096 */
-  uint32_t threads;       /* threads per CTA: 128, 256 or 512 (also 768, 1024 for the warp-tile kernel);
-                             0 = 256, or for the warp-tile kernel the most that fit */
+  uint32_t threads;       /* threads per CTA: 128, 256 or 512 (also 768, 1024 for the warp-tile kernel at
+                             N = 32, E = 16; 256, 512 or 768 for it at other shapes); 0 = 256, or for the
+                             warp-tile kernel the most that fit (at most 512 at other shapes) */
   uint32_t ctas_per_sm;   /* persistent CTAs per SM; 0 = as many as fit */
   uint32_t kernel;        /* fptc_kernel: which decode kernel; 0 = choose */
   uint32_t reserved[2];   /* must be 0 */
