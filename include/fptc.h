@@ -109,13 +109,13 @@ typedef enum fptc_schedule {
 } fptc_schedule;
 
 typedef enum fptc_kernel {
-  FPTC_KERNEL_AUTO = 0,        /* warp-tile if every domain has N = 32, E = 16, or if all domains share one
-                                  power-of-two N in [4, 128] (and their tables fit), else generic */
+  FPTC_KERNEL_AUTO = 0,        /* warp-tile if every domain has N = 32, E = 16, or a power-of-two N in
+                                  [4, 128] (and their tables fit), else generic */
   FPTC_KERNEL_GENERIC = 1,     /* any N, E: one block per tile, basis through L1 */
   FPTC_KERNEL_BLOCK_TILE = 2,  /* N = 32, E = 16: one block per tile, pipelined */
   FPTC_KERNEL_WARP_TILE = 3,   /* one warp per tile, no block barriers: N = 32, E = 16 (128-window tiles),
-                                  or one power-of-two N in [4, 128] shared by every domain, any E <= N
-                                  (tiles of about 2048 symbols); at most 8 domains */
+                                  or a power-of-two N in [4, 128] in every domain (several N in one
+                                  batch), any E <= N (tiles of about 2048 symbols); at most 8 domains */
   FPTC_KERNEL_TENSOR = 4       /* N = 32, E = 16, tensor-core transform; chosen by idct != FPTC_IDCT_FP32 */
 } fptc_kernel;
 

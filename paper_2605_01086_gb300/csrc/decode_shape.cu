@@ -1,7 +1,8 @@
 // Fused decode for window shapes other than the Table 1 default: every domain of
-// the plan has the same window size N (a power of two in [4, 128]) and any
-// kept-bin count E <= N (Table 1 gives the ranges; Fig. 14 measures how the
-// throughput moves with them).
+// the plan has a power-of-two window size N in [4, 128] and any kept-bin count
+// E <= N, domains of different N in one batch (Table 1 gives the ranges; Fig. 14
+// measures how the throughput moves with them).  The transform is compiled per
+// N and chosen per tile from the tile's domain (a warp-uniform switch).
 //
 // The SymLen decode, tile chaining, level staging and TMA output path are those
 // of the warp-tile kernel (warp_tile.cuh), with tiles of T windows per domain
@@ -36,7 +37,8 @@ struct DomS {
   uint32_t complete;
   uint32_t E, B1, kz;  // kz = min(E, B2)
   uint32_t T;          // windows per tile
-  uint32_t pad[3];
+  uint32_t N;
+  uint32_t pad[2];
 };
 
 template <int N>
@@ -66,17 +68,17 @@ __host__ __device__ constexpr uint32_t shape_tile_windows(uint32_t N, uint32_t E
 
 // Tables of every domain into shared memory from byte 0 (the layout of
 // shape_smem_layout).  Returns the end offset.  Contains no barrier.
-template <int N, int THREADS>
+template <int THREADS>
 __device__ __forceinline__ uint32_t load_shape_tables(const DecodeParams &p, uint32_t n_domains, unsigned char *smem) {
-  using K = ShapeK<N>;
   DomS *const ds = reinterpret_cast<DomS *>(smem);
   uint32_t off = (uint32_t)align16(sizeof(DomS) * (n_domains ? n_domains : 1));
   for (uint32_t d = 0; d < n_domains; ++d) {
     const DomainDev &dm = p.domains[d];
+    const uint32_t N = dm.N, brow = shape_brow(N), half = N / 2;
     const uint32_t lut_off = off;
     const uint32_t deq_off = lut_off + (uint32_t)align16((size_t)2 << dm.lmax);
     const uint32_t basis_off = deq_off + (uint32_t)align16(3u * kZStride * 4);
-    off = basis_off + (uint32_t)align16((size_t)dm.E * K::BROW * 4);
+    off = basis_off + (uint32_t)align16((size_t)dm.E * brow * 4);
     if (threadIdx.x == 0) {
       DomS x;
       x.lut_off = lut_off;
@@ -88,7 +90,8 @@ __device__ __forceinline__ uint32_t load_shape_tables(const DecodeParams &p, uin
       x.B1 = dm.B1;
       x.kz = dm.B2 < dm.E ? dm.B2 : dm.E;
       x.T = dm.tile_windows;
-      x.pad[0] = x.pad[1] = x.pad[2] = 0;
+      x.N = N;
+      x.pad[0] = x.pad[1] = 0;
       ds[d] = x;
     }
     uint16_t *lut = reinterpret_cast<uint16_t *>(smem + lut_off);
@@ -107,34 +110,180 @@ __device__ __forceinline__ uint32_t load_shape_tables(const DecodeParams &p, uin
       const uint32_t z = i / kZStride, L = i - z * kZStride;
       deq[i] = (L < 256u && z < 2u) ? (z == 0 ? a0 : a1) * dm.unit[z][L] : 0.0f;
     }
+    // the half basis B[k][n], n < N / 2: rows of brow floats, N >= 32 in groups of 16 (+ 4 pad)
     float *bas = reinterpret_cast<float *>(smem + basis_off);
     const float *g_bas = p.basis + dm.basis_offset;
-    for (uint32_t i = threadIdx.x; i < dm.E * (uint32_t)K::BROW; i += THREADS) {
-      const uint32_t k = i / K::BROW, r = i - k * K::BROW;
-      uint32_t n;
-      bool in;
-      if (N >= 32) {
-        n = 16 * (r / 20) + r % 20;
-        in = r % 20 < 16;
-      } else {
-        n = r;
-        in = r < (uint32_t)K::P;
-      }
+    for (uint32_t i = threadIdx.x; i < dm.E * brow; i += THREADS) {
+      const uint32_t k = i / brow, r = i - k * brow;
+      const uint32_t n = N >= 32 ? 16 * (r / 20) + r % 20 : r;
+      const bool in = N >= 32 ? r % 20 < 16 : r < half;
       bas[i] = in ? __ldg(g_bas + (size_t)k * N + n) : 0.0f;
     }
   }
   return off;
 }
 
-template <int N, int WARPS>
+// Where the transform of a tile writes: the warp's staging tile and its row
+// of it, the output tensor map, and whether a TMA store is still reading it.
+struct ShapeOut {
+  unsigned char *otile;
+  unsigned char *row;
+  uint32_t sx;
+  uint32_t lane;
+  const CUtensorMap *map;
+  bool tma_ok;  // the segment's output starts on a 128-byte boundary and the map is valid
+  bool vec32, vec16;
+};
+
+// Dequantization + inverse transform + reassembly of one decoded tile of nwin
+// windows (levels at stage[0..nwin E)), 1024 samples per step.
+template <int N>
+__device__ __forceinline__ void shape_transform(const DecodeParams &p, const SegDev &sg, const DomS &dd,
+                                                const unsigned char *smem, const uint8_t *stage, uint64_t win0,
+                                                uint32_t nwin, const ShapeOut &o, bool &tma_pending) {
+  using K = ShapeK<N>;
+  const uint32_t lane = o.lane;
+  const float *deq0 = reinterpret_cast<const float *>(smem + dd.deq_off);
+  const float *bas = reinterpret_cast<const float *>(smem + dd.basis_off);
+  const uint64_t S = sg.n_samples;
+#pragma unroll 1
+  for (uint32_t w0 = 0; w0 < nwin; w0 += K::R) {
+    const bool tma_step = o.tma_ok && w0 + K::R <= nwin && (win0 + w0 + K::R) * N <= S;
+    if (tma_pending) {
+      if (lane == 0) tma_wait_read();  // the previous step has left the staging tile
+      __syncwarp();
+      tma_pending = false;
+    }
+    float ev[16], od[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) ev[i] = od[i] = 0.0f;
+    if (N >= 32) {
+      const uint32_t wl = w0 + lane / K::L, q = lane % K::L;
+      if (wl < nwin) {
+        const uint8_t *lv = stage + wl * dd.E;
+        const float *bq = bas + q * 20;
+        uint32_t k = 0;
+#pragma unroll 1
+        for (; k + 2 <= dd.kz; k += 2) {
+          const float c0 = deq0[(k < dd.B1 ? 0 : kZStride) + lv[k]];
+          const float c1 = deq0[(k + 1 < dd.B1 ? 0 : kZStride) + lv[k + 1]];
+          const float4 *b0 = reinterpret_cast<const float4 *>(bq + k * K::BROW);
+          const float4 *b1 = reinterpret_cast<const float4 *>(bq + (k + 1) * K::BROW);
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const float4 u = b0[j], v = b1[j];
+            ev[4 * j] = fmaf(c0, u.x, ev[4 * j]);
+            ev[4 * j + 1] = fmaf(c0, u.y, ev[4 * j + 1]);
+            ev[4 * j + 2] = fmaf(c0, u.z, ev[4 * j + 2]);
+            ev[4 * j + 3] = fmaf(c0, u.w, ev[4 * j + 3]);
+            od[4 * j] = fmaf(c1, v.x, od[4 * j]);
+            od[4 * j + 1] = fmaf(c1, v.y, od[4 * j + 1]);
+            od[4 * j + 2] = fmaf(c1, v.z, od[4 * j + 2]);
+            od[4 * j + 3] = fmaf(c1, v.w, od[4 * j + 3]);
+          }
+        }
+        if (k < dd.kz) {  // a last even bin
+          const float c0 = deq0[(k < dd.B1 ? 0 : kZStride) + lv[k]];
+          const float4 *b0 = reinterpret_cast<const float4 *>(bq + k * K::BROW);
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const float4 u = b0[j];
+            ev[4 * j] = fmaf(c0, u.x, ev[4 * j]);
+            ev[4 * j + 1] = fmaf(c0, u.y, ev[4 * j + 1]);
+            ev[4 * j + 2] = fmaf(c0, u.z, ev[4 * j + 2]);
+            ev[4 * j + 3] = fmaf(c0, u.w, ev[4 * j + 3]);
+          }
+        }
+      }
+      // samples 16 q .. 16 q + 15 of the window and their mirrors, at step
+      // positions (lane / L) N + ...: two half rows of the staging tile
+      const uint32_t base = (lane / K::L) * N;
+      const uint32_t f0 = base + 16 * q, m0 = base + N - 16 * (q + 1);
+      float xf[16], xm[16];
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        xf[i] = ev[i] + od[i];
+        xm[15 - i] = ev[i] - od[i];
+      }
+      unsigned char *const rf = o.otile + (f0 >> 5) * 128;
+      unsigned char *const rm = o.otile + (m0 >> 5) * 128;
+      const uint32_t cf = (f0 & 31u) >> 2, cm = (m0 & 31u) >> 2;
+      const uint32_t sf = (f0 >> 5) & 7u, sm = (m0 >> 5) & 7u;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        *reinterpret_cast<float4 *>(rf + (((cf + j) ^ sf) << 4)) =
+            make_float4(xf[4 * j], xf[4 * j + 1], xf[4 * j + 2], xf[4 * j + 3]);
+        *reinterpret_cast<float4 *>(rm + (((cm + j) ^ sm) << 4)) =
+            make_float4(xm[4 * j], xm[4 * j + 1], xm[4 * j + 2], xm[4 * j + 3]);
+      }
+    } else {
+      // windows w0 + M lane + j, j < M: their pairs n < P
+      const uint32_t wl = w0 + K::M * lane;
+#pragma unroll 1
+      for (uint32_t k = 0; k < dd.kz; ++k) {
+        const float *dq = deq0 + (k < dd.B1 ? 0 : kZStride);
+        float b[K::P];
+#pragma unroll
+        for (int i = 0; i < K::P; i += 4) {
+          const float4 u = *reinterpret_cast<const float4 *>(bas + k * K::BROW + i);
+          b[i] = u.x;
+          if (i + 1 < K::P) b[i + 1] = u.y;
+          if (i + 2 < K::P) b[i + 2] = u.z;
+          if (i + 3 < K::P) b[i + 3] = u.w;
+        }
+#pragma unroll
+        for (int j = 0; j < K::M; ++j) {
+          const float c = wl + j < nwin ? dq[stage[(wl + j) * dd.E + k]] : 0.0f;
+#pragma unroll
+          for (int i = 0; i < K::P; ++i) {
+            if (k & 1u)
+              od[j * K::P + i] = fmaf(c, b[i], od[j * K::P + i]);
+            else
+              ev[j * K::P + i] = fmaf(c, b[i], ev[j * K::P + i]);
+          }
+        }
+      }
+      // the lane's row: windows j at positions j N .. j N + N - 1
+      float x[32];
+#pragma unroll
+      for (int j = 0; j < K::M; ++j)
+#pragma unroll
+        for (int i = 0; i < K::P; ++i) {
+          x[j * N + i] = ev[j * K::P + i] + od[j * K::P + i];
+          x[j * N + N - 1 - i] = ev[j * K::P + i] - od[j * K::P + i];
+        }
+#pragma unroll
+      for (int c = 0; c < 8; ++c)
+        *reinterpret_cast<float4 *>(o.row + ((c ^ o.sx) << 4)) =
+            make_float4(x[4 * c], x[4 * c + 1], x[4 * c + 2], x[4 * c + 3]);
+    }
+    const uint64_t s0 = (win0 + w0) * N;  // first sample of the step in the segment
+    if (tma_step) {
+      fence_async_shared();
+      __syncwarp();
+      if (lane == 0) tma_store_rows(o.map, o.otile, (int32_t)((sg.out_offset + s0) >> 5));
+      tma_pending = true;
+    } else {
+      __syncwarp();  // rows are written by other lanes
+      const uint64_t lim = (uint64_t)(nwin - w0) * N < S - s0 ? (uint64_t)(nwin - w0) * N : S - s0;
+      const uint64_t r0 = (uint64_t)lane * 32;
+      if (r0 < lim) {
+        const uint32_t m = lim - r0 < 32 ? (uint32_t)(lim - r0) : 32u;
+        store_row(o.row, o.sx, p.out + sg.out_offset + s0 + r0, m, o.vec32, o.vec16);
+      }
+      __syncwarp();  // before the next step rewrites the tile
+    }
+  }
+}
+
+template <int WARPS>
 __global__ void __launch_bounds__(WARPS * 32, 1) k_decode_shape(const DecodeParams p, const WarpParams wp,
                                                                 const __grid_constant__ CUtensorMap out_map) {
-  using K = ShapeK<N>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const DomS *const ds = reinterpret_cast<const DomS *>(smem_raw);
   const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 
-  load_shape_tables<N, WARPS * 32>(p, wp.n_domains, smem_raw);
+  load_shape_tables<WARPS * 32>(p, wp.n_domains, smem_raw);
   __syncthreads();
 
   unsigned char *const wbase = smem_raw + wp.warp_off + warp * kMiscBytes;
@@ -200,169 +349,28 @@ __global__ void __launch_bounds__(WARPS * 32, 1) k_decode_shape(const DecodePara
     }
 
     // ---- 2./3. dequantization + inverse transform + reassembly, 1024 samples per step
-    const float *deq0 = reinterpret_cast<const float *>(smem_raw + dd.deq_off);
-    const float *bas = reinterpret_cast<const float *>(smem_raw + dd.basis_off);
-    const uint64_t S = sg.n_samples;
     const uint32_t aligned = sg.out_aligned;
-    const bool vec32 = (aligned & 2u) && (reinterpret_cast<uintptr_t>(p.out) & 31u) == 0;
-    const bool tma_seg = wp.out_tma && (aligned & 4u);
-#pragma unroll 1
-    for (uint32_t w0 = 0; w0 < nwin; w0 += K::R) {
-      const bool tma_step = tma_seg && w0 + K::R <= nwin && (win0 + w0 + K::R) * N <= S;
-      if (tma_pending) {
-        if (lane == 0) tma_wait_read();  // the previous step has left the staging tile
-        __syncwarp();
-        tma_pending = false;
-      }
-      float ev[16], od[16];
-#pragma unroll
-      for (int i = 0; i < 16; ++i) ev[i] = od[i] = 0.0f;
-      if (N >= 32) {
-        const uint32_t wl = w0 + lane / K::L, q = lane % K::L;
-        if (wl < nwin) {
-          const uint8_t *lv = stage + wl * dd.E;
-          const float *bq = bas + q * 20;
-          uint32_t k = 0;
-#pragma unroll 1
-          for (; k + 2 <= dd.kz; k += 2) {
-            const float c0 = deq0[(k < dd.B1 ? 0 : kZStride) + lv[k]];
-            const float c1 = deq0[(k + 1 < dd.B1 ? 0 : kZStride) + lv[k + 1]];
-            const float4 *b0 = reinterpret_cast<const float4 *>(bq + k * K::BROW);
-            const float4 *b1 = reinterpret_cast<const float4 *>(bq + (k + 1) * K::BROW);
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-              const float4 u = b0[j], v = b1[j];
-              ev[4 * j] = fmaf(c0, u.x, ev[4 * j]);
-              ev[4 * j + 1] = fmaf(c0, u.y, ev[4 * j + 1]);
-              ev[4 * j + 2] = fmaf(c0, u.z, ev[4 * j + 2]);
-              ev[4 * j + 3] = fmaf(c0, u.w, ev[4 * j + 3]);
-              od[4 * j] = fmaf(c1, v.x, od[4 * j]);
-              od[4 * j + 1] = fmaf(c1, v.y, od[4 * j + 1]);
-              od[4 * j + 2] = fmaf(c1, v.z, od[4 * j + 2]);
-              od[4 * j + 3] = fmaf(c1, v.w, od[4 * j + 3]);
-            }
-          }
-          if (k < dd.kz) {  // a last even bin
-            const float c0 = deq0[(k < dd.B1 ? 0 : kZStride) + lv[k]];
-            const float4 *b0 = reinterpret_cast<const float4 *>(bq + k * K::BROW);
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-              const float4 u = b0[j];
-              ev[4 * j] = fmaf(c0, u.x, ev[4 * j]);
-              ev[4 * j + 1] = fmaf(c0, u.y, ev[4 * j + 1]);
-              ev[4 * j + 2] = fmaf(c0, u.z, ev[4 * j + 2]);
-              ev[4 * j + 3] = fmaf(c0, u.w, ev[4 * j + 3]);
-            }
-          }
-        }
-        // samples 16 q .. 16 q + 15 of the window and their mirrors, at step
-        // positions (lane / L) N + ...: two half rows of the staging tile
-        const uint32_t base = (lane / K::L) * N;
-        const uint32_t f0 = base + 16 * q, m0 = base + N - 16 * (q + 1);
-        float xf[16], xm[16];
-#pragma unroll
-        for (int i = 0; i < 16; ++i) {
-          xf[i] = ev[i] + od[i];
-          xm[15 - i] = ev[i] - od[i];
-        }
-        unsigned char *const rf = otile + (f0 >> 5) * 128;
-        unsigned char *const rm = otile + (m0 >> 5) * 128;
-        const uint32_t cf = (f0 & 31u) >> 2, cm = (m0 & 31u) >> 2;
-        const uint32_t sf = (f0 >> 5) & 7u, sm = (m0 >> 5) & 7u;
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          *reinterpret_cast<float4 *>(rf + (((cf + j) ^ sf) << 4)) =
-              make_float4(xf[4 * j], xf[4 * j + 1], xf[4 * j + 2], xf[4 * j + 3]);
-          *reinterpret_cast<float4 *>(rm + (((cm + j) ^ sm) << 4)) =
-              make_float4(xm[4 * j], xm[4 * j + 1], xm[4 * j + 2], xm[4 * j + 3]);
-        }
-      } else {
-        // windows w0 + M lane + j, j < M: their pairs n < P
-        const uint32_t wl = w0 + K::M * lane;
-        const float *bq = bas;
-#pragma unroll 1
-        for (uint32_t k = 0; k < dd.kz; ++k) {
-          const float *dq = deq0 + (k < dd.B1 ? 0 : kZStride);
-          float b[K::P];
-#pragma unroll
-          for (int i = 0; i < K::P; i += 4) {
-            const float4 u = *reinterpret_cast<const float4 *>(bq + k * K::BROW + i);
-            b[i] = u.x;
-            if (i + 1 < K::P) b[i + 1] = u.y;
-            if (i + 2 < K::P) b[i + 2] = u.z;
-            if (i + 3 < K::P) b[i + 3] = u.w;
-          }
-#pragma unroll
-          for (int j = 0; j < K::M; ++j) {
-            const float c = wl + j < nwin ? dq[stage[(wl + j) * dd.E + k]] : 0.0f;
-#pragma unroll
-            for (int i = 0; i < K::P; ++i) {
-              if (k & 1u)
-                od[j * K::P + i] = fmaf(c, b[i], od[j * K::P + i]);
-              else
-                ev[j * K::P + i] = fmaf(c, b[i], ev[j * K::P + i]);
-            }
-          }
-        }
-        // the lane's row: windows j at positions j N .. j N + N - 1
-        float x[32];
-#pragma unroll
-        for (int j = 0; j < K::M; ++j)
-#pragma unroll
-          for (int i = 0; i < K::P; ++i) {
-            x[j * N + i] = ev[j * K::P + i] + od[j * K::P + i];
-            x[j * N + N - 1 - i] = ev[j * K::P + i] - od[j * K::P + i];
-          }
-#pragma unroll
-        for (int c = 0; c < 8; ++c)
-          *reinterpret_cast<float4 *>(row + ((c ^ sx) << 4)) = make_float4(x[4 * c], x[4 * c + 1], x[4 * c + 2],
-                                                                           x[4 * c + 3]);
-      }
-      const uint64_t s0 = (win0 + w0) * N;  // first sample of the step in the segment
-      if (tma_step) {
-        fence_async_shared();
-        __syncwarp();
-        if (lane == 0) tma_store_rows(&out_map, otile, (int32_t)((sg.out_offset + s0) >> 5));
-        tma_pending = true;
-      } else {
-        __syncwarp();  // rows are written by other lanes
-        const uint64_t lim = (uint64_t)(nwin - w0) * N < S - s0 ? (uint64_t)(nwin - w0) * N : S - s0;
-        const uint64_t r0 = (uint64_t)lane * 32;
-        if (r0 < lim) {
-          const uint32_t m = lim - r0 < 32 ? (uint32_t)(lim - r0) : 32u;
-          store_row(row, sx, p.out + sg.out_offset + s0 + r0, m, vec32, aligned & 1u);
-        }
-        __syncwarp();  // before the next step rewrites the tile
-      }
+    ShapeOut o{otile, row, sx, lane, &out_map, wp.out_tma && (aligned & 4u),
+               (aligned & 2u) && (reinterpret_cast<uintptr_t>(p.out) & 31u) == 0, (aligned & 1u) != 0};
+    switch (dd.N) {  // the tile's domain: uniform over the warp
+      case 4: shape_transform<4>(p, sg, dd, smem_raw, stage, win0, nwin, o, tma_pending); break;
+      case 8: shape_transform<8>(p, sg, dd, smem_raw, stage, win0, nwin, o, tma_pending); break;
+      case 16: shape_transform<16>(p, sg, dd, smem_raw, stage, win0, nwin, o, tma_pending); break;
+      case 32: shape_transform<32>(p, sg, dd, smem_raw, stage, win0, nwin, o, tma_pending); break;
+      case 64: shape_transform<64>(p, sg, dd, smem_raw, stage, win0, nwin, o, tma_pending); break;
+      case 128: shape_transform<128>(p, sg, dd, smem_raw, stage, win0, nwin, o, tma_pending); break;
+      default: break;  // not a shape of this kernel (the plan never sends one)
     }
     __syncwarp();  // the level bytes are rewritten by the next tile
   }
   if (tma_pending && lane == 0) tma_wait_all();
 }
 
-template <int N, int WARPS>
-void *sptr() {
-  return reinterpret_cast<void *>(&k_decode_shape<N, WARPS>);
-}
-
-template <int WARPS>
-void *spick_n(uint32_t N) {
-  switch (N) {
-    case 4: return sptr<4, WARPS>();
-    case 8: return sptr<8, WARPS>();
-    case 16: return sptr<16, WARPS>();
-    case 32: return sptr<32, WARPS>();
-    case 64: return sptr<64, WARPS>();
-    case 128: return sptr<128, WARPS>();
-    default: return nullptr;
-  }
-}
-
-void *spick(uint32_t N, uint32_t threads) {
+void *spick(uint32_t threads) {
   switch (threads) {
-    case 256: return spick_n<8>(N);
-    case 512: return spick_n<16>(N);
-    case 768: return spick_n<24>(N);
+    case 256: return reinterpret_cast<void *>(&k_decode_shape<8>);
+    case 512: return reinterpret_cast<void *>(&k_decode_shape<16>);
+    case 768: return reinterpret_cast<void *>(&k_decode_shape<24>);
     default: return nullptr;
   }
 }
@@ -373,13 +381,13 @@ bool shape_supported(uint32_t N) { return N >= 4 && N <= 128 && (N & (N - 1)) ==
 
 uint32_t shape_windows_per_tile(uint32_t N, uint32_t E) { return shape_tile_windows(N, E); }
 
-size_t shape_smem_layout(uint32_t N, uint32_t threads, const uint32_t *lmax, const uint32_t *E, uint32_t n_domains,
-                         WarpParams *wp) {
+size_t shape_smem_layout(uint32_t threads, const uint32_t *lmax, const uint32_t *N, const uint32_t *E,
+                         uint32_t n_domains, WarpParams *wp) {
   size_t o = align16(sizeof(DomS) * (n_domains ? n_domains : 1));
   for (uint32_t d = 0; d < n_domains; ++d) {
     o += align16((size_t)2 << lmax[d]);
     o += align16(3u * kZStride * 4);
-    o += align16((size_t)E[d] * shape_brow(N) * 4);
+    o += align16((size_t)E[d] * shape_brow(N[d]) * 4);
   }
   o = align16(o);
   *wp = WarpParams{};
@@ -390,8 +398,8 @@ size_t shape_smem_layout(uint32_t N, uint32_t threads, const uint32_t *lmax, con
   return o + warps * kMiscBytes + 1023 + warps * kOutTile;  // + alignment of the staging tiles
 }
 
-cudaError_t shape_smem_config(uint32_t N, uint32_t threads, size_t smem) {
-  void *k = spick(N, threads);
+cudaError_t shape_smem_config(uint32_t threads, size_t smem) {
+  void *k = spick(threads);
   if (!k) return cudaErrorInvalidValue;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout,
                                        (int)cudaSharedmemCarveoutMaxShared);
@@ -399,16 +407,16 @@ cudaError_t shape_smem_config(uint32_t N, uint32_t threads, size_t smem) {
   return set_dynamic_smem_limit(k, smem);
 }
 
-cudaError_t shape_occupancy(uint32_t N, uint32_t threads, size_t smem, int *ctas_per_sm) {
-  void *k = spick(N, threads);
+cudaError_t shape_occupancy(uint32_t threads, size_t smem, int *ctas_per_sm) {
+  void *k = spick(threads);
   if (!k) return cudaErrorInvalidValue;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, k, (int)threads, smem);
 }
 
-cudaError_t launch_shape(const DecodeParams &p, const WarpParams &wp, const CUtensorMap &out_map, uint32_t N,
-                         uint32_t threads, uint32_t grid, size_t smem, cudaStream_t stream) {
+cudaError_t launch_shape(const DecodeParams &p, const WarpParams &wp, const CUtensorMap &out_map, uint32_t threads,
+                         uint32_t grid, size_t smem, cudaStream_t stream) {
   if (p.tile_end <= p.tile_begin || grid == 0) return cudaSuccess;
-  void *k = spick(N, threads);
+  void *k = spick(threads);
   if (!k) return cudaErrorInvalidValue;
   DecodeParams pp = p;
   WarpParams ww = wp;

@@ -47,8 +47,8 @@ struct fptc_plan {
   size_t device_bytes = 0;
   // launch settings
   int kind = FPTC_KERNEL_GENERIC;   // fptc_kernel in use
-  uint32_t shape_n = 0;   // every domain shares this N and the warp-tile kernel of decode_shape.cu serves it
-                          // (0: not such a plan; N = 32, E = 16 plans use decode_warp.cu)
+  bool shape = false;     // every domain has a power-of-two N in [4, 128] and the warp-tile kernel of
+                          // decode_shape.cu serves the plan (N = 32, E = 16 plans use decode_warp.cu)
   WarpParams wp{};
   TcParams tp{};
   uint32_t threads = 256, grid = 0, ctas_per_sm = 0;
@@ -139,7 +139,7 @@ void unit_tables(const fptc_domain &d, float unit[2][256]) {
 void layout_tiles(fptc_plan *p, uint32_t tile_samples) {
   p->coef_cap = 0;
   p->gx_cap = 0;
-  const bool shape = p->kind == FPTC_KERNEL_WARP_TILE && p->shape_n != 0;
+  const bool shape = p->kind == FPTC_KERNEL_WARP_TILE && p->shape;
   for (auto &dd : p->dom_dev) {
     dd.tile_windows = shape ? shape_windows_per_tile(dd.N, dd.E) : std::max<uint32_t>(1u, tile_samples / dd.N);
     p->coef_cap = std::max(p->coef_cap, dd.tile_windows * dd.E);
@@ -157,10 +157,11 @@ void layout_tiles(fptc_plan *p, uint32_t tile_samples) {
 
 fptc_status configure_launch(fptc_plan *p) {
   uint32_t threads = p->opts.threads ? p->opts.threads : (p->kind == FPTC_KERNEL_TENSOR ? 512u : 256u);
-  const bool shape = p->kind == FPTC_KERNEL_WARP_TILE && p->shape_n != 0;
-  std::vector<uint32_t> lm, es;
+  const bool shape = p->kind == FPTC_KERNEL_WARP_TILE && p->shape;
+  std::vector<uint32_t> lm, ns, es;
   for (const auto &d : p->domains) {
     lm.push_back(d.lmax);
+    ns.push_back(d.N);
     es.push_back(d.E);
   }
   if (p->kind == FPTC_KERNEL_WARP_TILE && p->opts.threads == 0) {
@@ -173,7 +174,7 @@ fptc_status configure_launch(fptc_plan *p) {
     threads = 128;
     if (shape) {
       for (uint32_t t : {512u, 256u})
-        if (shape_smem_layout(p->shape_n, t, lm.data(), es.data(), (uint32_t)lm.size(), &probe) <= (size_t)optin) {
+        if (shape_smem_layout(t, lm.data(), ns.data(), es.data(), (uint32_t)lm.size(), &probe) <= (size_t)optin) {
           threads = t;
           break;
         }
@@ -232,10 +233,10 @@ fptc_status configure_launch(fptc_plan *p) {
     }
     if (e == cudaSuccess) occ = std::min<int>(occ, 1);
   } else if (shape) {
-    p->smem = shape_smem_layout(p->shape_n, threads, lm.data(), es.data(), (uint32_t)lm.size(), &p->wp);
-    e = shape_smem_config(p->shape_n, threads, p->smem);
+    p->smem = shape_smem_layout(threads, lm.data(), ns.data(), es.data(), (uint32_t)lm.size(), &p->wp);
+    e = shape_smem_config(threads, p->smem);
     if (e != cudaSuccess) return cuda_fail(e, "decode shared-memory size");
-    e = shape_occupancy(p->shape_n, threads, p->smem, &occ);
+    e = shape_occupancy(threads, p->smem, &occ);
   } else if (p->kind == FPTC_KERNEL_WARP_TILE) {
     p->smem = warp_smem_layout(threads, lm.data(), (uint32_t)lm.size(), &p->wp);
     e = warp_smem_config(threads, p->smem);
@@ -398,7 +399,7 @@ cudaError_t run_range(const fptc_plan *p, const IndexParams &ip0, const DecodePa
     CUtensorMap map;
     std::memset(&map, 0, sizeof(map));
     wp.out_tma = encode_out_map(&map, dp.out, p->out_extent) ? 1u : 0u;
-    if (p->shape_n) return launch_shape(dp, wp, map, p->shape_n, p->threads, grid, p->smem, st);
+    if (p->shape) return launch_shape(dp, wp, map, p->threads, grid, p->smem, st);
     return launch_warp(dp, wp, map, p->threads, grid, p->smem, st);
   }
   if (p->kind == FPTC_KERNEL_TENSOR) {
@@ -492,18 +493,18 @@ fptc_status fptc_plan_create(fptc_plan **out, int device, const fptc_domain *dom
     set_error("unknown kernel %u", o.kernel);
     return FPTC_ERR_INVALID_ARGUMENT;
   }
-  bool all_fixed = true, same_n = n_domains > 0;
+  bool all_fixed = true, all_pow2 = n_domains > 0;
   for (uint32_t d = 0; d < n_domains; ++d) {
     all_fixed = all_fixed && domains[d].N == 32 && domains[d].E == 16;
-    same_n = same_n && domains[d].N == domains[0].N;
+    all_pow2 = all_pow2 && shape_supported(domains[d].N);
   }
   const bool fixed_ok = all_fixed && n_domains <= kWarpMaxDomains;
-  // other shapes: one power-of-two N for every domain
-  const bool shape_ok = !all_fixed && same_n && shape_supported(domains[0].N) && n_domains <= kWarpMaxDomains;
+  // other shapes: a power-of-two N in [4, 128] for every domain
+  const bool shape_ok = !all_fixed && all_pow2 && n_domains <= kWarpMaxDomains;
   const bool warp_ok = fixed_ok || shape_ok;
   if ((o.kernel == FPTC_KERNEL_BLOCK_TILE && !all_fixed) || (o.kernel == FPTC_KERNEL_WARP_TILE && !warp_ok)) {
-    set_error("the block-tile kernel needs N = 32, E = 16 in every domain; the warp-tile kernel that, or one "
-              "power-of-two N in [4, 128] shared by every domain (at most %u domains)", kWarpMaxDomains);
+    set_error("the block-tile kernel needs N = 32, E = 16 in every domain; the warp-tile kernel that, or a "
+              "power-of-two N in [4, 128] in every domain (at most %u domains)", kWarpMaxDomains);
     return FPTC_ERR_UNSUPPORTED;
   }
   if (o.idct != FPTC_IDCT_FP32 || o.kernel == FPTC_KERNEL_TENSOR) {
@@ -527,9 +528,12 @@ fptc_status fptc_plan_create(fptc_plan **out, int device, const fptc_domain *dom
       if (fixed_ok) {
         fits = warp_smem_layout(128, lm.data(), n_domains, &probe) <= (size_t)optin;
       } else {
-        std::vector<uint32_t> es(n_domains);
-        for (uint32_t d = 0; d < n_domains; ++d) es[d] = domains[d].E;
-        fits = shape_smem_layout(domains[0].N, 256, lm.data(), es.data(), n_domains, &probe) <= (size_t)optin;
+        std::vector<uint32_t> ns(n_domains), es(n_domains);
+        for (uint32_t d = 0; d < n_domains; ++d) {
+          ns[d] = domains[d].N;
+          es[d] = domains[d].E;
+        }
+        fits = shape_smem_layout(256, lm.data(), ns.data(), es.data(), n_domains, &probe) <= (size_t)optin;
       }
     }
     o.kernel = fits ? FPTC_KERNEL_WARP_TILE : (all_fixed ? FPTC_KERNEL_BLOCK_TILE : FPTC_KERNEL_GENERIC);
@@ -635,7 +639,7 @@ fptc_status fptc_plan_create(fptc_plan **out, int device, const fptc_domain *dom
   }
   p->lut_cap = 1u << max_lmax;
   p->kind = (int)o.kernel;
-  p->shape_n = shape_ok ? domains[0].N : 0u;
+  p->shape = shape_ok;
 
   // ---- tile queue: segments ordered by output offset
   p->queue.resize(n_segments);
@@ -1021,11 +1025,11 @@ fptc_status fptc_plan_autotune(fptc_plan *p, const uint64_t *d_words, const uint
     if (th > 512) {
       if (fixed && p->domains.size() <= kWarpMaxDomains)
         cands.push_back({FPTC_KERNEL_WARP_TILE, warp_tile_windows() * 32, th});
-      if (p->shape_n && th == 768) cands.push_back({FPTC_KERNEL_WARP_TILE, 4096, th});
+      if (p->shape && th == 768) cands.push_back({FPTC_KERNEL_WARP_TILE, 4096, th});
       continue;
     }
     if (fixed && p->domains.size() <= kWarpMaxDomains) cands.push_back({FPTC_KERNEL_WARP_TILE, warp_tile_windows() * 32, th});
-    if (p->shape_n && th >= 256) cands.push_back({FPTC_KERNEL_WARP_TILE, 4096, th});
+    if (p->shape && th >= 256) cands.push_back({FPTC_KERNEL_WARP_TILE, 4096, th});
     if (fixed)
       for (uint32_t ts : {4096u, 8192u}) cands.push_back({FPTC_KERNEL_BLOCK_TILE, ts, th});
     else

@@ -1,10 +1,10 @@
 """GPU parity of the warp-tile kernel for window shapes other than N = 32,
-E = 16 (one power-of-two N in [4, 128] shared by every domain of a plan, any
-E <= N per domain; Table 1 ranges): levels bit-exact and samples within the
+E = 16 (a power-of-two N in [4, 128] for every domain of a plan, several N in
+one batch, any E <= N per domain; Table 1 ranges): levels bit-exact and samples within the
 FP32 bound against the FP64 oracle, for random levels over every bin, ragged
 lengths (partial windows, partial tiles, partial output steps), outputs at
 128-byte boundaries (TMA stores) and at odd offsets (per-lane stores), several
-kept-bin counts in one batch, trained tables on synthetic signals, and tiles
+kept-bin counts and window sizes in one batch, trained tables on synthetic signals, and tiles
 chained across a segment the index rejects."""
 import numpy as np
 import pytest
@@ -76,15 +76,41 @@ def test_shape_thread_counts(threads):
 
 
 def test_shape_default_choice():
-    """Plans whose domains share a power-of-two N get the warp-tile kernel by
-    default; mixed N falls back to the generic kernel."""
+    """Plans whose domains all have a power-of-two N get the warp-tile kernel by
+    default, several N in one plan included; another N anywhere falls back to
+    the generic kernel."""
     b = _random_batch(16, [8], seed=3)
     assert make_plan(b).info["kernel"] == WARP_TILE
     cl = np.full(256, 8, np.uint8)
-    doms = [oracle.Domain(16, 8, 2, 8, 30.0, 0.02, (3.0, 1.0, 0.0), 8, cl),
-            oracle.Domain(64, 8, 2, 8, 30.0, 0.02, (3.0, 1.0, 0.0), 8, cl)]
-    lv = [np.full(d.windows(1000) * d.E, 128, np.uint8) for d in doms]
-    assert make_plan(crafted_batch(doms, lv, [1000, 1000], [0, 1])).info["kernel"] == 1
+    for n2, want in ((64, WARP_TILE), (24, 1)):
+        doms = [oracle.Domain(16, 8, 2, 8, 30.0, 0.02, (3.0, 1.0, 0.0), 8, cl),
+                oracle.Domain(n2, 8, 2, 8, 30.0, 0.02, (3.0, 1.0, 0.0), 8, cl)]
+        lv = [np.full(d.windows(1000) * d.E, 128, np.uint8) for d in doms]
+        assert make_plan(crafted_batch(doms, lv, [1000, 1000], [0, 1])).info["kernel"] == want
+
+
+@pytest.mark.parametrize("align", [32, 1])
+def test_shape_mixed_window_sizes(align):
+    """Domains of N = 4, 16, 32 (E = 16 and E = 8), 64 and 128 in one batch, streams
+    interleaved in the output: each tile takes its domain's transform."""
+    cl = np.full(256, 8, np.uint8)
+    shapes = [(4, 4, 1, 3), (16, 8, 2, 8), (32, 16, 2, 16), (32, 8, 2, 6), (64, 24, 3, 20), (128, 64, 2, 64)]
+    doms = [oracle.Domain(N, E, B1, B2, 25.0 + i, 0.03, (2.0 + i, 1.0 + 0.25 * i, 0.0), 8, cl)
+            for i, (N, E, B1, B2) in enumerate(shapes)]
+    rng = np.random.default_rng(99 + align)
+    lens, idx, levels = [], [], []
+    for r in range(5):
+        for d, dom in enumerate(doms):
+            S = int(rng.integers(1, 60000)) if r else dom.N * 300 + d
+            lens.append(S)
+            idx.append(d)
+            levels.append(rng.integers(0, 256, size=dom.windows(S) * dom.E).astype(np.uint8))
+    b = crafted_batch(doms, levels, lens, idx)
+    plan = make_plan(b, out_align=align, out_base=0 if align == 32 else 1)
+    assert plan.info["kernel"] == WARP_TILE
+    _, _, out, lv = gpu_decode(plan, b)
+    compare_with_oracle(plan, b, out, lv)
+    assert plan.device_status()[0] == 0
 
 
 @pytest.mark.parametrize("N,E", [(64, 32), (16, 8), (128, 64)])
