@@ -384,6 +384,46 @@ def decode_many(batch: EncodedBatch, idx=None, n_threads: int = 0, want_levels: 
     return x, out_off, lv, lv_off
 
 
+# ---- decoder-side scales at a fixed rate ---------------------------------------------
+
+def fit_zone_scales(levels_list, lengths, domain_idx, domains, x_list) -> np.ndarray:
+    """The per-zone scales A_z of every domain that minimise the squared error
+    sum_i ||x_i - x_hat_i(A)||^2 over the given streams, their levels (hence
+    their bit rate) fixed.  Every dequantized coefficient is A_z times a
+    function of its level (Sec. 3.2, Eq. 2 and Eq. 3 inverted), so x_hat is
+    linear in A: x_hat = sum_z A_z u_z, u_z the reconstruction with A_z = 1 and
+    the other zones 0, and the minimiser solves the normal equations
+    G A = b, G_yz = sum <u_y, u_z>, b_z = sum <u_z, x>, per domain (FP64).
+    Zones a domain does not use (no bin in them) keep their scale.  Returns
+    float64 [n_domains, 3]."""
+    out = np.array([np.asarray(d.A, np.float64) for d in domains])
+    for di, d in enumerate(domains):
+        zones = [z for z in (0, 1) if (z == 0 and d.B1 > 0) or (z == 1 and d.B2 > d.B1)]
+        if not zones:
+            continue
+        units = [Domain(d.N, d.E, d.B1, d.B2, d.mu, d.alpha1, tuple(1.0 if q == z else 0.0 for q in range(3)),
+                        d.lmax, d.code_len) for z in zones]
+        G = np.zeros((len(zones), len(zones)))
+        b = np.zeros(len(zones))
+        seen = False
+        for lv, S, k, x in zip(levels_list, lengths, domain_idx, x_list):
+            if k != di or S == 0:
+                continue
+            seen = True
+            u = [reconstruct(lv, int(S), ud) for ud in units]
+            xx = np.asarray(x, np.float64)
+            for i in range(len(zones)):
+                b[i] += float(np.dot(u[i], xx))
+                for j in range(len(zones)):
+                    G[i, j] += float(np.dot(u[i], u[j]))
+        if not seen:
+            continue
+        sol = np.linalg.solve(G, b)
+        for i, z in enumerate(zones):
+            out[di, z] = sol[i]
+    return out
+
+
 # ---- metrics (Sec. 5.1) ---------------------------------------------------------------
 
 def prd(x, x_hat) -> float:
