@@ -1,4 +1,4 @@
-"""ctypes binding of libfptc (include/fptc.h, include/fptc_codec.h): struct mirrors,
+"""ctypes binding of libfptc (include/fptc.h, include/fptc_codec.h, include/fptc_encoder.h): struct mirrors,
 argument types and status checking.  Argument marshalling only."""
 from __future__ import annotations
 
@@ -13,6 +13,7 @@ _d, _f, _p = ctypes.c_double, ctypes.c_float, ctypes.c_void_p
 
 OK, INVALID_ARGUMENT, UNSUPPORTED, OUT_OF_MEMORY, CUDA_ERROR, CORRUPT_STREAM = range(6)
 FLAG_SYMLEN_RANGE, FLAG_BIT_OVERRUN, FLAG_INVALID_CODE, FLAG_SYMBOL_COUNT, FLAG_TIMEOUT = 1, 2, 4, 8, 16
+ENC_FLAG_NO_CODE, ENC_FLAG_ROOM = 1, 2
 STAGE_INDEX, STAGE_DECODE = 1, 2
 IDCT = {"fp32": 0, "tf32": 1, "bf16x3": 2, "tf32x3": 3}
 SCHEDULE = {"persistent": 0, "per_segment": 1, "three_kernel": 2}
@@ -73,6 +74,13 @@ SIGNATURES = {
     "fptc_word_capacity": (_u64, [_p, _u64]),
     "fptc_encode_stream": (_i32, [_p, _p, _u64, _p, _p, _u64, _p, _p]),
     "fptc_encode_batch": (_i32, [_p, _u32, _p, _p, _p, _p, _u64, _p, _p, _p, _p, _i32]),
+    "fptc_encoder_create": (_i32, [ctypes.POINTER(_p), _i32, _p, _u32, _p, _u64]),
+    "fptc_encoder_destroy": (None, [_p]),
+    "fptc_encoder_levels": (_u64, [_p]),
+    "fptc_encoder_level_offsets": (_i32, [_p, _p]),
+    "fptc_encode_device": (_i32, [_p, _p, _p, _p, _p, _p, _p]),
+    "fptc_pack_device": (_i32, [_p, _p, _p, _p, _p, _p]),
+    "fptc_encoder_status": (_i32, [_p, ctypes.POINTER(_u32), ctypes.POINTER(_u64)]),
 }
 
 

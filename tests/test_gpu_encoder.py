@@ -1,0 +1,147 @@
+"""GPU encoder (Eq. 1, the zone quantizer of Sec. 3.2, Alg. 1) against the
+oracle: packing given levels is bit-exact (ragged and empty streams, one-bit
+and maximum-length codes); levels from signals equal the oracle's except where
+a coefficient sits on a rounding boundary (then by one level), words and
+symbol counts are exact wherever the levels are; the GPU decoder reads what the
+GPU encoder wrote; rooms that are too small and levels without a codeword are
+flagged on the device."""
+import numpy as np
+import pytest
+
+import oracle
+import siggen
+
+from gpu_util import compare_with_oracle, make_plan, oracle_domains, product_domain
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2605_01086_gb300 import build
+    build()
+
+
+def _oracle_stream(x, d):
+    return oracle.encode_stream(x, d)  # words, symlen, levels
+
+
+def _room_words(enc, words, symlen, n_words, i):
+    a, n = int(enc.room_offsets[i]), int(n_words[i])
+    return words[a:a + n], symlen[a:a + n]
+
+
+@pytest.mark.parametrize("case", ["trained", "one_bit", "max_length"])
+def test_pack_matches_oracle(case):
+    from paper_2605_01086_gb300 import Encoder
+    rng = np.random.default_rng(5)
+    if case == "trained":
+        doms = oracle_domains()
+        lens = [0, 1, 31, 32, 33, 4097, 70000, 1000, 12345, 2]
+        idx = [i % 4 for i in range(len(lens))]
+        levels = []
+        for S, di in zip(lens, idx):
+            x = siggen.signal(di, int(siggen.stream_seed(7, len(levels))), S)
+            levels.append(_oracle_stream(x, doms[di])[2] if S else np.zeros(0, np.uint8))
+    else:
+        cl = np.zeros(256, np.uint8)
+        if case == "one_bit":   # levels 0 and 128 with one-bit codes: 64 codewords per word
+            cl[128], cl[0] = 1, 1
+            lmax, pool = 8, np.array([128, 0])
+        else:                   # levels 128..255 with 16-bit codes (lmax): 4 codewords per word
+            cl[:128], cl[128:] = 8, 16
+            lmax, pool = 16, np.arange(128, 256)
+        d = oracle.Domain(32, 16, 2, 16, 50.0, 0.004, (1.0, 1.0, 0.0), lmax, cl)
+        doms = [d]
+        lens = [0, 5, 3200, 32 * 999 + 7]
+        idx = [0] * len(lens)
+        levels = []
+        for S in lens:
+            W = d.windows(S) * d.E
+            levels.append(rng.choice(pool, size=W).astype(np.uint8) if W else np.zeros(0, np.uint8))
+    enc = Encoder([product_domain(d) for d in doms], lens, idx)
+    lv = np.zeros(max(1, enc.n_levels), np.uint8)
+    for i, L in enumerate(levels):
+        lv[int(enc.level_offsets[i]):int(enc.level_offsets[i]) + L.size] = L
+    words, symlen, n_words = enc.pack(torch.from_numpy(lv).to(enc.device))
+    assert enc.status()[0] == 0
+    wh, sh, nh = words.cpu().numpy().view(np.uint64), symlen.cpu().numpy(), n_words.cpu().numpy()
+    for i, L in enumerate(levels):
+        codes = oracle.canonical_codes(doms[idx[i]].code_len, doms[idx[i]].lmax)
+        w_o, s_o = oracle.pack_symlen(L, codes, doms[idx[i]].code_len) if L.size else (np.zeros(0, np.uint64),
+                                                                                       np.zeros(0, np.uint8))
+        w_g, s_g = _room_words(enc, wh, sh, nh, i)
+        np.testing.assert_array_equal(w_g, w_o, err_msg=f"words of stream {i}")
+        np.testing.assert_array_equal(s_g, s_o, err_msg=f"symlen of stream {i}")
+
+
+def test_encode_matches_oracle_and_round_trips():
+    from paper_2605_01086_gb300 import Encoder, Plan, codec
+    doms = oracle_domains()
+    wl = siggen.mixed_10000_logu(n=40, lo=1, hi=150000)
+    flat, offs = siggen.signals(wl.domains, wl.seeds, wl.lengths)
+    enc = Encoder([product_domain(d) for d in doms], wl.lengths, wl.domains)
+    x = torch.from_numpy(flat).to(enc.device)
+    lv = torch.empty(max(1, enc.n_levels), dtype=torch.uint8, device=enc.device)
+    words, symlen, n_words = enc.encode(x, levels=lv)
+    assert enc.status()[0] == 0
+    wh, sh, nh, lh = (words.cpu().numpy().view(np.uint64), symlen.cpu().numpy(), n_words.cpu().numpy(),
+                      lv.cpu().numpy())
+    total = mism_total = 0
+    exact = 0
+    for i in range(wl.n_streams):
+        d = doms[wl.domains[i]]
+        S = int(wl.lengths[i])
+        w_o, s_o, l_o = _oracle_stream(flat[int(offs[i]):int(offs[i]) + S], d)
+        l_g = lh[int(enc.level_offsets[i]):int(enc.level_offsets[i]) + l_o.size]
+        mism = np.flatnonzero(l_g != l_o)
+        total += l_o.size
+        mism_total += mism.size
+        assert np.all(np.abs(l_g[mism].astype(int) - l_o[mism].astype(int)) == 1), i
+        if mism.size == 0:
+            w_g, s_g = _room_words(enc, wh, sh, nh, i)
+            np.testing.assert_array_equal(w_g, w_o)
+            np.testing.assert_array_equal(s_g, s_o)
+            exact += 1
+    assert mism_total <= max(2, total // 100000)
+    assert exact >= wl.n_streams - 2
+    # the decoder reads the GPU-encoded streams: levels and samples against the oracle's
+    # decode of those same words
+    segs = enc.segments(n_words, codec.packed_out_offsets(wl.lengths, 32))
+    plan = Plan([product_domain(d) for d in doms], segs)
+    out = plan.empty_out()
+    lv2 = torch.empty(plan.info["n_levels_total"], dtype=torch.uint8, device=plan.device)
+    plan.decode(words, symlen, out=out, levels=lv2)
+    assert plan.device_status()[0] == 0
+    b = oracle.EncodedBatch(wh, sh, np.ascontiguousarray(enc.room_offsets), nh[:wl.n_streams].astype(np.uint64),
+                            np.asarray(wl.lengths, np.uint64), np.asarray(wl.domains, np.int32), doms)
+    compare_with_oracle(plan, b, out, lv2)
+
+
+def test_room_and_code_flags():
+    from paper_2605_01086_gb300 import Encoder, _lib
+    doms = oracle_domains()
+    wl = siggen.mixed_10000_logu(n=6, lo=5000, hi=9000)
+    flat, _ = siggen.signals(wl.domains, wl.seeds, wl.lengths)
+    from paper_2605_01086_gb300.codec import word_capacity
+    pd = [product_domain(d) for d in doms]
+    room = [word_capacity(pd[wl.domains[i]], int(wl.lengths[i])) for i in range(6)]
+    room[3] = 2
+    enc = Encoder(pd, wl.lengths, wl.domains, room=room)
+    enc.encode(torch.from_numpy(flat).to(enc.device))
+    st, flags, first = enc.status()
+    assert st == _lib.CORRUPT_STREAM and flags & _lib.ENC_FLAG_ROOM and first == 3
+    assert enc.status()[0] == 0   # cleared
+    # a level whose domain has no codeword for it
+    cl = np.zeros(256, np.uint8)
+    cl[128], cl[10] = 1, 1
+    d = oracle.Domain(32, 16, 2, 16, 50.0, 0.004, (1.0, 1.0, 0.0), 8, cl)
+    enc2 = Encoder([product_domain(d)], [320], [0])
+    lv = np.full(enc2.n_levels, 128, np.uint8)
+    lv[37] = 11
+    enc2.pack(torch.from_numpy(lv).to(enc2.device))
+    st, flags, first = enc2.status()
+    assert st == _lib.CORRUPT_STREAM and flags & _lib.ENC_FLAG_NO_CODE and first == 0
