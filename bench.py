@@ -443,6 +443,36 @@ def run(args):
                          "kernel": "k_backward_warp (adjoint)"}}
         del lv, gco, sc
 
+    # the GPU encoder (Eq. 1, zone quantizer, Alg. 1) re-encoding the decoded batch in place:
+    # same streams and domains, samples read from the decoder's output layout
+    if not args.no_encode and rank == 0:
+        from paper_2605_01086_gb300 import Encoder
+        enc = Encoder(doms, wl.lengths, wl.domains, device=local, in_offsets=batch.segments["out_offset"])
+        ew, es, enw = enc.buffers()
+        elv = torch.empty(max(1, enc.n_levels), dtype=torch.uint8, device=dev)
+        lvd = torch.empty_like(elv)  # the original streams' levels, same layout (caller order, packed)
+        with torch.cuda.stream(stream):
+            plan.decode(w, s, out=out, levels=lvd, stream=stream)
+            enc.encode(out, ew, es, enw, levels=elv, stream=stream)
+            ems = time_steps(lambda: enc.encode(out, ew, es, enw, levels=elv, stream=stream), 3, stream, torch)
+            pms = time_steps(lambda: enc.pack(elv, ew, es, enw, stream=stream), 3, stream, torch)
+        torch.cuda.synchronize()
+        est = enc.status()[0]
+        n_enc_words = int(enw[:wl.n_streams].sum())
+        same = float((lvd[:enc.n_levels] == elv[:enc.n_levels]).double().mean())
+        del lvd
+        line["gpu_encode"] = {"value": 4.0 * n_samples / (statistics.median(ems) / 1e3) / 1e9,
+                              "unit": "GB/s of float32 input", "ms_per_step": statistics.median(ems),
+                              "pack_ms": statistics.median(pms),
+                              "levels_ms": statistics.median(ems) - statistics.median(pms),
+                              "compressed_bytes": 9 * n_enc_words, "status": est,
+                              "levels_equal_to_decoded_fraction": same,
+                              "input": "the decoded batch (re-encoding)",
+                              "arithmetic": "compensated FP32 transform and FP32 quantizer, FP64 where a bin is near a "
+                                            "level boundary (levels equal to the FP64 encoder's)"}
+        enc.close()
+        del ew, es, enw, elv
+
     # the paper's three-kernel GPU design on the same streams (global per-word offsets and
     # level array, one thread per output sample), for comparison with the fused kernels
     if not args.no_plain and rank == 0:
@@ -583,6 +613,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-forms", action="store_true")
+    ap.add_argument("--no-encode", action="store_true", help="skip the GPU encoder line")
     ap.add_argument("--kernel", default=None, help="fix the decode kernel (no autotuning): warp_tile, block_tile, generic")
     ap.add_argument("--threads", type=int, default=0)
     ap.add_argument("--sweep", action="store_true", help="throughput over window size N and kept bins E instead")
