@@ -2,7 +2,7 @@
 
 Python binding (ctypes) of ``fptc_oracle.c``: the sequential encoder (Sec. 3.1-3.3,
 Sec. 4.1, Alg. 1) and a plain decoder (bit-serial canonical Huffman, FP64
-inverse transform), plus the analytic adjoint used to judge the decoder's
+inverse transform), plus the analytic adjoint used to check the decoder's
 gradients.  It shares no code with the CUDA path.  Only ``tests/``,
 ``__graft_entry__.smoke()`` and the benchmark's CPU-baseline leg may use it.
 """

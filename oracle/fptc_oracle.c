@@ -5,7 +5,7 @@
  * Transform-based Codec for Efficient Asymmetric Signal Compression",
  * arXiv 2605.01086): the sequential encoder (Sec. 3.1-3.3, Sec. 4.1, Alg. 1) and
  * a deliberately different decoder (bit-serial canonical Huffman, no lookup
- * table; FP64 inverse transform).  It is the judge of the CUDA decoder and shares
+ * table; FP64 inverse transform).  The CUDA decoder is checked against it; it shares
  * no code with it.  Only tests/, __graft_entry__.smoke() and the benchmark's CPU
  * baseline may load it.
  *

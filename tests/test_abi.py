@@ -151,3 +151,33 @@ def test_plan_rejects_bad_metadata_before_touching_a_gpu(L):
     assert b"overlap" in L.fptc_last_error_message()
     # NULL plan handles are rejected, not dereferenced
     assert L.fptc_decode_batch(None, None, None, None, None, None, None) == _lib.INVALID_ARGUMENT
+
+
+def test_encoder_rejects_bad_arguments_before_touching_a_gpu(L):
+    import ctypes
+    _, d = od()
+    cds = codec.c_domains([d])
+    h = ctypes.c_void_p()
+    # rooms of two streams overlap
+    segs = codec.segments_array([0, 5], [10, 10], [320, 320], [0, 320], [0, 0])
+    assert L.fptc_encoder_create(ctypes.byref(h), 0, cds, 1, segs.ctypes.data, 2) == _lib.INVALID_ARGUMENT
+    assert not h.value and b"overlap" in L.fptc_last_error_message()
+    # domain index out of range
+    segs = codec.segments_array([0], [10], [320], [0], [1])
+    assert L.fptc_encoder_create(ctypes.byref(h), 0, cds, 1, segs.ctypes.data, 1) == _lib.INVALID_ARGUMENT
+    assert b"domain" in L.fptc_last_error_message()
+    # an invalid domain (E > N) is rejected by the domain validation
+    bad = codec.Domain(8, 9, 1, 2, 50.0, 0.004, (1.0, 1.0, 0.0), 12, d.code_len.copy())
+    segs = codec.segments_array([0], [10], [320], [0], [0])
+    assert L.fptc_encoder_create(ctypes.byref(h), 0, codec.c_domains([bad]), 1, segs.ctypes.data, 1) \
+        == _lib.INVALID_ARGUMENT
+    # no handle pointer, no domains
+    assert L.fptc_encoder_create(None, 0, cds, 1, segs.ctypes.data, 1) == _lib.INVALID_ARGUMENT
+    assert L.fptc_encoder_create(ctypes.byref(h), 0, None, 0, segs.ctypes.data, 1) == _lib.INVALID_ARGUMENT
+    # NULL encoders are rejected, not dereferenced
+    assert L.fptc_encoder_levels(None) == 0
+    assert L.fptc_encoder_level_offsets(None, None) == _lib.INVALID_ARGUMENT
+    assert L.fptc_encode_device(None, None, None, None, None, None, None) == _lib.INVALID_ARGUMENT
+    assert L.fptc_pack_device(None, None, None, None, None, None) == _lib.INVALID_ARGUMENT
+    assert L.fptc_encoder_status(None, None, None) == _lib.INVALID_ARGUMENT
+    L.fptc_encoder_destroy(None)
