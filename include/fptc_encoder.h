@@ -62,7 +62,8 @@ fptc_status fptc_encoder_level_offsets(const fptc_encoder *enc, uint64_t *offset
  * `stream`.  Without d_levels the first such call allocates the encoder's own
  * level buffer (kept until fptc_encoder_destroy); otherwise nothing is
  * allocated.  Problems found on the device (a level with no codeword, a room
- * too small) are reported by fptc_encoder_status. */
+ * too small) are reported by fptc_encoder_status; such a stream gets
+ * d_n_words[i] = 0 and the contents of its room are undefined. */
 fptc_status fptc_encode_device(fptc_encoder *enc, const float *d_x, uint64_t *d_words, uint8_t *d_symlen,
                                uint64_t *d_n_words, uint8_t *d_levels, fptc_stream stream);
 
