@@ -122,8 +122,10 @@ typedef enum fptc_kernel {
 typedef struct fptc_plan_options {
   uint32_t idct;          /* fptc_idct */
   uint32_t schedule;      /* fptc_schedule */
-  uint32_t tile_samples;  /* target output samples per tile (whole windows); 0 = 8192 if every domain
-                             has N = 32, E = 16, else 4096 */
+  uint32_t tile_samples;  /* target output samples per tile (whole windows) of the block-tile and generic
+                             kernels; 0 = 8192 for the block-tile kernel, else 4096.  The warp-tile and
+                             tensor-core kernels fix their tiles: 128 windows at N = 32, E = 16; at other
+                             shapes about 2048 symbols in whole 1024-sample steps (at most 8) */
   uint32_t threads;       /* threads per CTA: 128, 256 or 512 (also 768, 1024 for the warp-tile kernel at
                              N = 32, E = 16; 256, 512 or 768 for it at other shapes); 0 = 256, or for the
                              warp-tile kernel the most that fit (at most 512 at other shapes) */
