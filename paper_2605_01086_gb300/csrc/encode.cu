@@ -51,7 +51,6 @@ struct EncSeg {
   uint64_t word_offset;
   uint64_t room;
   uint64_t level_offset;
-  uint64_t win_base;    // first global window
   uint64_t n_windows;
   uint64_t block_base;  // first global packing block
   uint32_t domain;
@@ -600,7 +599,6 @@ fptc_status fptc_encoder_create(fptc_encoder **enc, int device, const fptc_domai
     e.word_offset = s.word_offset;
     e.room = s.n_words;
     e.level_offset = lv;
-    e.win_base = win;
     e.n_windows = (s.n_samples + dm.N - 1) / dm.N;
     e.block_base = blocks;
     e.domain = s.domain;
