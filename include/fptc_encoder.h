@@ -9,9 +9,12 @@
  * MSB first into 64-bit words, a new word whenever the next codeword does not
  * fit, symlen[w] = codewords in word w.
  *
- * Levels come from FP64 arithmetic like the host encoder's; where a
- * coefficient sits on a rounding boundary of the quantizer the GPU and a CPU
- * may round to neighbouring levels.  Packing given levels is exact.
+ * Levels are those of the FP64 coefficient computed as the host encoder does
+ * (products and sums rounded separately, in sample order): each bin is computed
+ * in compensated FP32 with an error bound and again in FP64 wherever that bound
+ * straddles a level boundary.  A CPU that sums in another order may round a
+ * coefficient sitting on a boundary to a neighbouring level.  Packing given
+ * levels is exact.
  */
 #ifndef FPTC_ENCODER_H_
 #define FPTC_ENCODER_H_

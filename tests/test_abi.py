@@ -181,3 +181,31 @@ def test_encoder_rejects_bad_arguments_before_touching_a_gpu(L):
     assert L.fptc_pack_device(None, None, None, None, None, None) == _lib.INVALID_ARGUMENT
     assert L.fptc_encoder_status(None, None, None) == _lib.INVALID_ARGUMENT
     L.fptc_encoder_destroy(None)
+
+
+@pytest.mark.parametrize("lmax,lengths", [(16, "max"), (8, "uniform"), (12, "trained"), (4, "one_bit")])
+def test_word_capacity_bounds_alg1(L, lmax, lengths):
+    """fptc_word_capacity (the room the encoders reserve) is at least the number
+    of words Alg. 1 produces, for the worst code lengths (every codeword lmax
+    bits) and for ordinary ones, at ragged stream lengths."""
+    rng = np.random.default_rng(lmax)
+    cl = np.zeros(256, np.uint8)
+    if lengths == "max":
+        cl[:128], cl[128:] = 8, lmax
+        pool = np.arange(128, 256)
+    elif lengths == "uniform":
+        cl[:] = 8
+        pool = np.arange(256)
+    elif lengths == "trained":
+        cl = od(1)[0].code_len.copy()
+        pool = np.flatnonzero(cl)
+    else:
+        cl[128], cl[0] = 1, 1
+        pool = np.array([0, 128])
+    o = oracle.Domain(32, 16, 2, 16, 50.0, 0.004, (1.0, 1.0, 0.0), lmax, cl)
+    d = codec.Domain(o.N, o.E, o.B1, o.B2, o.mu, o.alpha1, o.A, o.lmax, o.code_len)
+    codes = oracle.canonical_codes(cl, lmax)
+    for S in (1, 31, 32, 33, 1000, 4097, 65536):
+        X = rng.choice(pool, size=o.windows(S) * o.E).astype(np.uint8)
+        words, _ = oracle.pack_symlen(X, codes, cl)
+        assert words.size <= codec.word_capacity(d, S), (S, words.size)
