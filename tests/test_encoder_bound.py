@@ -1,0 +1,88 @@
+"""CPU check of the error bound the GPU encoder's level kernel relies on: the
+compensated FP32 bin of Eq. 1 (exact products by FMA, exact two-sums, hi/lo
+cosines, in the kernel's order of operations, emulated here with numpy float32
+arithmetic, which rounds each operation as the GPU does, and the FMA's exact
+product error formed in float64) lies within the kernel's bound of the FP64 bin
+the host encoder computes (products and sums rounded separately, in sample
+order).  Adversarial windows: large offsets with small variations, mixed signs,
+magnitudes from 1e-20 to 1e6, N from 4 to 128."""
+import numpy as np
+import pytest
+
+f32 = np.float32
+
+
+def _emulate(x, ch, cl):
+    """hi, lo, s1 of the kernel's loop for one bin (x, ch, cl float32 arrays)."""
+    hi = lo = s1 = f32(0.0)
+    for xv, c_h, c_l in zip(x, ch, cl):
+        pr = f32(xv * c_h)
+        fma = f32(np.float64(xv) * np.float64(c_h) - np.float64(pr))  # exact product error, rounded once
+        pe = f32(fma + f32(xv * c_l))
+        t = f32(hi + pr)
+        bp = f32(t - hi)
+        lo = f32(lo + f32(f32(f32(hi - f32(t - bp)) + f32(pr - bp)) + pe))
+        hi = t
+        s1 = f32(s1 + abs(xv))
+    return hi, lo, s1
+
+
+def _fp64_bin(x, cos64, N):
+    acc = 0.0
+    for xv, c in zip(x, cos64):
+        acc = acc + float(xv) * float(c)   # Python floats: each operation rounded separately
+    return acc * (2.0 / N)
+
+
+@pytest.mark.parametrize("N", [4, 16, 32, 128])
+def test_compensated_bin_within_bound(N):
+    rng = np.random.default_rng(N)
+    E = min(N, 16)
+    cos64 = np.array([[np.cos(np.pi * (2 * n + 1) * k / (2 * N)) for n in range(N)] for k in range(E)])
+    ch = cos64.astype(f32)
+    cl = (cos64 - ch.astype(np.float64)).astype(f32)
+    worst = 0.0
+    for trial in range(300):
+        kind = trial % 5
+        if kind == 0:
+            x = rng.normal(0, 1, N)
+        elif kind == 1:
+            x = 1e4 + rng.normal(0, 1e-2, N)              # large offset, small variation
+        elif kind == 2:
+            x = rng.choice([-1, 1], N) * 10.0 ** rng.uniform(-20, 6, N)
+        elif kind == 3:
+            x = np.full(N, 3.0) + rng.integers(-1, 2, N) * 2.0 ** -20
+        else:
+            x = rng.normal(100, 5, N) * rng.choice([1, -1], N)
+        x = x.astype(f32)
+        for k in range(E):
+            hi, lo, s1 = _emulate(x, ch[k], cl[k])
+            c64 = _fp64_bin(x, cos64[k], N)
+            cd = (float(hi) + float(lo)) * (2.0 / N)
+            err = float(s1) * (2.0 / N) * 2.0 ** -34 + 1e-30
+            gap = abs(cd - c64)
+            assert gap <= 2.0 * err, (N, trial, k, gap, err)   # the zone-1 deadzone test's margin
+            c = float(f32(f32(hi + lo) * f32(2.0 / N)))
+            assert abs(c - c64) <= err + abs(c) * 2.0 ** -21, (N, trial, k)   # the bracket's margin
+            worst = max(worst, gap / err if err > 1e-29 else 0.0)
+    assert worst < 1.0
+
+
+def test_plain_fp32_sum_would_break_the_bound():
+    """The bound is tight enough to matter: an uncompensated FP32 dot product of
+    an offset window misses it by orders of magnitude."""
+    N = 32
+    rng = np.random.default_rng(1)
+    cos64 = np.array([[np.cos(np.pi * (2 * n + 1) * k / (2 * N)) for n in range(N)] for k in range(16)])
+    ch = cos64.astype(f32)
+    worst = 0.0
+    for _ in range(20):
+        x = (1e4 + rng.normal(0, 1e-2, N)).astype(f32)
+        s1 = float(np.abs(x.astype(np.float64)).sum())
+        for k in range(1, 16):
+            acc = f32(0.0)
+            for xv, c in zip(x, ch[k]):
+                acc = f32(acc + f32(xv * c))
+            err = s1 * (2.0 / N) * 2.0 ** -34
+            worst = max(worst, abs(float(acc) * (2.0 / N) - _fp64_bin(x, cos64[k], N)) / err)
+    assert worst > 100.0
