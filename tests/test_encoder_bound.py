@@ -86,3 +86,40 @@ def test_plain_fp32_sum_would_break_the_bound():
             err = s1 * (2.0 / N) * 2.0 ** -34
             worst = max(worst, abs(float(acc) * (2.0 / N) - _fp64_bin(x, cos64[k], N)) / err)
     assert worst > 100.0
+
+
+def _zone0_64(c, A0, mu):
+    a = min(abs(c), A0)
+    q = np.log1p(mu * (a / A0)) / np.log1p(mu)
+    v = 128 + int(np.floor(127.0 * q + 0.5)) if c >= 0 else 128 - int(np.floor(128.0 * q + 0.5))
+    return min(max(v, 0), 255)
+
+
+def _zone0_32(c, A0, mu):
+    c = f32(c)
+    a = min(f32(abs(c)), f32(A0))
+    q = f32(np.log1p(f32(f32(mu) * f32(a * f32(1.0 / A0))))) * f32(1.0 / np.log1p(mu))
+    q = f32(q)
+    v = 128 + int(np.floor(f32(f32(127.0) * q + f32(0.5)))) if c >= 0 else 128 - int(np.floor(f32(f32(128.0) * q + f32(0.5))))
+    return min(max(v, 0), 255)
+
+
+@pytest.mark.parametrize("A0", [2.2589, 65.02, 305.3, 1e-3])
+def test_zone0_slack_brackets_the_fp64_map(A0):
+    """Levels of the FP32 evaluation at c - slack and c + slack bracket the FP64
+    level at c (slack = 2^-18 A0), densely around every level boundary."""
+    mu = 50.0
+    slack = A0 * 2.0 ** -18
+    # coefficients at every level boundary of the FP64 map, and just around them
+    cs = []
+    for L in range(1, 128):
+        q = (L - 0.5) / 127.0
+        b = A0 / mu * ((1.0 + mu) ** q - 1.0)
+        cs += [b * (1 + e) for e in (-1e-6, -1e-9, 0.0, 1e-9, 1e-6)]
+        q = (L - 0.5) / 128.0
+        b = A0 / mu * ((1.0 + mu) ** q - 1.0)
+        cs += [-b * (1 + e) for e in (-1e-6, 0.0, 1e-6)]
+    cs += list(np.random.default_rng(0).uniform(-1.2 * A0, 1.2 * A0, 2000))
+    for c in cs:
+        lo, hi = _zone0_32(c - slack, A0, mu), _zone0_32(c + slack, A0, mu)
+        assert lo <= _zone0_64(c, A0, mu) <= hi, (c, lo, hi)
