@@ -22,16 +22,20 @@ namespace {
 thread_local std::string g_error;
 }
 
-void set_error(const char *fmt, ...) {
+void set_error(const char *fmt, ...) noexcept {
   char buf[512];
   va_list ap;
   va_start(ap, fmt);
   std::vsnprintf(buf, sizeof(buf), fmt, ap);
   va_end(ap);
-  g_error = buf;
+  try {
+    g_error = buf;
+  } catch (...) {  // no memory for the text: keep the status, drop the message
+    g_error.clear();
+  }
 }
 
-void clear_error() { g_error.clear(); }
+void clear_error() noexcept { g_error.clear(); }
 
 namespace {
 
@@ -150,92 +154,98 @@ extern "C" {
 const char *fptc_last_error_message(void) { return g_error.c_str(); }
 
 fptc_status fptc_validate_domain(const fptc_domain *d) {
-  if (!d) {
-    set_error("domain is NULL");
-    return FPTC_ERR_INVALID_ARGUMENT;
-  }
-  if (d->N < 4 || d->N > 128) {
-    set_error("N = %u outside [4, 128]", d->N);
-    return FPTC_ERR_INVALID_ARGUMENT;
-  }
-  if (d->E < 1 || d->E > d->N) {
-    set_error("E = %u outside [1, N]", d->E);
-    return FPTC_ERR_INVALID_ARGUMENT;
-  }
-  if (d->B1 > d->B2 || d->B2 > d->E) {
-    set_error("zone boundaries need 0 <= B1 <= B2 <= E (B1 = %u, B2 = %u)", d->B1, d->B2);
-    return FPTC_ERR_INVALID_ARGUMENT;
-  }
-  if (!(d->mu > 0.0) || !std::isfinite(d->mu)) {
-    set_error("mu must be positive");
-    return FPTC_ERR_INVALID_ARGUMENT;
-  }
-  if (!(d->alpha1 >= 0.0 && d->alpha1 <= 1.0)) {
-    set_error("alpha1 must lie in [0, 1]");
-    return FPTC_ERR_INVALID_ARGUMENT;
-  }
-  for (int z = 0; z < 3; ++z) {
-    if (!std::isfinite(d->scale[z]) || d->scale[z] < 0.0) {
-      set_error("scale[%d] must be finite and >= 0", z);
+  return guarded([&]() -> fptc_status {
+    if (!d) {
+      set_error("domain is NULL");
       return FPTC_ERR_INVALID_ARGUMENT;
     }
-  }
-  if (d->lmax < 1 || d->lmax > 16) {
-    set_error("lmax = %u outside [1, 16]", d->lmax);
-    return FPTC_ERR_INVALID_ARGUMENT;
-  }
-  uint64_t kraft = 0;
-  int coded = 0;
-  for (int s = 0; s < 256; ++s) {
-    if (d->code_len[s] > d->lmax) {
-      set_error("code length %u of level %d exceeds lmax %u", d->code_len[s], s, d->lmax);
+    if (d->N < 4 || d->N > 128) {
+      set_error("N = %u outside [4, 128]", d->N);
       return FPTC_ERR_INVALID_ARGUMENT;
     }
-    if (d->code_len[s]) {
-      kraft += uint64_t(1) << (d->lmax - d->code_len[s]);
-      ++coded;
+    if (d->E < 1 || d->E > d->N) {
+      set_error("E = %u outside [1, N]", d->E);
+      return FPTC_ERR_INVALID_ARGUMENT;
     }
-  }
-  if (coded == 0) {
-    set_error("no level has a code");
-    return FPTC_ERR_INVALID_ARGUMENT;
-  }
-  if (kraft > (uint64_t(1) << d->lmax)) {
-    set_error("code lengths break the Kraft inequality");
-    return FPTC_ERR_INVALID_ARGUMENT;
-  }
-  return FPTC_OK;
+    if (d->B1 > d->B2 || d->B2 > d->E) {
+      set_error("zone boundaries need 0 <= B1 <= B2 <= E (B1 = %u, B2 = %u)", d->B1, d->B2);
+      return FPTC_ERR_INVALID_ARGUMENT;
+    }
+    if (!(d->mu > 0.0) || !std::isfinite(d->mu)) {
+      set_error("mu must be positive");
+      return FPTC_ERR_INVALID_ARGUMENT;
+    }
+    if (!(d->alpha1 >= 0.0 && d->alpha1 <= 1.0)) {
+      set_error("alpha1 must lie in [0, 1]");
+      return FPTC_ERR_INVALID_ARGUMENT;
+    }
+    for (int z = 0; z < 3; ++z) {
+      if (!std::isfinite(d->scale[z]) || d->scale[z] < 0.0) {
+        set_error("scale[%d] must be finite and >= 0", z);
+        return FPTC_ERR_INVALID_ARGUMENT;
+      }
+    }
+    if (d->lmax < 1 || d->lmax > 16) {
+      set_error("lmax = %u outside [1, 16]", d->lmax);
+      return FPTC_ERR_INVALID_ARGUMENT;
+    }
+    uint64_t kraft = 0;
+    int coded = 0;
+    for (int s = 0; s < 256; ++s) {
+      if (d->code_len[s] > d->lmax) {
+        set_error("code length %u of level %d exceeds lmax %u", d->code_len[s], s, d->lmax);
+        return FPTC_ERR_INVALID_ARGUMENT;
+      }
+      if (d->code_len[s]) {
+        kraft += uint64_t(1) << (d->lmax - d->code_len[s]);
+        ++coded;
+      }
+    }
+    if (coded == 0) {
+      set_error("no level has a code");
+      return FPTC_ERR_INVALID_ARGUMENT;
+    }
+    if (kraft > (uint64_t(1) << d->lmax)) {
+      set_error("code lengths break the Kraft inequality");
+      return FPTC_ERR_INVALID_ARGUMENT;
+    }
+    return FPTC_OK;
+  });
 }
 
 fptc_status fptc_canonical_codes(const fptc_domain *d, uint32_t *codes) {
-  fptc_status st = fptc_validate_domain(d);
-  if (st != FPTC_OK) return st;
-  uint32_t count[17] = {0};
-  for (int s = 0; s < 256; ++s) count[d->code_len[s]]++;
-  count[0] = 0;
-  uint32_t first[17] = {0};
-  uint32_t c = 0;
-  for (uint32_t l = 1; l <= 16; ++l) {
-    c = (c + count[l - 1]) << 1;
-    first[l] = c;
-  }
-  for (int s = 0; s < 256; ++s) codes[s] = d->code_len[s] ? first[d->code_len[s]]++ : 0u;
-  return FPTC_OK;
+  return guarded([&]() -> fptc_status {
+    fptc_status st = fptc_validate_domain(d);
+    if (st != FPTC_OK) return st;
+    uint32_t count[17] = {0};
+    for (int s = 0; s < 256; ++s) count[d->code_len[s]]++;
+    count[0] = 0;
+    uint32_t first[17] = {0};
+    uint32_t c = 0;
+    for (uint32_t l = 1; l <= 16; ++l) {
+      c = (c + count[l - 1]) << 1;
+      first[l] = c;
+    }
+    for (int s = 0; s < 256; ++s) codes[s] = d->code_len[s] ? first[d->code_len[s]]++ : 0u;
+    return FPTC_OK;
+  });
 }
 
 fptc_status fptc_build_decode_table(const fptc_domain *d, uint16_t *table) {
-  uint32_t codes[256];
-  fptc_status st = fptc_canonical_codes(d, codes);
-  if (st != FPTC_OK) return st;
-  const uint32_t L = d->lmax;
-  std::memset(table, 0, sizeof(uint16_t) << L);
-  for (int s = 0; s < 256; ++s) {
-    const uint32_t l = d->code_len[s];
-    if (!l) continue;
-    const uint32_t lo = codes[s] << (L - l), hi = (codes[s] + 1) << (L - l);
-    for (uint32_t p = lo; p < hi; ++p) table[p] = (uint16_t)(s | (l << 8));
-  }
-  return FPTC_OK;
+  return guarded([&]() -> fptc_status {
+    uint32_t codes[256];
+    fptc_status st = fptc_canonical_codes(d, codes);
+    if (st != FPTC_OK) return st;
+    const uint32_t L = d->lmax;
+    std::memset(table, 0, sizeof(uint16_t) << L);
+    for (int s = 0; s < 256; ++s) {
+      const uint32_t l = d->code_len[s];
+      if (!l) continue;
+      const uint32_t lo = codes[s] << (L - l), hi = (codes[s] + 1) << (L - l);
+      for (uint32_t p = lo; p < hi; ++p) table[p] = (uint16_t)(s | (l << 8));
+    }
+    return FPTC_OK;
+  });
 }
 
 uint64_t fptc_word_capacity(const fptc_domain *d, uint64_t S) {
@@ -247,157 +257,163 @@ uint64_t fptc_word_capacity(const fptc_domain *d, uint64_t S) {
 
 fptc_status fptc_train_domain(const float *x, const uint64_t *offsets, const uint64_t *lengths, uint64_t n_signals,
                               double percentile, fptc_domain *d) {
-  clear_error();
-  if (!d || (n_signals && (!x || !offsets || !lengths))) {
-    set_error("NULL argument");
-    return FPTC_ERR_INVALID_ARGUMENT;
-  }
-  if (!(percentile > 0.0 && percentile <= 100.0)) {
-    set_error("percentile must lie in (0, 100]");
-    return FPTC_ERR_INVALID_ARGUMENT;
-  }
-  // validate the shape parameters with a placeholder complete code
-  fptc_domain probe = *d;
-  for (int s = 0; s < 256; ++s) probe.code_len[s] = 8;
-  probe.scale[0] = probe.scale[1] = probe.scale[2] = 0.0;
-  if (d->lmax < 8) probe.lmax = 8;
-  fptc_status st = fptc_validate_domain(&probe);
-  if (st != FPTC_OK) return st;
-  if (d->lmax < 8) {
-    set_error("lmax must be >= 8 to code 256 levels");
-    return FPTC_ERR_INVALID_ARGUMENT;
-  }
-  const uint32_t N = d->N, E = d->E;
-  const auto cosv = cos_table(N, E);
-  std::vector<double> coef;
-  for (uint64_t i = 0; i < n_signals; ++i) {
-    const uint64_t S = lengths[i];
-    const uint64_t W = (S + N - 1) / N;
-    const size_t base = coef.size();
-    coef.resize(base + W * E);
-    for (uint64_t w = 0; w < W; ++w)
-      forward_window(x + offsets[i] + w * N, S - w * N, N, E, cosv, coef.data() + base + w * E);
-  }
-  const uint64_t rows = coef.size() / E;
-  for (int z = 0; z < 2; ++z) {
-    const uint32_t k0 = z == 0 ? 0 : d->B1, k1 = z == 0 ? d->B1 : d->B2;
-    std::vector<double> v;
-    v.reserve(rows * (k1 - k0));
-    for (uint64_t r = 0; r < rows; ++r)
-      for (uint32_t k = k0; k < k1; ++k) v.push_back(std::fabs(coef[r * E + k]));
-    double A = 0.0;
-    if (!v.empty()) {
-      long rank = (long)std::ceil(percentile / 100.0 * (double)v.size() - 1e-9);
-      size_t idx = (size_t)std::clamp(rank - 1, 0L, (long)v.size() - 1);
-      std::nth_element(v.begin(), v.begin() + idx, v.end());
-      A = v[idx];
+  return guarded([&]() -> fptc_status {
+    clear_error();
+    if (!d || (n_signals && (!x || !offsets || !lengths))) {
+      set_error("NULL argument");
+      return FPTC_ERR_INVALID_ARGUMENT;
     }
-    d->scale[z] = A;
-  }
-  d->scale[2] = 0.0;
-  const Quantizer qz(*d);
-  uint64_t hist[256];
-  for (int s = 0; s < 256; ++s) hist[s] = 1;
-  for (uint64_t r = 0; r < rows; ++r)
-    for (uint32_t k = 0; k < E; ++k) hist[qz.level(k, coef[r * E + k])]++;
-  if (!package_merge(hist, d->lmax, d->code_len)) {
-    set_error("package-merge failed");
-    return FPTC_ERR_INVALID_ARGUMENT;
-  }
-  return FPTC_OK;
+    if (!(percentile > 0.0 && percentile <= 100.0)) {
+      set_error("percentile must lie in (0, 100]");
+      return FPTC_ERR_INVALID_ARGUMENT;
+    }
+    // validate the shape parameters with a placeholder complete code
+    fptc_domain probe = *d;
+    for (int s = 0; s < 256; ++s) probe.code_len[s] = 8;
+    probe.scale[0] = probe.scale[1] = probe.scale[2] = 0.0;
+    if (d->lmax < 8) probe.lmax = 8;
+    fptc_status st = fptc_validate_domain(&probe);
+    if (st != FPTC_OK) return st;
+    if (d->lmax < 8) {
+      set_error("lmax must be >= 8 to code 256 levels");
+      return FPTC_ERR_INVALID_ARGUMENT;
+    }
+    const uint32_t N = d->N, E = d->E;
+    const auto cosv = cos_table(N, E);
+    std::vector<double> coef;
+    for (uint64_t i = 0; i < n_signals; ++i) {
+      const uint64_t S = lengths[i];
+      const uint64_t W = (S + N - 1) / N;
+      const size_t base = coef.size();
+      coef.resize(base + W * E);
+      for (uint64_t w = 0; w < W; ++w)
+        forward_window(x + offsets[i] + w * N, S - w * N, N, E, cosv, coef.data() + base + w * E);
+    }
+    const uint64_t rows = coef.size() / E;
+    for (int z = 0; z < 2; ++z) {
+      const uint32_t k0 = z == 0 ? 0 : d->B1, k1 = z == 0 ? d->B1 : d->B2;
+      std::vector<double> v;
+      v.reserve(rows * (k1 - k0));
+      for (uint64_t r = 0; r < rows; ++r)
+        for (uint32_t k = k0; k < k1; ++k) v.push_back(std::fabs(coef[r * E + k]));
+      double A = 0.0;
+      if (!v.empty()) {
+        long rank = (long)std::ceil(percentile / 100.0 * (double)v.size() - 1e-9);
+        size_t idx = (size_t)std::clamp(rank - 1, 0L, (long)v.size() - 1);
+        std::nth_element(v.begin(), v.begin() + idx, v.end());
+        A = v[idx];
+      }
+      d->scale[z] = A;
+    }
+    d->scale[2] = 0.0;
+    const Quantizer qz(*d);
+    uint64_t hist[256];
+    for (int s = 0; s < 256; ++s) hist[s] = 1;
+    for (uint64_t r = 0; r < rows; ++r)
+      for (uint32_t k = 0; k < E; ++k) hist[qz.level(k, coef[r * E + k])]++;
+    if (!package_merge(hist, d->lmax, d->code_len)) {
+      set_error("package-merge failed");
+      return FPTC_ERR_INVALID_ARGUMENT;
+    }
+    return FPTC_OK;
+  });
 }
 
 fptc_status fptc_encode_stream(const fptc_domain *d, const float *x, uint64_t S, uint64_t *words, uint8_t *symlen,
                                uint64_t capacity, uint64_t *n_words, uint8_t *levels) {
-  uint32_t codes[256];
-  fptc_status st = fptc_canonical_codes(d, codes);
-  if (st != FPTC_OK) return st;
-  if ((S && !x) || !n_words || (capacity && (!words || !symlen))) {
-    set_error("NULL argument");
-    return FPTC_ERR_INVALID_ARGUMENT;
-  }
-  const uint32_t N = d->N, E = d->E;
-  const auto cosv = cos_table(N, E);
-  const Quantizer qz(*d);
-  const uint64_t W = (S + N - 1) / N;
-  double C[128];
-  uint64_t w_out = 0, buf = 0;
-  uint32_t bits = 0, count = 0;
-  for (uint64_t w = 0; w < W; ++w) {
-    forward_window(x + w * N, S - w * N, N, E, cosv, C);
-    for (uint32_t k = 0; k < E; ++k) {
-      const uint8_t lv = qz.level(k, C[k]);
-      if (levels) levels[w * E + k] = lv;
-      const uint32_t cl = d->code_len[lv];
-      if (!cl) {
-        set_error("level %u has no code", lv);
-        return FPTC_ERR_INVALID_ARGUMENT;
-      }
-      if (bits + cl > 64) {  // close the word; the codeword goes to the next one
-        if (w_out >= capacity) {
-          set_error("word capacity exceeded");
-          return FPTC_ERR_INVALID_ARGUMENT;
-        }
-        words[w_out] = buf;
-        symlen[w_out] = (uint8_t)count;
-        ++w_out;
-        buf = 0;
-        bits = 0;
-        count = 0;
-      }
-      buf |= (uint64_t)codes[lv] << (64 - bits - cl);
-      bits += cl;
-      ++count;
-    }
-  }
-  if (count) {
-    if (w_out >= capacity) {
-      set_error("word capacity exceeded");
+  return guarded([&]() -> fptc_status {
+    uint32_t codes[256];
+    fptc_status st = fptc_canonical_codes(d, codes);
+    if (st != FPTC_OK) return st;
+    if ((S && !x) || !n_words || (capacity && (!words || !symlen))) {
+      set_error("NULL argument");
       return FPTC_ERR_INVALID_ARGUMENT;
     }
-    words[w_out] = buf;
-    symlen[w_out] = (uint8_t)count;
-    ++w_out;
-  }
-  *n_words = w_out;
-  return FPTC_OK;
+    const uint32_t N = d->N, E = d->E;
+    const auto cosv = cos_table(N, E);
+    const Quantizer qz(*d);
+    const uint64_t W = (S + N - 1) / N;
+    double C[128];
+    uint64_t w_out = 0, buf = 0;
+    uint32_t bits = 0, count = 0;
+    for (uint64_t w = 0; w < W; ++w) {
+      forward_window(x + w * N, S - w * N, N, E, cosv, C);
+      for (uint32_t k = 0; k < E; ++k) {
+        const uint8_t lv = qz.level(k, C[k]);
+        if (levels) levels[w * E + k] = lv;
+        const uint32_t cl = d->code_len[lv];
+        if (!cl) {
+          set_error("level %u has no code", lv);
+          return FPTC_ERR_INVALID_ARGUMENT;
+        }
+        if (bits + cl > 64) {  // close the word; the codeword goes to the next one
+          if (w_out >= capacity) {
+            set_error("word capacity exceeded");
+            return FPTC_ERR_INVALID_ARGUMENT;
+          }
+          words[w_out] = buf;
+          symlen[w_out] = (uint8_t)count;
+          ++w_out;
+          buf = 0;
+          bits = 0;
+          count = 0;
+        }
+        buf |= (uint64_t)codes[lv] << (64 - bits - cl);
+        bits += cl;
+        ++count;
+      }
+    }
+    if (count) {
+      if (w_out >= capacity) {
+        set_error("word capacity exceeded");
+        return FPTC_ERR_INVALID_ARGUMENT;
+      }
+      words[w_out] = buf;
+      symlen[w_out] = (uint8_t)count;
+      ++w_out;
+    }
+    *n_words = w_out;
+    return FPTC_OK;
+  });
 }
 
 fptc_status fptc_encode_batch(const fptc_domain *domains, uint32_t n_domains, const float *x,
                               const uint64_t *x_offsets, const uint64_t *lengths, const uint32_t *domain_idx,
                               uint64_t n, uint64_t *words, uint8_t *symlen, const uint64_t *capacity_offsets,
                               uint64_t *n_words, int n_threads) {
-  clear_error();
-  for (uint64_t i = 0; i < n; ++i) {
-    if (domain_idx[i] >= n_domains) {
-      set_error("signal %llu: domain out of range", (unsigned long long)i);
+  return guarded([&]() -> fptc_status {
+    clear_error();
+    for (uint64_t i = 0; i < n; ++i) {
+      if (domain_idx[i] >= n_domains) {
+        set_error("signal %llu: domain out of range", (unsigned long long)i);
+        return FPTC_ERR_INVALID_ARGUMENT;
+      }
+    }
+    unsigned hw = std::thread::hardware_concurrency();
+    const unsigned nt = n_threads > 0 ? (unsigned)n_threads : (hw ? hw : 1u);
+    std::atomic<uint64_t> next{0};
+    std::atomic<int> failed{0};
+    auto work = [&]() {
+      for (;;) {
+        const uint64_t i = next.fetch_add(1);
+        if (i >= n || failed.load()) return;
+        const fptc_domain &d = domains[domain_idx[i]];
+        const uint64_t cap = fptc_word_capacity(&d, lengths[i]);
+        if (fptc_encode_stream(&d, x + x_offsets[i], lengths[i], words + capacity_offsets[i],
+                               symlen + capacity_offsets[i], cap, &n_words[i], nullptr) != FPTC_OK)
+          failed.store(1);
+      }
+    };
+    std::vector<std::thread> pool;
+    for (unsigned t = 1; t < nt; ++t) pool.emplace_back(work);
+    work();
+    for (auto &t : pool) t.join();
+    if (failed.load()) {
+      set_error("encoding failed");
       return FPTC_ERR_INVALID_ARGUMENT;
     }
-  }
-  unsigned hw = std::thread::hardware_concurrency();
-  const unsigned nt = n_threads > 0 ? (unsigned)n_threads : (hw ? hw : 1u);
-  std::atomic<uint64_t> next{0};
-  std::atomic<int> failed{0};
-  auto work = [&]() {
-    for (;;) {
-      const uint64_t i = next.fetch_add(1);
-      if (i >= n || failed.load()) return;
-      const fptc_domain &d = domains[domain_idx[i]];
-      const uint64_t cap = fptc_word_capacity(&d, lengths[i]);
-      if (fptc_encode_stream(&d, x + x_offsets[i], lengths[i], words + capacity_offsets[i],
-                             symlen + capacity_offsets[i], cap, &n_words[i], nullptr) != FPTC_OK)
-        failed.store(1);
-    }
-  };
-  std::vector<std::thread> pool;
-  for (unsigned t = 1; t < nt; ++t) pool.emplace_back(work);
-  work();
-  for (auto &t : pool) t.join();
-  if (failed.load()) {
-    set_error("encoding failed");
-    return FPTC_ERR_INVALID_ARGUMENT;
-  }
-  return FPTC_OK;
+    return FPTC_OK;
+  });
 }
 
 }  // extern "C"

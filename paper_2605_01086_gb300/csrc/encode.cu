@@ -513,142 +513,144 @@ extern "C" {
 
 fptc_status fptc_encoder_create(fptc_encoder **enc, int device, const fptc_domain *domains, uint32_t n_domains,
                                 const fptc_segment *segments, uint64_t n_segments) {
-  clear_error();
-  if (!enc) {
-    set_error("NULL encoder pointer");
-    return FPTC_ERR_INVALID_ARGUMENT;
-  }
-  *enc = nullptr;
-  if (!domains || n_domains == 0 || (n_segments && !segments)) {
-    set_error("need at least one domain and a segment array");
-    return FPTC_ERR_INVALID_ARGUMENT;
-  }
-  std::vector<EncDomain> doms(n_domains);
-  std::vector<double> cosv;
-  std::vector<uint32_t> codes;
-  std::vector<uint8_t> lens;
-  for (uint32_t d = 0; d < n_domains; ++d) {
-    const fptc_domain &dm = domains[d];
-    fptc_status st = fptc_validate_domain(&dm);
-    if (st != FPTC_OK) return st;
-    EncDomain &x = doms[d];
-    x.N = dm.N;
-    x.E = dm.E;
-    x.B1 = dm.B1;
-    x.B2 = dm.B2;
-    x.A0 = dm.scale[0];
-    x.A1 = dm.scale[1];
-    x.mu = dm.mu;
-    x.alpha1 = dm.alpha1;
-    x.log1pmu = std::log1p(dm.mu);
-    x.A0f = (float)dm.scale[0];
-    x.A1f = (float)dm.scale[1];
-    x.muf = (float)dm.mu;
-    x.d1f = (float)(dm.alpha1 * dm.scale[1]);
-    x.d1 = dm.alpha1 * dm.scale[1];
-    x.inv_A0f = dm.scale[0] > 1e-30 ? (float)(1.0 / dm.scale[0]) : 0.0f;
-    x.inv_span1f = dm.scale[1] > 1e-30 && dm.scale[1] * (1.0 - dm.alpha1) > 0.0
-                       ? (float)(1.0 / (dm.scale[1] - dm.alpha1 * dm.scale[1])) : 0.0f;
-    x.inv_log1pmuf = (float)(1.0 / std::log1p(dm.mu));
-    // 2^-18 of the zone scale: well above the FP32 evaluation error of either
-    // map expressed in the coefficient (a few ulp of the scale: the maps'
-    // arguments carry relative errors of a few 2^-24, over slopes of at most
-    // mu / log1p(mu) and 1 / (1 - alpha1) per scale)
-    x.slack0 = (float)(std::fabs(dm.scale[0]) * 0x1p-18);
-    x.slack1 = (float)(std::fabs(dm.scale[1]) * 0x1p-18);
-    x.cos_off = (uint32_t)cosv.size();
-    for (uint32_t k = 0; k < dm.E; ++k)
-      for (uint32_t n = 0; n < dm.N; ++n) cosv.push_back(std::cos(M_PI * (2.0 * n + 1.0) * k / (2.0 * dm.N)));
-    x.code_off = (uint32_t)codes.size();
-    uint32_t c[256];
-    st = fptc_canonical_codes(&dm, c);
-    if (st != FPTC_OK) return st;
-    for (int s = 0; s < 256; ++s) {
-      codes.push_back(c[s]);
-      lens.push_back(dm.code_len[s]);
+  return guarded([&]() -> fptc_status {
+    clear_error();
+    if (!enc) {
+      set_error("NULL encoder pointer");
+      return FPTC_ERR_INVALID_ARGUMENT;
     }
-  }
-  // the same cosines as FP32 high and low parts, transposed per domain:
-  // cosf[2 (cos_off + n E + k)] = hi, [+1] = lo, hi + lo = the FP64 cosine to 2^-48
-  std::vector<float> cosf(2 * cosv.size());
-  for (uint32_t d = 0; d < n_domains; ++d) {
-    const EncDomain &x = doms[d];
-    for (uint32_t k = 0; k < x.E; ++k)
-      for (uint32_t n = 0; n < x.N; ++n) {
-        const double c = cosv[x.cos_off + (size_t)k * x.N + n];
-        const float h = (float)c;
-        const size_t j = 2 * (x.cos_off + (size_t)n * x.E + k);
-        cosf[j] = h;
-        cosf[j + 1] = (float)(c - (double)h);
+    *enc = nullptr;
+    if (!domains || n_domains == 0 || (n_segments && !segments)) {
+      set_error("need at least one domain and a segment array");
+      return FPTC_ERR_INVALID_ARGUMENT;
+    }
+    std::vector<EncDomain> doms(n_domains);
+    std::vector<double> cosv;
+    std::vector<uint32_t> codes;
+    std::vector<uint8_t> lens;
+    for (uint32_t d = 0; d < n_domains; ++d) {
+      const fptc_domain &dm = domains[d];
+      fptc_status st = fptc_validate_domain(&dm);
+      if (st != FPTC_OK) return st;
+      EncDomain &x = doms[d];
+      x.N = dm.N;
+      x.E = dm.E;
+      x.B1 = dm.B1;
+      x.B2 = dm.B2;
+      x.A0 = dm.scale[0];
+      x.A1 = dm.scale[1];
+      x.mu = dm.mu;
+      x.alpha1 = dm.alpha1;
+      x.log1pmu = std::log1p(dm.mu);
+      x.A0f = (float)dm.scale[0];
+      x.A1f = (float)dm.scale[1];
+      x.muf = (float)dm.mu;
+      x.d1f = (float)(dm.alpha1 * dm.scale[1]);
+      x.d1 = dm.alpha1 * dm.scale[1];
+      x.inv_A0f = dm.scale[0] > 1e-30 ? (float)(1.0 / dm.scale[0]) : 0.0f;
+      x.inv_span1f = dm.scale[1] > 1e-30 && dm.scale[1] * (1.0 - dm.alpha1) > 0.0
+                         ? (float)(1.0 / (dm.scale[1] - dm.alpha1 * dm.scale[1])) : 0.0f;
+      x.inv_log1pmuf = (float)(1.0 / std::log1p(dm.mu));
+      // 2^-18 of the zone scale: well above the FP32 evaluation error of either
+      // map expressed in the coefficient (a few ulp of the scale: the maps'
+      // arguments carry relative errors of a few 2^-24, over slopes of at most
+      // mu / log1p(mu) and 1 / (1 - alpha1) per scale)
+      x.slack0 = (float)(std::fabs(dm.scale[0]) * 0x1p-18);
+      x.slack1 = (float)(std::fabs(dm.scale[1]) * 0x1p-18);
+      x.cos_off = (uint32_t)cosv.size();
+      for (uint32_t k = 0; k < dm.E; ++k)
+        for (uint32_t n = 0; n < dm.N; ++n) cosv.push_back(std::cos(M_PI * (2.0 * n + 1.0) * k / (2.0 * dm.N)));
+      x.code_off = (uint32_t)codes.size();
+      uint32_t c[256];
+      st = fptc_canonical_codes(&dm, c);
+      if (st != FPTC_OK) return st;
+      for (int s = 0; s < 256; ++s) {
+        codes.push_back(c[s]);
+        lens.push_back(dm.code_len[s]);
       }
-  }
-  std::vector<EncSeg> segs(n_segments);
-  std::vector<uint64_t> level_off(n_segments);
-  std::vector<std::pair<uint64_t, uint64_t>> rooms;
-  uint64_t win = 0, lv = 0, blocks = 0;
-  for (uint64_t i = 0; i < n_segments; ++i) {
-    const fptc_segment &s = segments[i];
-    if (s.domain >= n_domains) {
-      set_error("segment %llu: domain %u out of range", (unsigned long long)i, s.domain);
-      return FPTC_ERR_INVALID_ARGUMENT;
     }
-    const fptc_domain &dm = domains[s.domain];
-    EncSeg &e = segs[i];
-    e.in_offset = s.out_offset;
-    e.n_samples = s.n_samples;
-    e.word_offset = s.word_offset;
-    e.room = s.n_words;
-    e.level_offset = lv;
-    e.n_windows = (s.n_samples + dm.N - 1) / dm.N;
-    e.block_base = blocks;
-    e.domain = s.domain;
-    e.pad = 0;
-    level_off[i] = lv;
-    win += e.n_windows;
-    lv += e.n_windows * dm.E;
-    blocks += (e.n_windows * dm.E + kPackBlock - 1) / kPackBlock;
-    if (s.n_words) rooms.push_back({s.word_offset, s.word_offset + s.n_words});
-  }
-  std::sort(rooms.begin(), rooms.end());
-  for (size_t i = 1; i < rooms.size(); ++i)
-    if (rooms[i].first < rooms[i - 1].second) {
-      set_error("segment rooms overlap at word %llu", (unsigned long long)rooms[i].first);
-      return FPTC_ERR_INVALID_ARGUMENT;
+    // the same cosines as FP32 high and low parts, transposed per domain:
+    // cosf[2 (cos_off + n E + k)] = hi, [+1] = lo, hi + lo = the FP64 cosine to 2^-48
+    std::vector<float> cosf(2 * cosv.size());
+    for (uint32_t d = 0; d < n_domains; ++d) {
+      const EncDomain &x = doms[d];
+      for (uint32_t k = 0; k < x.E; ++k)
+        for (uint32_t n = 0; n < x.N; ++n) {
+          const double c = cosv[x.cos_off + (size_t)k * x.N + n];
+          const float h = (float)c;
+          const size_t j = 2 * (x.cos_off + (size_t)n * x.E + k);
+          cosf[j] = h;
+          cosf[j + 1] = (float)(c - (double)h);
+        }
     }
-  DevGuard g(device);
-  if (!g.ok) return enc_cuda_fail(cudaGetLastError(), "set device");
-  fptc_encoder *e = new fptc_encoder;
-  e->device = device;
-  e->n_segs = n_segments;
-  e->n_windows = win;
-  e->n_levels = lv;
-  e->n_blocks = blocks;
-  e->level_off = level_off;
-  cudaError_t err = enc_upload(&e->d_segs, segs.data(), segs.size());
-  if (err == cudaSuccess) err = enc_upload(&e->d_doms, doms.data(), doms.size());
-  if (err == cudaSuccess) err = enc_upload(&e->d_cos, cosv.data(), cosv.size());
-  if (err == cudaSuccess) err = enc_upload(&e->d_cosf, cosf.data(), cosf.size());
-  if (err == cudaSuccess) err = cudaMalloc(&e->d_blocks, std::max<uint64_t>(blocks, 1) * sizeof(PackState));
-  if (err == cudaSuccess) err = cudaMalloc(&e->d_seg_bad, std::max<uint64_t>(n_segments, 1) * sizeof(uint32_t));
-  // room for the bins decided in FP64 (a few percent of them at most on signals; when it
-  // fills, the level kernel decides the rest itself)
-  e->fb_cap = (uint32_t)std::min<uint64_t>(std::max<uint64_t>(lv / 16, 4096), uint64_t(1) << 24);
-  if (err == cudaSuccess) err = cudaMalloc(&e->d_fb_list, (size_t)e->fb_cap * sizeof(unsigned long long));
-  if (err == cudaSuccess) err = cudaMalloc(&e->d_fb_count, sizeof(unsigned int));
-  if (err == cudaSuccess) err = cudaDeviceGetAttribute(&e->sm_count, cudaDevAttrMultiProcessorCount, device);
-  if (err == cudaSuccess) err = enc_upload(&e->d_codes, codes.data(), codes.size());
-  if (err == cudaSuccess) err = enc_upload(&e->d_lens, lens.data(), lens.size());
-  if (err == cudaSuccess) {
-    const EncStatus s0{0u, 0u, ~0ull};
-    err = enc_upload(&e->d_status, &s0, 1);
-  }
-  if (err != cudaSuccess) {
-    enc_free(e);
-    delete e;
-    return enc_cuda_fail(err, "encoder upload");
-  }
-  *enc = e;
-  return FPTC_OK;
+    std::vector<EncSeg> segs(n_segments);
+    std::vector<uint64_t> level_off(n_segments);
+    std::vector<std::pair<uint64_t, uint64_t>> rooms;
+    uint64_t win = 0, lv = 0, blocks = 0;
+    for (uint64_t i = 0; i < n_segments; ++i) {
+      const fptc_segment &s = segments[i];
+      if (s.domain >= n_domains) {
+        set_error("segment %llu: domain %u out of range", (unsigned long long)i, s.domain);
+        return FPTC_ERR_INVALID_ARGUMENT;
+      }
+      const fptc_domain &dm = domains[s.domain];
+      EncSeg &e = segs[i];
+      e.in_offset = s.out_offset;
+      e.n_samples = s.n_samples;
+      e.word_offset = s.word_offset;
+      e.room = s.n_words;
+      e.level_offset = lv;
+      e.n_windows = (s.n_samples + dm.N - 1) / dm.N;
+      e.block_base = blocks;
+      e.domain = s.domain;
+      e.pad = 0;
+      level_off[i] = lv;
+      win += e.n_windows;
+      lv += e.n_windows * dm.E;
+      blocks += (e.n_windows * dm.E + kPackBlock - 1) / kPackBlock;
+      if (s.n_words) rooms.push_back({s.word_offset, s.word_offset + s.n_words});
+    }
+    std::sort(rooms.begin(), rooms.end());
+    for (size_t i = 1; i < rooms.size(); ++i)
+      if (rooms[i].first < rooms[i - 1].second) {
+        set_error("segment rooms overlap at word %llu", (unsigned long long)rooms[i].first);
+        return FPTC_ERR_INVALID_ARGUMENT;
+      }
+    DevGuard g(device);
+    if (!g.ok) return enc_cuda_fail(cudaGetLastError(), "set device");
+    fptc_encoder *e = new fptc_encoder;
+    e->device = device;
+    e->n_segs = n_segments;
+    e->n_windows = win;
+    e->n_levels = lv;
+    e->n_blocks = blocks;
+    e->level_off = level_off;
+    cudaError_t err = enc_upload(&e->d_segs, segs.data(), segs.size());
+    if (err == cudaSuccess) err = enc_upload(&e->d_doms, doms.data(), doms.size());
+    if (err == cudaSuccess) err = enc_upload(&e->d_cos, cosv.data(), cosv.size());
+    if (err == cudaSuccess) err = enc_upload(&e->d_cosf, cosf.data(), cosf.size());
+    if (err == cudaSuccess) err = cudaMalloc(&e->d_blocks, std::max<uint64_t>(blocks, 1) * sizeof(PackState));
+    if (err == cudaSuccess) err = cudaMalloc(&e->d_seg_bad, std::max<uint64_t>(n_segments, 1) * sizeof(uint32_t));
+    // room for the bins decided in FP64 (a few percent of them at most on signals; when it
+    // fills, the level kernel decides the rest itself)
+    e->fb_cap = (uint32_t)std::min<uint64_t>(std::max<uint64_t>(lv / 16, 4096), uint64_t(1) << 24);
+    if (err == cudaSuccess) err = cudaMalloc(&e->d_fb_list, (size_t)e->fb_cap * sizeof(unsigned long long));
+    if (err == cudaSuccess) err = cudaMalloc(&e->d_fb_count, sizeof(unsigned int));
+    if (err == cudaSuccess) err = cudaDeviceGetAttribute(&e->sm_count, cudaDevAttrMultiProcessorCount, device);
+    if (err == cudaSuccess) err = enc_upload(&e->d_codes, codes.data(), codes.size());
+    if (err == cudaSuccess) err = enc_upload(&e->d_lens, lens.data(), lens.size());
+    if (err == cudaSuccess) {
+      const EncStatus s0{0u, 0u, ~0ull};
+      err = enc_upload(&e->d_status, &s0, 1);
+    }
+    if (err != cudaSuccess) {
+      enc_free(e);
+      delete e;
+      return enc_cuda_fail(err, "encoder upload");
+    }
+    *enc = e;
+    return FPTC_OK;
+  });
 }
 
 void fptc_encoder_destroy(fptc_encoder *enc) {
@@ -662,13 +664,15 @@ void fptc_encoder_destroy(fptc_encoder *enc) {
 uint64_t fptc_encoder_levels(const fptc_encoder *enc) { return enc ? enc->n_levels : 0; }
 
 fptc_status fptc_encoder_level_offsets(const fptc_encoder *enc, uint64_t *offsets) {
-  clear_error();
-  if (!enc || (!offsets && enc->n_segs)) {
-    set_error("NULL argument");
-    return FPTC_ERR_INVALID_ARGUMENT;
-  }
-  std::copy(enc->level_off.begin(), enc->level_off.end(), offsets);
-  return FPTC_OK;
+  return guarded([&]() -> fptc_status {
+    clear_error();
+    if (!enc || (!offsets && enc->n_segs)) {
+      set_error("NULL argument");
+      return FPTC_ERR_INVALID_ARGUMENT;
+    }
+    std::copy(enc->level_off.begin(), enc->level_off.end(), offsets);
+    return FPTC_OK;
+  });
 }
 
 // One encode: the level kernel (unless the levels are given) and the packing.

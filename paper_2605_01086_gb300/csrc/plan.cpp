@@ -462,288 +462,290 @@ const char *fptc_status_string(fptc_status s) {
 
 fptc_status fptc_plan_create(fptc_plan **out, int device, const fptc_domain *domains, uint32_t n_domains,
                              const fptc_segment *segments, uint64_t n_segments, const fptc_plan_options *opts) {
-  clear_error();
-  if (!out) {
-    set_error("plan output pointer is NULL");
-    return FPTC_ERR_INVALID_ARGUMENT;
-  }
-  *out = nullptr;
-  if (n_domains == 0 || !domains) {
-    set_error("at least one domain is required");
-    return FPTC_ERR_INVALID_ARGUMENT;
-  }
-  if (n_segments > 0 && !segments) {
-    set_error("segments is NULL");
-    return FPTC_ERR_INVALID_ARGUMENT;
-  }
-  if (n_segments > 0xFFFFFFF0ull) {
-    set_error("too many segments");
-    return FPTC_ERR_UNSUPPORTED;
-  }
-  fptc_plan_options o{};
-  o.idct = FPTC_IDCT_FP32;
-  o.schedule = FPTC_SCHEDULE_PERSISTENT;
-  if (opts) o = *opts;
-  if (o.idct > FPTC_IDCT_TF32X3 || o.schedule > FPTC_SCHEDULE_THREE_KERNEL || o.reserved[0] || o.reserved[1] ||
-      (o.schedule == FPTC_SCHEDULE_THREE_KERNEL && o.idct != FPTC_IDCT_FP32)) {
-    set_error("invalid plan options");
-    return FPTC_ERR_INVALID_ARGUMENT;
-  }
-  if (o.kernel > FPTC_KERNEL_TENSOR) {
-    set_error("unknown kernel %u", o.kernel);
-    return FPTC_ERR_INVALID_ARGUMENT;
-  }
-  bool all_fixed = true, all_pow2 = n_domains > 0;
-  for (uint32_t d = 0; d < n_domains; ++d) {
-    all_fixed = all_fixed && domains[d].N == 32 && domains[d].E == 16;
-    all_pow2 = all_pow2 && shape_supported(domains[d].N);
-  }
-  const bool fixed_ok = all_fixed && n_domains <= kWarpMaxDomains;
-  // other shapes: a power-of-two N in [4, 128] for every domain
-  const bool shape_ok = !all_fixed && all_pow2 && n_domains <= kWarpMaxDomains;
-  const bool warp_ok = fixed_ok || shape_ok;
-  if ((o.kernel == FPTC_KERNEL_BLOCK_TILE && !all_fixed) || (o.kernel == FPTC_KERNEL_WARP_TILE && !warp_ok)) {
-    set_error("the block-tile kernel needs N = 32, E = 16 in every domain; the warp-tile kernel that, or a "
-              "power-of-two N in [4, 128] in every domain (at most %u domains)", kWarpMaxDomains);
-    return FPTC_ERR_UNSUPPORTED;
-  }
-  if (o.idct != FPTC_IDCT_FP32 || o.kernel == FPTC_KERNEL_TENSOR) {
-    if (!fixed_ok || o.idct == FPTC_IDCT_FP32) {
-      set_error("the tensor-core transform needs N = 32, E = 16 in every domain (at most %u domains) and "
-                "idct = TF32, BF16X3 or TF32X3", kWarpMaxDomains);
+  return guarded([&]() -> fptc_status {
+    clear_error();
+    if (!out) {
+      set_error("plan output pointer is NULL");
+      return FPTC_ERR_INVALID_ARGUMENT;
+    }
+    *out = nullptr;
+    if (n_domains == 0 || !domains) {
+      set_error("at least one domain is required");
+      return FPTC_ERR_INVALID_ARGUMENT;
+    }
+    if (n_segments > 0 && !segments) {
+      set_error("segments is NULL");
+      return FPTC_ERR_INVALID_ARGUMENT;
+    }
+    if (n_segments > 0xFFFFFFF0ull) {
+      set_error("too many segments");
       return FPTC_ERR_UNSUPPORTED;
     }
-    o.kernel = FPTC_KERNEL_TENSOR;
-  }
-  if (o.kernel == FPTC_KERNEL_AUTO) {
-    // the warp-tile kernel keeps every domain's tables in shared memory: it is
-    // the default when they fit beside at least four warps' buffers
-    bool fits = false;
-    if (warp_ok) {
-      std::vector<uint32_t> lm(n_domains);
-      for (uint32_t d = 0; d < n_domains; ++d) lm[d] = domains[d].lmax;
-      WarpParams probe{};
-      int optin = 0;
-      if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device) != cudaSuccess) optin = 0;
-      if (fixed_ok) {
-        fits = warp_smem_layout(128, lm.data(), n_domains, &probe) <= (size_t)optin;
-      } else {
-        std::vector<uint32_t> ns(n_domains), es(n_domains);
-        for (uint32_t d = 0; d < n_domains; ++d) {
-          ns[d] = domains[d].N;
-          es[d] = domains[d].E;
+    fptc_plan_options o{};
+    o.idct = FPTC_IDCT_FP32;
+    o.schedule = FPTC_SCHEDULE_PERSISTENT;
+    if (opts) o = *opts;
+    if (o.idct > FPTC_IDCT_TF32X3 || o.schedule > FPTC_SCHEDULE_THREE_KERNEL || o.reserved[0] || o.reserved[1] ||
+        (o.schedule == FPTC_SCHEDULE_THREE_KERNEL && o.idct != FPTC_IDCT_FP32)) {
+      set_error("invalid plan options");
+      return FPTC_ERR_INVALID_ARGUMENT;
+    }
+    if (o.kernel > FPTC_KERNEL_TENSOR) {
+      set_error("unknown kernel %u", o.kernel);
+      return FPTC_ERR_INVALID_ARGUMENT;
+    }
+    bool all_fixed = true, all_pow2 = n_domains > 0;
+    for (uint32_t d = 0; d < n_domains; ++d) {
+      all_fixed = all_fixed && domains[d].N == 32 && domains[d].E == 16;
+      all_pow2 = all_pow2 && shape_supported(domains[d].N);
+    }
+    const bool fixed_ok = all_fixed && n_domains <= kWarpMaxDomains;
+    // other shapes: a power-of-two N in [4, 128] for every domain
+    const bool shape_ok = !all_fixed && all_pow2 && n_domains <= kWarpMaxDomains;
+    const bool warp_ok = fixed_ok || shape_ok;
+    if ((o.kernel == FPTC_KERNEL_BLOCK_TILE && !all_fixed) || (o.kernel == FPTC_KERNEL_WARP_TILE && !warp_ok)) {
+      set_error("the block-tile kernel needs N = 32, E = 16 in every domain; the warp-tile kernel that, or a "
+                "power-of-two N in [4, 128] in every domain (at most %u domains)", kWarpMaxDomains);
+      return FPTC_ERR_UNSUPPORTED;
+    }
+    if (o.idct != FPTC_IDCT_FP32 || o.kernel == FPTC_KERNEL_TENSOR) {
+      if (!fixed_ok || o.idct == FPTC_IDCT_FP32) {
+        set_error("the tensor-core transform needs N = 32, E = 16 in every domain (at most %u domains) and "
+                  "idct = TF32, BF16X3 or TF32X3", kWarpMaxDomains);
+        return FPTC_ERR_UNSUPPORTED;
+      }
+      o.kernel = FPTC_KERNEL_TENSOR;
+    }
+    if (o.kernel == FPTC_KERNEL_AUTO) {
+      // the warp-tile kernel keeps every domain's tables in shared memory: it is
+      // the default when they fit beside at least four warps' buffers
+      bool fits = false;
+      if (warp_ok) {
+        std::vector<uint32_t> lm(n_domains);
+        for (uint32_t d = 0; d < n_domains; ++d) lm[d] = domains[d].lmax;
+        WarpParams probe{};
+        int optin = 0;
+        if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device) != cudaSuccess) optin = 0;
+        if (fixed_ok) {
+          fits = warp_smem_layout(128, lm.data(), n_domains, &probe) <= (size_t)optin;
+        } else {
+          std::vector<uint32_t> ns(n_domains), es(n_domains);
+          for (uint32_t d = 0; d < n_domains; ++d) {
+            ns[d] = domains[d].N;
+            es[d] = domains[d].E;
+          }
+          fits = shape_smem_layout(256, lm.data(), ns.data(), es.data(), n_domains, &probe) <= (size_t)optin;
         }
-        fits = shape_smem_layout(256, lm.data(), ns.data(), es.data(), n_domains, &probe) <= (size_t)optin;
+      }
+      o.kernel = fits ? FPTC_KERNEL_WARP_TILE : (all_fixed ? FPTC_KERNEL_BLOCK_TILE : FPTC_KERNEL_GENERIC);
+    }
+    if (o.kernel == FPTC_KERNEL_WARP_TILE) o.tile_samples = shape_ok ? 0 : warp_tile_windows() * 32;
+    if (o.kernel == FPTC_KERNEL_TENSOR) o.tile_samples = tc_tile_windows() * 32;
+    if (o.tile_samples == 0) o.tile_samples = o.kernel == FPTC_KERNEL_BLOCK_TILE ? 8192 : 4096;
+    if (o.tile_samples > 65536) {
+      set_error("tile_samples must be <= 65536");
+      return FPTC_ERR_INVALID_ARGUMENT;
+    }
+    for (uint32_t d = 0; d < n_domains; ++d) {
+      fptc_status st = fptc_validate_domain(&domains[d]);
+      if (st != FPTC_OK) {
+        std::string m = fptc_last_error_message();
+        set_error("domain %u: %s", d, m.c_str());
+        return st;
       }
     }
-    o.kernel = fits ? FPTC_KERNEL_WARP_TILE : (all_fixed ? FPTC_KERNEL_BLOCK_TILE : FPTC_KERNEL_GENERIC);
-  }
-  if (o.kernel == FPTC_KERNEL_WARP_TILE) o.tile_samples = shape_ok ? 0 : warp_tile_windows() * 32;
-  if (o.kernel == FPTC_KERNEL_TENSOR) o.tile_samples = tc_tile_windows() * 32;
-  if (o.tile_samples == 0) o.tile_samples = o.kernel == FPTC_KERNEL_BLOCK_TILE ? 8192 : 4096;
-  if (o.tile_samples > 65536) {
-    set_error("tile_samples must be <= 65536");
-    return FPTC_ERR_INVALID_ARGUMENT;
-  }
-  for (uint32_t d = 0; d < n_domains; ++d) {
-    fptc_status st = fptc_validate_domain(&domains[d]);
-    if (st != FPTC_OK) {
-      std::string m = fptc_last_error_message();
-      set_error("domain %u: %s", d, m.c_str());
-      return st;
-    }
-  }
 
-  fptc_plan *p = new (std::nothrow) fptc_plan();
-  if (!p) return FPTC_ERR_OUT_OF_MEMORY;
-  p->device = device;
-  p->opts = o;
-  p->domains.assign(domains, domains + n_domains);
-  p->caller_segs.assign(segments, segments + n_segments);
+    fptc_plan *p = new (std::nothrow) fptc_plan();
+    if (!p) return FPTC_ERR_OUT_OF_MEMORY;
+    p->device = device;
+    p->opts = o;
+    p->domains.assign(domains, domains + n_domains);
+    p->caller_segs.assign(segments, segments + n_segments);
 
-  // ---- segment metadata checks
-  std::vector<std::pair<uint64_t, uint64_t>> out_ranges;
-  for (uint64_t i = 0; i < n_segments; ++i) {
-    const fptc_segment &s = segments[i];
-    if (s.domain >= n_domains || s.reserved != 0) {
-      set_error("segment %llu: domain %u out of range", (unsigned long long)i, s.domain);
-      delete p;
-      return FPTC_ERR_INVALID_ARGUMENT;
+    // ---- segment metadata checks
+    std::vector<std::pair<uint64_t, uint64_t>> out_ranges;
+    for (uint64_t i = 0; i < n_segments; ++i) {
+      const fptc_segment &s = segments[i];
+      if (s.domain >= n_domains || s.reserved != 0) {
+        set_error("segment %llu: domain %u out of range", (unsigned long long)i, s.domain);
+        delete p;
+        return FPTC_ERR_INVALID_ARGUMENT;
+      }
+      const fptc_domain &d = domains[s.domain];
+      const uint64_t W = (s.n_samples + d.N - 1) / d.N;
+      const uint64_t L = W * d.E;
+      // each word holds 1..64 codewords (Alg. 1 never closes an empty word)
+      const uint64_t min_words = (L + 63) / 64;
+      if (s.n_words < min_words || s.n_words > L) {
+        set_error("segment %llu: %llu words cannot hold %llu symbols", (unsigned long long)i,
+                  (unsigned long long)s.n_words, (unsigned long long)L);
+        delete p;
+        return FPTC_ERR_INVALID_ARGUMENT;
+      }
+      if (s.word_offset + s.n_words < s.word_offset || s.out_offset + s.n_samples < s.out_offset) {
+        set_error("segment %llu: offset overflow", (unsigned long long)i);
+        delete p;
+        return FPTC_ERR_INVALID_ARGUMENT;
+      }
+      p->words_extent = std::max(p->words_extent, s.word_offset + s.n_words);
+      p->out_extent = std::max(p->out_extent, s.out_offset + s.n_samples);
+      p->n_samples += s.n_samples;
+      p->n_words += s.n_words;
+      if (s.n_samples) out_ranges.push_back({s.out_offset, s.out_offset + s.n_samples});
     }
-    const fptc_domain &d = domains[s.domain];
-    const uint64_t W = (s.n_samples + d.N - 1) / d.N;
-    const uint64_t L = W * d.E;
-    // each word holds 1..64 codewords (Alg. 1 never closes an empty word)
-    const uint64_t min_words = (L + 63) / 64;
-    if (s.n_words < min_words || s.n_words > L) {
-      set_error("segment %llu: %llu words cannot hold %llu symbols", (unsigned long long)i,
-                (unsigned long long)s.n_words, (unsigned long long)L);
-      delete p;
-      return FPTC_ERR_INVALID_ARGUMENT;
+    std::sort(out_ranges.begin(), out_ranges.end());
+    for (size_t i = 1; i < out_ranges.size(); ++i) {
+      if (out_ranges[i].first < out_ranges[i - 1].second) {
+        set_error("segment output ranges overlap");
+        delete p;
+        return FPTC_ERR_INVALID_ARGUMENT;
+      }
     }
-    if (s.word_offset + s.n_words < s.word_offset || s.out_offset + s.n_samples < s.out_offset) {
-      set_error("segment %llu: offset overflow", (unsigned long long)i);
-      delete p;
-      return FPTC_ERR_INVALID_ARGUMENT;
-    }
-    p->words_extent = std::max(p->words_extent, s.word_offset + s.n_words);
-    p->out_extent = std::max(p->out_extent, s.out_offset + s.n_samples);
-    p->n_samples += s.n_samples;
-    p->n_words += s.n_words;
-    if (s.n_samples) out_ranges.push_back({s.out_offset, s.out_offset + s.n_samples});
-  }
-  std::sort(out_ranges.begin(), out_ranges.end());
-  for (size_t i = 1; i < out_ranges.size(); ++i) {
-    if (out_ranges[i].first < out_ranges[i - 1].second) {
-      set_error("segment output ranges overlap");
-      delete p;
-      return FPTC_ERR_INVALID_ARGUMENT;
-    }
-  }
 
-  // ---- per-domain tables on the host
-  p->dom_dev.resize(n_domains);
-  std::vector<uint16_t> luts;
-  std::vector<float> basis;
-  uint32_t max_lmax = 1;
-  p->basis_cap = 0;
-  for (uint32_t d = 0; d < n_domains; ++d) {
-    const fptc_domain &dm = domains[d];
-    DomainDev &dd = p->dom_dev[d];
-    std::memset(&dd, 0, sizeof(dd));
-    dd.N = dm.N;
-    dd.E = dm.E;
-    dd.B1 = dm.B1;
-    dd.B2 = dm.B2;
-    dd.lmax = dm.lmax;
-    for (int z = 0; z < 3; ++z) dd.scale[z] = static_cast<float>(dm.scale[z]);
+    // ---- per-domain tables on the host
+    p->dom_dev.resize(n_domains);
+    std::vector<uint16_t> luts;
+    std::vector<float> basis;
+    uint32_t max_lmax = 1;
+    p->basis_cap = 0;
+    for (uint32_t d = 0; d < n_domains; ++d) {
+      const fptc_domain &dm = domains[d];
+      DomainDev &dd = p->dom_dev[d];
+      std::memset(&dd, 0, sizeof(dd));
+      dd.N = dm.N;
+      dd.E = dm.E;
+      dd.B1 = dm.B1;
+      dd.B2 = dm.B2;
+      dd.lmax = dm.lmax;
+      for (int z = 0; z < 3; ++z) dd.scale[z] = static_cast<float>(dm.scale[z]);
+      {
+        uint64_t kraft = 0;
+        for (int sy = 0; sy < 256; ++sy)
+          if (dm.code_len[sy]) kraft += uint64_t(1) << (dm.lmax - dm.code_len[sy]);
+        dd.complete = kraft == (uint64_t(1) << dm.lmax);
+      }
+      unit_tables(dm, dd.unit);
+      max_lmax = std::max(max_lmax, dm.lmax);
+      while (luts.size() % 8) luts.push_back(0);  // 16-byte aligned table starts
+      dd.lut_offset = (uint32_t)luts.size();
+      luts.resize(luts.size() + (size_t(1) << dm.lmax));
+      fptc_build_decode_table(&dm, luts.data() + dd.lut_offset);
+      while (basis.size() % 4) basis.push_back(0.f);
+      dd.basis_offset = (uint32_t)basis.size();
+      for (uint32_t k = 0; k < dm.E; ++k)
+        for (uint32_t n = 0; n < dm.N; ++n)
+          basis.push_back(k == 0 ? 0.5f
+                                 : static_cast<float>(std::cos(M_PI * (2.0 * n + 1.0) * k / (2.0 * dm.N))));
+      p->basis_cap = std::max(p->basis_cap, dm.N * dm.E);
+    }
+    p->lut_cap = 1u << max_lmax;
+    p->kind = (int)o.kernel;
+    p->shape = shape_ok;
+
+    // ---- tile queue: segments ordered by output offset
+    p->queue.resize(n_segments);
+    std::iota(p->queue.begin(), p->queue.end(), 0u);
+    std::stable_sort(p->queue.begin(), p->queue.end(), [&](uint32_t a, uint32_t b) {
+      return segments[a].out_offset < segments[b].out_offset;
+    });
+    p->level_off.resize(n_segments);
+    uint64_t lv = 0;
+    for (uint64_t i = 0; i < n_segments; ++i) {
+      const fptc_domain &d = domains[segments[i].domain];
+      p->level_off[i] = lv;
+      lv += (segments[i].n_samples + d.N - 1) / d.N * d.E;
+    }
+    p->n_levels = lv;
+    p->segs.resize(n_segments);
+    uint64_t chunk = 0;
+    for (uint64_t qi = 0; qi < n_segments; ++qi) {
+      const uint32_t ci = p->queue[qi];
+      const fptc_segment &s = segments[ci];
+      const fptc_domain &d = domains[s.domain];
+      SegDev &sd = p->segs[qi];
+      std::memset(&sd, 0, sizeof(sd));
+      sd.word_offset = s.word_offset;
+      sd.n_words = s.n_words;
+      sd.n_samples = s.n_samples;
+      sd.out_offset = s.out_offset;
+      sd.level_offset = p->level_off[ci];
+      sd.n_windows = (s.n_samples + d.N - 1) / d.N;
+      sd.domain = s.domain;
+      sd.caller_index = ci;
+      sd.out_aligned = ((s.out_offset % 4) == 0 ? 1u : 0u) | ((s.out_offset % 8) == 0 ? 2u : 0u) |
+                       ((s.out_offset % 32) == 0 ? 4u : 0u);
+      sd.chunk_base = chunk;
+      sd.n_chunks = (uint32_t)chunks_of(s.n_words);
+      chunk += sd.n_chunks;
+    }
+    p->n_chunks = chunk;
+    layout_tiles(p, o.tile_samples);
+
+    // ---- device
+    fptc_status st = FPTC_OK;
     {
-      uint64_t kraft = 0;
-      for (int sy = 0; sy < 256; ++sy)
-        if (dm.code_len[sy]) kraft += uint64_t(1) << (dm.lmax - dm.code_len[sy]);
-      dd.complete = kraft == (uint64_t(1) << dm.lmax);
-    }
-    unit_tables(dm, dd.unit);
-    max_lmax = std::max(max_lmax, dm.lmax);
-    while (luts.size() % 8) luts.push_back(0);  // 16-byte aligned table starts
-    dd.lut_offset = (uint32_t)luts.size();
-    luts.resize(luts.size() + (size_t(1) << dm.lmax));
-    fptc_build_decode_table(&dm, luts.data() + dd.lut_offset);
-    while (basis.size() % 4) basis.push_back(0.f);
-    dd.basis_offset = (uint32_t)basis.size();
-    for (uint32_t k = 0; k < dm.E; ++k)
-      for (uint32_t n = 0; n < dm.N; ++n)
-        basis.push_back(k == 0 ? 0.5f
-                               : static_cast<float>(std::cos(M_PI * (2.0 * n + 1.0) * k / (2.0 * dm.N))));
-    p->basis_cap = std::max(p->basis_cap, dm.N * dm.E);
-  }
-  p->lut_cap = 1u << max_lmax;
-  p->kind = (int)o.kernel;
-  p->shape = shape_ok;
-
-  // ---- tile queue: segments ordered by output offset
-  p->queue.resize(n_segments);
-  std::iota(p->queue.begin(), p->queue.end(), 0u);
-  std::stable_sort(p->queue.begin(), p->queue.end(), [&](uint32_t a, uint32_t b) {
-    return segments[a].out_offset < segments[b].out_offset;
-  });
-  p->level_off.resize(n_segments);
-  uint64_t lv = 0;
-  for (uint64_t i = 0; i < n_segments; ++i) {
-    const fptc_domain &d = domains[segments[i].domain];
-    p->level_off[i] = lv;
-    lv += (segments[i].n_samples + d.N - 1) / d.N * d.E;
-  }
-  p->n_levels = lv;
-  p->segs.resize(n_segments);
-  uint64_t chunk = 0;
-  for (uint64_t qi = 0; qi < n_segments; ++qi) {
-    const uint32_t ci = p->queue[qi];
-    const fptc_segment &s = segments[ci];
-    const fptc_domain &d = domains[s.domain];
-    SegDev &sd = p->segs[qi];
-    std::memset(&sd, 0, sizeof(sd));
-    sd.word_offset = s.word_offset;
-    sd.n_words = s.n_words;
-    sd.n_samples = s.n_samples;
-    sd.out_offset = s.out_offset;
-    sd.level_offset = p->level_off[ci];
-    sd.n_windows = (s.n_samples + d.N - 1) / d.N;
-    sd.domain = s.domain;
-    sd.caller_index = ci;
-    sd.out_aligned = ((s.out_offset % 4) == 0 ? 1u : 0u) | ((s.out_offset % 8) == 0 ? 2u : 0u) |
-                     ((s.out_offset % 32) == 0 ? 4u : 0u);
-    sd.chunk_base = chunk;
-    sd.n_chunks = (uint32_t)chunks_of(s.n_words);
-    chunk += sd.n_chunks;
-  }
-  p->n_chunks = chunk;
-  layout_tiles(p, o.tile_samples);
-
-  // ---- device
-  fptc_status st = FPTC_OK;
-  {
-    DeviceGuard g(device);
-    if (!g.ok) {
-      set_error("cannot select device %d", device);
-      delete p;
-      return FPTC_ERR_CUDA;
-    }
-    cudaError_t e = cudaDeviceGetAttribute(&p->sm_count, cudaDevAttrMultiProcessorCount, device);
-    if (e != cudaSuccess) {
-      st = cuda_fail(e, "device query");
-      delete p;
-      return st;
-    }
-    size_t b = 0;
-    if ((e = upload(&p->d_domains, p->dom_dev, &b)) != cudaSuccess ||
-        (e = upload(&p->d_segs, p->segs, &b)) != cudaSuccess ||
-        (e = upload(&p->d_luts, luts, &b)) != cudaSuccess || (e = upload(&p->d_basis, basis, &b)) != cudaSuccess) {
-      st = cuda_fail(e, "plan upload");
-    }
-    if (st == FPTC_OK) {
-      const size_t nc = std::max<uint64_t>(p->n_chunks, 1), ns = std::max<uint64_t>(n_segments, 1);
-      if ((e = cudaMalloc(&p->d_chunk_sum, nc * 4)) != cudaSuccess ||
-          (e = cudaMalloc(&p->d_chunk_off, nc * 8)) != cudaSuccess ||
-          (e = cudaMalloc(&p->d_seg_bad, ns * 4)) != cudaSuccess ||
-          (e = cudaMalloc(&p->d_status, sizeof(DevStatus))) != cudaSuccess) {
-        st = cuda_fail(e, "plan scratch");
-      } else {
-        b += nc * 12 + ns * 4 + sizeof(DevStatus);
-        DevStatus s0{0u, 0u, ~0ull};
-        e = cudaMemcpy(p->d_status, &s0, sizeof(s0), cudaMemcpyHostToDevice);
-        if (e == cudaSuccess) e = cudaMemset(p->d_seg_bad, 0, ns * 4);
-        if (e == cudaSuccess && o.schedule == FPTC_SCHEDULE_THREE_KERNEL) {
-          e = cudaMalloc(&p->d_word_off, std::max<uint64_t>(p->words_extent, 1) * 4);
-          if (e == cudaSuccess) e = cudaMalloc(&p->d_lev_scratch, std::max<uint64_t>(p->n_levels, 1));
-          if (e == cudaSuccess) b += std::max<uint64_t>(p->words_extent, 1) * 4 + std::max<uint64_t>(p->n_levels, 1);
+      DeviceGuard g(device);
+      if (!g.ok) {
+        set_error("cannot select device %d", device);
+        delete p;
+        return FPTC_ERR_CUDA;
+      }
+      cudaError_t e = cudaDeviceGetAttribute(&p->sm_count, cudaDevAttrMultiProcessorCount, device);
+      if (e != cudaSuccess) {
+        st = cuda_fail(e, "device query");
+        delete p;
+        return st;
+      }
+      size_t b = 0;
+      if ((e = upload(&p->d_domains, p->dom_dev, &b)) != cudaSuccess ||
+          (e = upload(&p->d_segs, p->segs, &b)) != cudaSuccess ||
+          (e = upload(&p->d_luts, luts, &b)) != cudaSuccess || (e = upload(&p->d_basis, basis, &b)) != cudaSuccess) {
+        st = cuda_fail(e, "plan upload");
+      }
+      if (st == FPTC_OK) {
+        const size_t nc = std::max<uint64_t>(p->n_chunks, 1), ns = std::max<uint64_t>(n_segments, 1);
+        if ((e = cudaMalloc(&p->d_chunk_sum, nc * 4)) != cudaSuccess ||
+            (e = cudaMalloc(&p->d_chunk_off, nc * 8)) != cudaSuccess ||
+            (e = cudaMalloc(&p->d_seg_bad, ns * 4)) != cudaSuccess ||
+            (e = cudaMalloc(&p->d_status, sizeof(DevStatus))) != cudaSuccess) {
+          st = cuda_fail(e, "plan scratch");
+        } else {
+          b += nc * 12 + ns * 4 + sizeof(DevStatus);
+          DevStatus s0{0u, 0u, ~0ull};
+          e = cudaMemcpy(p->d_status, &s0, sizeof(s0), cudaMemcpyHostToDevice);
+          if (e == cudaSuccess) e = cudaMemset(p->d_seg_bad, 0, ns * 4);
+          if (e == cudaSuccess && o.schedule == FPTC_SCHEDULE_THREE_KERNEL) {
+            e = cudaMalloc(&p->d_word_off, std::max<uint64_t>(p->words_extent, 1) * 4);
+            if (e == cudaSuccess) e = cudaMalloc(&p->d_lev_scratch, std::max<uint64_t>(p->n_levels, 1));
+            if (e == cudaSuccess) b += std::max<uint64_t>(p->words_extent, 1) * 4 + std::max<uint64_t>(p->n_levels, 1);
+          }
+          if (e != cudaSuccess) st = cuda_fail(e, "plan scratch init");
         }
-        if (e != cudaSuccess) st = cuda_fail(e, "plan scratch init");
+      }
+      p->device_bytes = b;
+      if (st == FPTC_OK) st = upload_layout(p);
+      if (st == FPTC_OK) st = configure_launch(p);
+      if (st == FPTC_OK) {
+        for (auto &a : p->aux)
+          if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&a, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->up, cudaStreamNonBlocking);
+        for (auto &v : p->ev)
+          if (e == cudaSuccess) e = cudaEventCreateWithFlags(&v, cudaEventDisableTiming);
+        for (auto &v : p->evh)
+          if (e == cudaSuccess) e = cudaEventCreateWithFlags(&v, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_start, cudaEventDisableTiming);
+        if (e != cudaSuccess)
+          st = cuda_fail(e, "plan streams");
+      }
+      if (st != FPTC_OK) {
+        free_device(p);
+        delete p;
+        return st;
       }
     }
-    p->device_bytes = b;
-    if (st == FPTC_OK) st = upload_layout(p);
-    if (st == FPTC_OK) st = configure_launch(p);
-    if (st == FPTC_OK) {
-      for (auto &a : p->aux)
-        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&a, cudaStreamNonBlocking);
-      if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->up, cudaStreamNonBlocking);
-      for (auto &v : p->ev)
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&v, cudaEventDisableTiming);
-      for (auto &v : p->evh)
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&v, cudaEventDisableTiming);
-      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_start, cudaEventDisableTiming);
-      if (e != cudaSuccess)
-        st = cuda_fail(e, "plan streams");
-    }
-    if (st != FPTC_OK) {
-      free_device(p);
-      delete p;
-      return st;
-    }
-  }
-  *out = p;
-  return FPTC_OK;
+    *out = p;
+    return FPTC_OK;
+  });
 }
 
 void fptc_plan_destroy(fptc_plan *p) {
@@ -782,13 +784,15 @@ fptc_status fptc_plan_get_info(const fptc_plan *p, fptc_plan_info *info) {
 }
 
 fptc_status fptc_plan_level_offsets(const fptc_plan *p, uint64_t *offsets) {
-  if (check_plan(p) != FPTC_OK) return FPTC_ERR_INVALID_ARGUMENT;
-  if (!offsets && !p->level_off.empty()) {
-    set_error("offsets is NULL");
-    return FPTC_ERR_INVALID_ARGUMENT;
-  }
-  std::copy(p->level_off.begin(), p->level_off.end(), offsets);
-  return FPTC_OK;
+  return guarded([&]() -> fptc_status {
+    if (check_plan(p) != FPTC_OK) return FPTC_ERR_INVALID_ARGUMENT;
+    if (!offsets && !p->level_off.empty()) {
+      set_error("offsets is NULL");
+      return FPTC_ERR_INVALID_ARGUMENT;
+    }
+    std::copy(p->level_off.begin(), p->level_off.end(), offsets);
+    return FPTC_OK;
+  });
 }
 
 uint32_t fptc_plan_launches_per_decode(const fptc_plan *p) {
@@ -885,98 +889,101 @@ fptc_status fptc_decode_backward(fptc_plan *p, const uint64_t *d_words, const ui
 
 fptc_status fptc_decode_host(fptc_plan *p, const uint64_t *h_words, const uint8_t *h_symlen, float *h_out,
                              uint64_t *d_words, uint8_t *d_symlen, float *d_out, fptc_stream stream) {
-  clear_error();
-  fptc_status st = check_plan(p);
-  if (st != FPTC_OK) return st;
-  if (p->segs.empty()) return FPTC_OK;
-  const bool any_words = p->words_extent > 0, any_out = p->out_extent > 0;
-  if ((st = check_ptr(h_words, 8, any_words, "h_words")) != FPTC_OK ||
-      (st = check_ptr(h_symlen, 1, any_words, "h_symlen")) != FPTC_OK ||
-      (st = check_ptr(h_out, 4, any_out, "h_out")) != FPTC_OK ||
-      (st = check_ptr(d_words, 8, any_words, "d_words")) != FPTC_OK ||
-      (st = check_ptr(d_symlen, 1, any_words, "d_symlen")) != FPTC_OK ||
-      (st = check_ptr(d_out, 16, any_out, "d_out")) != FPTC_OK)
-    return st;
-  DeviceGuard g(p->device);
-  if (!g.ok) return cuda_fail(cudaGetLastError(), "set device");
-  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  // Pieces of about equal output in queue (output) order.  Piece k's words go
-  // up on the upload stream, it is indexed and decoded on `stream` once they
-  // are there, and its samples go back on one of the copy-back streams, so
-  // uploads, decoding and copies back of different pieces overlap.
-  struct Piece {
-    uint32_t s0, s1;
-    uint64_t w0, w1;  // hull of the piece's words
-    uint64_t o0, o1;  // hull of its output
-  };
-  std::vector<Piece> pieces;
-  {
-    const uint32_t n = (uint32_t)p->segs.size();
-    const uint64_t per = (p->n_samples + fptc_plan::kPieces - 1) / fptc_plan::kPieces;
-    uint32_t s0 = 0;
-    while (s0 < n) {
-      uint32_t s1 = s0;
-      uint64_t acc = 0;
-      while (s1 < n && (acc < per || s1 == s0)) acc += p->segs[s1++].n_samples;
-      if (pieces.size() == fptc_plan::kPieces - 1) s1 = n;  // the last piece takes the rest
-      Piece pc{s0, s1, UINT64_MAX, 0, UINT64_MAX, 0};
-      for (uint32_t i = s0; i < s1; ++i) {
-        const SegDev &sg = p->segs[i];
-        if (sg.n_words) {
-          pc.w0 = std::min(pc.w0, sg.word_offset);
-          pc.w1 = std::max(pc.w1, sg.word_offset + sg.n_words);
+  return guarded([&]() -> fptc_status {
+    clear_error();
+    fptc_status st = check_plan(p);
+    if (st != FPTC_OK) return st;
+    if (p->segs.empty()) return FPTC_OK;
+    const bool any_words = p->words_extent > 0, any_out = p->out_extent > 0;
+    if ((st = check_ptr(h_words, 8, any_words, "h_words")) != FPTC_OK ||
+        (st = check_ptr(h_symlen, 1, any_words, "h_symlen")) != FPTC_OK ||
+        (st = check_ptr(h_out, 4, any_out, "h_out")) != FPTC_OK ||
+        (st = check_ptr(d_words, 8, any_words, "d_words")) != FPTC_OK ||
+        (st = check_ptr(d_symlen, 1, any_words, "d_symlen")) != FPTC_OK ||
+        (st = check_ptr(d_out, 16, any_out, "d_out")) != FPTC_OK)
+      return st;
+    DeviceGuard g(p->device);
+    if (!g.ok) return cuda_fail(cudaGetLastError(), "set device");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    // Pieces of about equal output in queue (output) order.  Piece k's words go
+    // up on the upload stream, it is indexed and decoded on `stream` once they
+    // are there, and its samples go back on one of the copy-back streams, so
+    // uploads, decoding and copies back of different pieces overlap.
+    struct Piece {
+      uint32_t s0, s1;
+      uint64_t w0, w1;  // hull of the piece's words
+      uint64_t o0, o1;  // hull of its output
+    };
+    std::vector<Piece> pieces;
+    {
+      const uint32_t n = (uint32_t)p->segs.size();
+      const uint64_t per = (p->n_samples + fptc_plan::kPieces - 1) / fptc_plan::kPieces;
+      uint32_t s0 = 0;
+      while (s0 < n) {
+        uint32_t s1 = s0;
+        uint64_t acc = 0;
+        while (s1 < n && (acc < per || s1 == s0)) acc += p->segs[s1++].n_samples;
+        if (pieces.size() == fptc_plan::kPieces - 1) s1 = n;  // the last piece takes the rest
+        Piece pc{s0, s1, UINT64_MAX, 0, UINT64_MAX, 0};
+        for (uint32_t i = s0; i < s1; ++i) {
+          const SegDev &sg = p->segs[i];
+          if (sg.n_words) {
+            pc.w0 = std::min(pc.w0, sg.word_offset);
+            pc.w1 = std::max(pc.w1, sg.word_offset + sg.n_words);
+          }
+          if (sg.n_samples) {
+            pc.o0 = std::min(pc.o0, sg.out_offset);
+            pc.o1 = std::max(pc.o1, sg.out_offset + sg.n_samples);
+          }
         }
-        if (sg.n_samples) {
-          pc.o0 = std::min(pc.o0, sg.out_offset);
-          pc.o1 = std::max(pc.o1, sg.out_offset + sg.n_samples);
-        }
+        pieces.push_back(pc);
+        s0 = s1;
       }
-      pieces.push_back(pc);
-      s0 = s1;
     }
-  }
-  // uploads per piece only where the pieces' word hulls are disjoint and ascending
-  // (words laid out in output order); otherwise every word goes up first
-  bool split_up = true;
-  {
-    uint64_t end = 0;
-    for (const Piece &pc : pieces)
-      if (pc.w1 > pc.w0) {
-        split_up = split_up && pc.w0 >= end;
-        end = pc.w1;
-      }
-  }
-  auto upload = [&](uint64_t w0, uint64_t w1) -> cudaError_t {
-    if (w1 <= w0) return cudaSuccess;
-    cudaError_t r = cudaMemcpyAsync(d_words + w0, h_words + w0, (w1 - w0) * 8, cudaMemcpyHostToDevice, p->up);
-    if (r == cudaSuccess) r = cudaMemcpyAsync(d_symlen + w0, h_symlen + w0, w1 - w0, cudaMemcpyHostToDevice, p->up);
-    return r;
-  };
-  // the device buffers are the caller's: uploads start after the work already on `stream`
-  cudaError_t e = cudaEventRecord(p->ev_start, s);
-  if (e == cudaSuccess) e = cudaStreamWaitEvent(p->up, p->ev_start, 0);
-  if (e == cudaSuccess && any_words && !split_up) e = upload(0, p->words_extent);
-  if (e != cudaSuccess) return cuda_fail(e, "copy to device");
-  const IndexParams ip = index_params(p, d_symlen, needs_records(p));
-  const DecodeParams dp = decode_params(p, d_words, d_symlen, d_out, nullptr, nullptr);
-  for (size_t k = 0; k < pieces.size() && e == cudaSuccess; ++k) {
-    const Piece &pc = pieces[k];
-    if (split_up) e = upload(pc.w0, pc.w1);
-    if (e == cudaSuccess) e = cudaEventRecord(p->evh[k], p->up);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, p->evh[k], 0);
-    if (e == cudaSuccess) e = run_range(p, ip, dp, pc.s0, pc.s1, true, s);
-    if (e != cudaSuccess) break;
-    cudaStream_t a = p->aux[k % fptc_plan::kAux];
-    if ((e = cudaEventRecord(p->ev[k], s)) != cudaSuccess) break;
-    if ((e = cudaStreamWaitEvent(a, p->ev[k], 0)) != cudaSuccess) break;
-    if (pc.o1 > pc.o0) e = cudaMemcpyAsync(h_out + pc.o0, d_out + pc.o0, (pc.o1 - pc.o0) * 4, cudaMemcpyDeviceToHost, a);
-  }
-  if (e == cudaSuccess) e = cudaStreamSynchronize(p->up);
-  for (auto &a : p->aux)
-    if (e == cudaSuccess) e = cudaStreamSynchronize(a);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  if (e != cudaSuccess) return cuda_fail(e, "end-to-end decode");
-  return FPTC_OK;
+    // uploads per piece only where the pieces' word hulls are disjoint and ascending
+    // (words laid out in output order); otherwise every word goes up first
+    bool split_up = true;
+    {
+      uint64_t end = 0;
+      for (const Piece &pc : pieces)
+        if (pc.w1 > pc.w0) {
+          split_up = split_up && pc.w0 >= end;
+          end = pc.w1;
+        }
+    }
+    auto upload = [&](uint64_t w0, uint64_t w1) -> cudaError_t {
+      if (w1 <= w0) return cudaSuccess;
+      cudaError_t r = cudaMemcpyAsync(d_words + w0, h_words + w0, (w1 - w0) * 8, cudaMemcpyHostToDevice, p->up);
+      if (r == cudaSuccess) r = cudaMemcpyAsync(d_symlen + w0, h_symlen + w0, w1 - w0, cudaMemcpyHostToDevice, p->up);
+      return r;
+    };
+    // the device buffers are the caller's: uploads start after the work already on `stream`
+    cudaError_t e = cudaEventRecord(p->ev_start, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(p->up, p->ev_start, 0);
+    if (e == cudaSuccess && any_words && !split_up) e = upload(0, p->words_extent);
+    if (e != cudaSuccess) return cuda_fail(e, "copy to device");
+    const IndexParams ip = index_params(p, d_symlen, needs_records(p));
+    const DecodeParams dp = decode_params(p, d_words, d_symlen, d_out, nullptr, nullptr);
+    for (size_t k = 0; k < pieces.size() && e == cudaSuccess; ++k) {
+      const Piece &pc = pieces[k];
+      if (split_up) e = upload(pc.w0, pc.w1);
+      if (e == cudaSuccess) e = cudaEventRecord(p->evh[k], p->up);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(s, p->evh[k], 0);
+      if (e == cudaSuccess) e = run_range(p, ip, dp, pc.s0, pc.s1, true, s);
+      if (e != cudaSuccess) break;
+      cudaStream_t a = p->aux[k % fptc_plan::kAux];
+      if ((e = cudaEventRecord(p->ev[k], s)) != cudaSuccess) break;
+      if ((e = cudaStreamWaitEvent(a, p->ev[k], 0)) != cudaSuccess) break;
+      if (pc.o1 > pc.o0)
+        e = cudaMemcpyAsync(h_out + pc.o0, d_out + pc.o0, (pc.o1 - pc.o0) * 4, cudaMemcpyDeviceToHost, a);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(p->up);
+    for (auto &a : p->aux)
+      if (e == cudaSuccess) e = cudaStreamSynchronize(a);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "end-to-end decode");
+    return FPTC_OK;
+  });
 }
 
 fptc_status fptc_plan_device_status(fptc_plan *p, uint32_t *flags, uint64_t *first_bad) {
@@ -1004,84 +1011,88 @@ fptc_status fptc_plan_device_status(fptc_plan *p, uint32_t *flags, uint64_t *fir
 
 fptc_status fptc_plan_autotune(fptc_plan *p, const uint64_t *d_words, const uint8_t *d_symlen, float *d_out,
                                uint32_t trials, fptc_stream stream, fptc_plan_options *best, float *best_ms) {
-  clear_error();
-  fptc_status st = check_plan(p);
-  if (st != FPTC_OK) return st;
-  if (trials == 0) trials = 3;
-  DeviceGuard g(p->device);
-  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  const fptc_plan_options keep = p->opts;
-  const int keep_kind = p->kind;
-  bool fixed = true;
-  for (const auto &d : p->domains) fixed = fixed && d.N == 32 && d.E == 16;
-  struct Cand {
-    uint32_t kernel, tile_samples, threads;
-  };
-  std::vector<Cand> cands;
-  if (keep.idct != FPTC_IDCT_FP32)
-    for (uint32_t th : {256u, 384u, 512u, 640u, 768u}) cands.push_back({FPTC_KERNEL_TENSOR, tc_tile_windows() * 32, th});
-  for (uint32_t th : {128u, 256u, 512u, 768u, 1024u}) {
-    if (keep.idct != FPTC_IDCT_FP32) continue;
-    if (th > 512) {
+  return guarded([&]() -> fptc_status {
+    clear_error();
+    fptc_status st = check_plan(p);
+    if (st != FPTC_OK) return st;
+    if (trials == 0) trials = 3;
+    DeviceGuard g(p->device);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const fptc_plan_options keep = p->opts;
+    const int keep_kind = p->kind;
+    bool fixed = true;
+    for (const auto &d : p->domains) fixed = fixed && d.N == 32 && d.E == 16;
+    struct Cand {
+      uint32_t kernel, tile_samples, threads;
+    };
+    std::vector<Cand> cands;
+    if (keep.idct != FPTC_IDCT_FP32)
+      for (uint32_t th : {256u, 384u, 512u, 640u, 768u})
+        cands.push_back({FPTC_KERNEL_TENSOR, tc_tile_windows() * 32, th});
+    for (uint32_t th : {128u, 256u, 512u, 768u, 1024u}) {
+      if (keep.idct != FPTC_IDCT_FP32) continue;
+      if (th > 512) {
+        if (fixed && p->domains.size() <= kWarpMaxDomains)
+          cands.push_back({FPTC_KERNEL_WARP_TILE, warp_tile_windows() * 32, th});
+        if (p->shape && th == 768) cands.push_back({FPTC_KERNEL_WARP_TILE, 4096, th});
+        continue;
+      }
       if (fixed && p->domains.size() <= kWarpMaxDomains)
         cands.push_back({FPTC_KERNEL_WARP_TILE, warp_tile_windows() * 32, th});
-      if (p->shape && th == 768) cands.push_back({FPTC_KERNEL_WARP_TILE, 4096, th});
-      continue;
+      if (p->shape && th >= 256) cands.push_back({FPTC_KERNEL_WARP_TILE, 4096, th});
+      if (fixed)
+        for (uint32_t ts : {4096u, 8192u}) cands.push_back({FPTC_KERNEL_BLOCK_TILE, ts, th});
+      else
+        for (uint32_t ts : {2048u, 4096u, 8192u}) cands.push_back({FPTC_KERNEL_GENERIC, ts, th});
     }
-    if (fixed && p->domains.size() <= kWarpMaxDomains) cands.push_back({FPTC_KERNEL_WARP_TILE, warp_tile_windows() * 32, th});
-    if (p->shape && th >= 256) cands.push_back({FPTC_KERNEL_WARP_TILE, 4096, th});
-    if (fixed)
-      for (uint32_t ts : {4096u, 8192u}) cands.push_back({FPTC_KERNEL_BLOCK_TILE, ts, th});
-    else
-      for (uint32_t ts : {2048u, 4096u, 8192u}) cands.push_back({FPTC_KERNEL_GENERIC, ts, th});
-  }
-  fptc_plan_options win = keep;
-  int win_kind = keep_kind;
-  float win_ms = 1e30f;
-  cudaEvent_t a, b;
-  cudaEventCreate(&a);
-  cudaEventCreate(&b);
-  for (const Cand &c : cands) {
-    p->opts = keep;
-    p->opts.kernel = c.kernel;
-    p->opts.tile_samples = c.tile_samples;
-    p->opts.threads = c.threads;
-    p->opts.ctas_per_sm = 0;
-    p->kind = (int)c.kernel;
-    layout_tiles(p, c.tile_samples);
-    if (upload_layout(p) != FPTC_OK || configure_launch(p) != FPTC_OK) continue;
-    if (fptc_decode_batch(p, d_words, d_symlen, d_out, nullptr, nullptr, stream) != FPTC_OK) continue;
-    std::vector<float> ms;
-    for (uint32_t t = 0; t < trials; ++t) {
-      cudaEventRecord(a, s);
-      fptc_decode_batch(p, d_words, d_symlen, d_out, nullptr, nullptr, stream);
-      cudaEventRecord(b, s);
-      cudaEventSynchronize(b);
-      float m = 0;
-      cudaEventElapsedTime(&m, a, b);
-      ms.push_back(m);
+    fptc_plan_options win = keep;
+    int win_kind = keep_kind;
+    float win_ms = 1e30f;
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    for (const Cand &c : cands) {
+      p->opts = keep;
+      p->opts.kernel = c.kernel;
+      p->opts.tile_samples = c.tile_samples;
+      p->opts.threads = c.threads;
+      p->opts.ctas_per_sm = 0;
+      p->kind = (int)c.kernel;
+      layout_tiles(p, c.tile_samples);
+      if (upload_layout(p) != FPTC_OK || configure_launch(p) != FPTC_OK) continue;
+      if (fptc_decode_batch(p, d_words, d_symlen, d_out, nullptr, nullptr, stream) != FPTC_OK) continue;
+      std::vector<float> ms;
+      for (uint32_t t = 0; t < trials; ++t) {
+        cudaEventRecord(a, s);
+        fptc_decode_batch(p, d_words, d_symlen, d_out, nullptr, nullptr, stream);
+        cudaEventRecord(b, s);
+        cudaEventSynchronize(b);
+        float m = 0;
+        cudaEventElapsedTime(&m, a, b);
+        ms.push_back(m);
+      }
+      std::sort(ms.begin(), ms.end());
+      const float med = ms[ms.size() / 2];
+      if (med < win_ms) {
+        win_ms = med;
+        win = p->opts;
+        win_kind = p->kind;
+      }
     }
-    std::sort(ms.begin(), ms.end());
-    const float med = ms[ms.size() / 2];
-    if (med < win_ms) {
-      win_ms = med;
-      win = p->opts;
-      win_kind = p->kind;
-    }
-  }
-  cudaEventDestroy(a);
-  cudaEventDestroy(b);
-  p->opts = win;
-  p->kind = win_kind;
-  layout_tiles(p, win.tile_samples);
-  st = upload_layout(p);
-  if (st == FPTC_OK) st = configure_launch(p);
-  if (st != FPTC_OK) return st;
-  if (best) *best = win;
-  if (best_ms) *best_ms = win_ms;
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return cuda_fail(e, "autotune");
-  return FPTC_OK;
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    p->opts = win;
+    p->kind = win_kind;
+    layout_tiles(p, win.tile_samples);
+    st = upload_layout(p);
+    if (st == FPTC_OK) st = configure_launch(p);
+    if (st != FPTC_OK) return st;
+    if (best) *best = win;
+    if (best_ms) *best_ms = win_ms;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "autotune");
+    return FPTC_OK;
+  });
 }
 
 }  // extern "C"
