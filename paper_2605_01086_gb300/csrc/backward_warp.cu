@@ -185,6 +185,7 @@ __global__ void __launch_bounds__(WARPS * 32, 1) k_backward_warp(const BackwardP
 
   uint32_t phase[2] = {0u, 0u};
   uint32_t nload = 0;       // TMA loads issued (buffer = count & 1)
+  uint32_t pend = 0;        // buffers with a load not yet waited for (bit b = buffer b)
   bool timeout = false;
   double acc0 = 0.0, acc1 = 0.0;
   uint32_t acc_dom = 0xFFFFFFFFu;
@@ -252,6 +253,7 @@ __global__ void __launch_bounds__(WARPS * 32, 1) k_backward_warp(const BackwardP
       if (!si.tma) return;
       si.buf = nload & 1u;
       ++nload;
+      pend |= 1u << si.buf;
       if (lane == 0) tma_load_rows(&gx_map, gtile + si.buf * kGxTile, smem_addr(mbar + si.buf), (int32_t)si.row);
     };
     StepIn si = step_in(0);  // first step's gradient rows in flight during the decode
@@ -283,11 +285,12 @@ __global__ void __launch_bounds__(WARPS * 32, 1) k_backward_warp(const BackwardP
             break;
           }
         }
-        phase[si.buf] ^= 1u;
-        if (__any_sync(0xffffffffu, late)) {
+        if (__any_sync(0xffffffffu, late)) {  // the load stays pending: waited for again below
           timeout = true;
           break;
         }
+        phase[si.buf] ^= 1u;
+        pend &= ~(1u << si.buf);
         const unsigned char *row = gtile + si.buf * kGxTile + lane * (kN * 4);
         const uint32_t sx = lane & 7u;
 #pragma unroll
@@ -348,6 +351,16 @@ __global__ void __launch_bounds__(WARPS * 32, 1) k_backward_warp(const BackwardP
       si = sn2;
     }
     __syncwarp();
+  }
+  // After an expired wait, up to two loads (the late one and the next step's)
+  // may still be writing this warp's tiles: wait for them again, bounded, so
+  // that no bulk copy into shared memory outlives the CTA.  Without a timeout
+  // nothing is pending here (a tile's last step issues no further load).
+  for (uint32_t b = 0; b < 2; ++b) {
+    if (!(pend & (1u << b))) continue;
+    uint32_t it = 0;
+    while (!mbar_try_wait(smem_addr(mbar + b), phase[b]) && ++it < kWaitLimit) {
+    }
   }
   flush();
   if (timeout && lane == 0) atomicOr(&p.status->flags, kFlagTimeout);

@@ -472,7 +472,16 @@ __global__ void __launch_bounds__(NWG * 128, 1) k_decode_tc(const DecodeParams p
     __syncwarp();  // the level bytes are rewritten by the next tile
   }
   if (!stop && !timeout && k > 0) drain(prev);
-  if ((stop || timeout) && lane == 0) atomicOr(&p.status->flags, kFlagTimeout);
+  if (stop || timeout) {
+    // An expired wait leaves the product it waited for possibly still writing
+    // D (no later product was issued: the warpgroup stops at the barrier that
+    // follows).  Wait for its commit once more, bounded, before the tensor
+    // memory is released; the phase of that commit is the one before `phase`.
+    uint32_t it = 0;
+    while (!mbar_try_wait(smem_addr(mbar + wg), phase ^ 1u) && ++it < kWaitLimit) {
+    }
+    if (lane == 0) atomicOr(&p.status->flags, kFlagTimeout);
+  }
   if (tma_pending && lane == 0) tma_wait_all();
 
   // ---- release tensor memory (every warp has finished its tcgen05.ld)
