@@ -200,6 +200,15 @@ fptc_status fptc_decode_batch(fptc_plan *plan, const uint64_t *d_words, const ui
  * stages = FPTC_STAGE_INDEX | FPTC_STAGE_DECODE is fptc_decode_batch. */
 #define FPTC_STAGE_INDEX 1u
 #define FPTC_STAGE_DECODE 2u
+/* Plans of schedule FPTC_SCHEDULE_THREE_KERNEL only (the paper's lossless and
+ * lossy kernels, Sec. 4.2, whose run-time split Sec. 6 reports): the decode
+ * stage's two halves on their own.  FPTC_STAGE_LOSSLESS decodes every word's
+ * codewords into the plan's global level array; FPTC_STAGE_LOSSY dequantizes and
+ * inverse transforms that array into d_out (it reads what the last lossless
+ * stage of this plan wrote).  FPTC_STAGE_DECODE = both.  Other schedules fuse
+ * the two halves in one kernel and return FPTC_ERR_UNSUPPORTED for these bits. */
+#define FPTC_STAGE_LOSSLESS 4u
+#define FPTC_STAGE_LOSSY 8u
 fptc_status fptc_decode_stages(fptc_plan *plan, const uint64_t *d_words, const uint8_t *d_symlen, float *d_out,
                                uint8_t *d_levels, const float *d_scale, uint32_t stages, fptc_stream stream);
 
@@ -261,16 +270,20 @@ fptc_status fptc_plan_autotune(fptc_plan *plan, const uint64_t *d_words, const u
  * d_out[0 .. n_samples).  All working memory (domain tables, records, index
  * scratch, status word) is one file-scope device array of about 2 MB that
  * every device which loads the library keeps until exit; nothing is allocated
- * and no library routine that allocates is called.
+ * and no library routine that allocates is called.  The small tables reach
+ * the array as the argument of a set-up kernel launched on `stream` (no
+ * host-to-device copy; no host memory is read after the call returns).
  * Limits: n_samples <= 67,108,864 and domain->lmax <= 12, else
  * FPTC_ERR_UNSUPPORTED with a message.  Device-side stream errors are not
  * reported by this call (decode with a plan for that).
- * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) on the current device: make that first call before
- * any stream capture.  Every call shares the array, so calls whose work
- * overlaps on the GPU (different streams, or other host threads) race; serialize
- * them.  Asynchronous on `stream` (host-to-device copies of the small tables
- * from host memory are staged before the call returns). */
+ * Every call looks up the array's device address on the current device
+ * (cudaGetSymbolAddress).  The first call on a device also loads this
+ * library's device code there (lazy module loading), and that load can
+ * allocate device memory: make one call on each device at start-up, before
+ * the phase that must not allocate and before any stream capture.  Every call
+ * shares the array, so calls whose work overlaps on the GPU (different
+ * streams, or other host threads) race; serialize them.  Asynchronous on
+ * `stream`. */
 fptc_status fptc_decode_stream_noalloc(const fptc_domain *domain, const uint64_t *d_words, const uint8_t *d_symlen,
                                        uint64_t n_words, uint64_t n_samples, float *d_out, fptc_stream stream);
 

@@ -22,6 +22,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <memory>
 #include <vector>
 
 #include "fptc_codec.h"
@@ -473,6 +474,13 @@ void enc_free(fptc_encoder *e) {
   cudaFree(e->d_lev_scratch);
 }
 
+struct EncDeleter {
+  void operator()(fptc_encoder *e) const {
+    enc_free(e);
+    delete e;
+  }
+};
+
 template <typename T>
 cudaError_t enc_upload(T **dst, const T *src, size_t n) {
   cudaError_t e = cudaMalloc(reinterpret_cast<void **>(dst), std::max<size_t>(n, 1) * sizeof(T));
@@ -618,7 +626,11 @@ fptc_status fptc_encoder_create(fptc_encoder **enc, int device, const fptc_domai
       }
     DevGuard g(device);
     if (!g.ok) return enc_cuda_fail(cudaGetLastError(), "set device");
-    fptc_encoder *e = new fptc_encoder;
+    // the encoder under construction: released into *enc only on success, so
+    // that an error return or an exception frees what it holds (destroyed
+    // before g, with the encoder's device still current)
+    std::unique_ptr<fptc_encoder, EncDeleter> owner(new fptc_encoder);
+    fptc_encoder *const e = owner.get();
     e->device = device;
     e->n_segs = n_segments;
     e->n_windows = win;
@@ -643,12 +655,8 @@ fptc_status fptc_encoder_create(fptc_encoder **enc, int device, const fptc_domai
       const EncStatus s0{0u, 0u, ~0ull};
       err = enc_upload(&e->d_status, &s0, 1);
     }
-    if (err != cudaSuccess) {
-      enc_free(e);
-      delete e;
-      return enc_cuda_fail(err, "encoder upload");
-    }
-    *enc = e;
+    if (err != cudaSuccess) return enc_cuda_fail(err, "encoder upload");
+    *enc = owner.release();
     return FPTC_OK;
   });
 }
@@ -657,8 +665,7 @@ void fptc_encoder_destroy(fptc_encoder *enc) {
   if (!enc) return;
   DevGuard g(enc->device);
   cudaDeviceSynchronize();
-  enc_free(enc);
-  delete enc;
+  EncDeleter()(enc);
 }
 
 uint64_t fptc_encoder_levels(const fptc_encoder *enc) { return enc ? enc->n_levels : 0; }

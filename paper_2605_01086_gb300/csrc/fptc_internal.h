@@ -3,6 +3,7 @@
 #pragma once
 
 #include <algorithm>
+#include <cmath>
 #include <cstdint>
 
 #include <cuda.h>
@@ -40,6 +41,19 @@ struct DomainDev {
   uint32_t complete;       // 1 if the code lengths meet Kraft with equality (no invalid prefix)
   float unit[2][256];      // reconstruction at A_z = 1 for zones 0 and 1 (FP64 -> FP32)
 };
+
+// Entry B[k][n] of the inverse-transform basis of Eq. 1 (window size N):
+// 1/2 for k = 0, else cos(pi (2n + 1) k / (2N)), evaluated in FP64 and rounded
+// to FP32.  Host and device code evaluate the same expression.
+__host__ __device__ inline float basis_value(uint32_t N, uint32_t n, uint32_t k) {
+  return k == 0 ? 0.5f
+                : static_cast<float>(cos(3.14159265358979323846 * (2.0 * n + 1.0) * k / (2.0 * N)));
+}
+
+// Host: the per-domain record of the decode kernels from a validated domain
+// (shape, scales, whether the code is complete, reconstruction at A_z = 1 of
+// Sec. 3.2); lut_offset, basis_offset and tile_windows are left 0.
+void fill_domain_dev(const fptc_domain &dm, DomainDev *dd);
 
 // One segment, in tile-queue order (segments sorted by domain).
 struct SegDev {
@@ -144,8 +158,9 @@ cudaError_t launch_index(const IndexParams &p, cudaStream_t stream);
 // per-word symbol offsets (index.cu) and the lossless / lossy kernels (decode_paper.cu) of the
 // three-kernel schedule
 cudaError_t launch_word_offsets(const IndexParams &p, uint32_t *word_off, cudaStream_t stream);
+// halves: bit 0 runs the lossless kernel, bit 1 the lossy kernel.
 cudaError_t launch_three_kernel(const DecodeParams &p, const uint32_t *word_off, uint8_t *levels,
-                                uint64_t chunk_begin, uint64_t chunk_end, cudaStream_t stream);
+                                uint64_t chunk_begin, uint64_t chunk_end, uint32_t halves, cudaStream_t stream);
 // generic kernel (any N, E)
 cudaError_t launch_decode(const DecodeParams &p, int kind, uint32_t threads, uint32_t grid, size_t smem,
                           cudaStream_t stream);

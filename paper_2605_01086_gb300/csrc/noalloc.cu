@@ -11,9 +11,7 @@
 // word) lives in one file-scope device array of fixed size.  The caller still
 // passes the input words/symlen and the output buffer.
 #include <algorithm>
-#include <cmath>
 #include <cstring>
-#include <mutex>
 
 #include "fptc.h"
 #include "fptc_codec.h"
@@ -47,27 +45,48 @@ constexpr size_t kScratchBytes = a256(kOffTiles + kNaTileCap * sizeof(TileRec));
 
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
-// Device address of g_scratch, per device (host code may not use the symbol itself).
-constexpr int kMaxDevices = 64;
-std::mutex g_setup_mu;
-void *g_scratch_ptr[kMaxDevices] = {nullptr};
+// Everything the decode needs besides the caller's buffers, passed by value as
+// the set-up kernel's argument (about 10 KB): no host memory is read once the
+// launch returns, and no host-to-device copy is made.
+struct NaSetup {
+  DevStatus status;                 // cleared status word
+  SegDev seg;
+  DomainDev dom;
+  uint32_t lut_entries;
+  uint16_t lut[1u << kNaMaxLmax];
+};
+static_assert(sizeof(NaSetup) <= 32000, "kernel arguments are limited to 32,764 bytes");
 
-fptc_status scratch_for_current_device(int dev, unsigned char **out) {
-  if (dev < 0 || dev >= kMaxDevices) {
-    set_error("device %d out of range for the allocation-free path", dev);
-    return FPTC_ERR_UNSUPPORTED;
+// Fills the scratch array: status word, segment flag, records, decode table and
+// the E x N inverse-transform basis (the same expression the plan evaluates on
+// the host).  Device code names the array directly.
+__global__ void k_na_setup(const __grid_constant__ NaSetup a) {
+  unsigned char *const scr = g_scratch;
+  if (threadIdx.x == 0) {
+    *reinterpret_cast<DevStatus *>(scr + kOffStatus) = a.status;
+    *reinterpret_cast<uint32_t *>(scr + kOffSegBad) = 0u;
+    *reinterpret_cast<SegDev *>(scr + kOffSeg) = a.seg;
+    *reinterpret_cast<DomainDev *>(scr + kOffDom) = a.dom;
   }
-  std::lock_guard<std::mutex> lk(g_setup_mu);
-  if (!g_scratch_ptr[dev]) {
-    void *ptr = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&ptr, g_scratch);
-    if (e != cudaSuccess || !ptr) {
-      set_error("cudaGetSymbolAddress of the decode scratch failed: %s", cudaGetErrorString(e));
-      return FPTC_ERR_CUDA;
-    }
-    g_scratch_ptr[dev] = ptr;
+  uint16_t *const lut = reinterpret_cast<uint16_t *>(scr + kOffLut);
+  for (uint32_t i = threadIdx.x; i < a.lut_entries; i += blockDim.x) lut[i] = a.lut[i];
+  float *const basis = reinterpret_cast<float *>(scr + kOffBasis);
+  const uint32_t N = a.dom.N, E = a.dom.E;
+  for (uint32_t i = threadIdx.x; i < N * E; i += blockDim.x) basis[i] = basis_value(N, i % N, i / N);
+}
+
+// Device address of g_scratch on the current device.  Host code may not use
+// the symbol itself (it names a host-side stand-in).  Looked up on every call:
+// after the library's device code is loaded this is a table lookup, and a
+// fresh lookup stays right after the context has been reset.
+fptc_status scratch_for_current_device(unsigned char **out) {
+  void *ptr = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&ptr, g_scratch);
+  if (e != cudaSuccess || !ptr) {
+    set_error("cudaGetSymbolAddress of the decode scratch failed: %s", cudaGetErrorString(e));
+    return FPTC_ERR_CUDA;
   }
-  *out = static_cast<unsigned char *>(g_scratch_ptr[dev]);
+  *out = static_cast<unsigned char *>(ptr);
   return FPTC_OK;
 }
 
@@ -111,46 +130,22 @@ extern "C" fptc_status fptc_decode_stream_noalloc(const fptc_domain *domain, con
     return FPTC_ERR_CUDA;
   }
   unsigned char *scr = nullptr;
-  if ((st = scratch_for_current_device(dev, &scr)) != FPTC_OK) return st;
+  if ((st = scratch_for_current_device(&scr)) != FPTC_OK) return st;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
 
-  // ---- host-side records (no heap allocation: fixed-size locals)
-  DomainDev dd;
-  std::memset(&dd, 0, sizeof(dd));
-  dd.N = dm.N;
-  dd.E = dm.E;
-  dd.B1 = dm.B1;
-  dd.B2 = dm.B2;
-  dd.lmax = dm.lmax;
+  // ---- records and tables, built on the host in the set-up kernel's argument
+  // (a stack object: no heap allocation)
+  NaSetup a;
+  std::memset(&a, 0, sizeof(a));
+  a.status = DevStatus{0u, 0u, ~0ull};
+  DomainDev &dd = a.dom;
+  fill_domain_dev(dm, &dd);  // the plan's own per-domain record
   dd.tile_windows = std::max<uint32_t>(1u, kNaTileSamples / dm.N);
   dd.lut_offset = 0;
   dd.basis_offset = 0;
-  for (int z = 0; z < 3; ++z) dd.scale[z] = static_cast<float>(dm.scale[z]);
-  {
-    uint64_t kraft = 0;
-    for (int sy = 0; sy < 256; ++sy)
-      if (dm.code_len[sy]) kraft += uint64_t(1) << (dm.lmax - dm.code_len[sy]);
-    dd.complete = kraft == (uint64_t(1) << dm.lmax);
-  }
-  {
-    const double mu = dm.mu, a = dm.alpha1, span = 1.0 - dm.alpha1;
-    for (int Lv = 0; Lv < 256; ++Lv) {
-      double u0 = 0.0, u1 = 0.0;
-      if (Lv > 128) {
-        u0 = (std::pow(1.0 + mu, (Lv - 128) / 127.0) - 1.0) / mu;
-        u1 = a + (Lv - 129) / 126.0 * span;
-      } else if (Lv < 128) {
-        u0 = -(std::pow(1.0 + mu, (128 - Lv) / 128.0) - 1.0) / mu;
-        u1 = -(a + (127 - Lv) / 127.0 * span);
-      }
-      dd.unit[0][Lv] = static_cast<float>(u0);
-      dd.unit[1][Lv] = static_cast<float>(u1);
-    }
-  }
-  uint16_t lut[1u << kNaMaxLmax];
-  if ((st = fptc_build_decode_table(&dm, lut)) != FPTC_OK) return st;
-  SegDev sg;
-  std::memset(&sg, 0, sizeof(sg));
+  a.lut_entries = 1u << dm.lmax;
+  if ((st = fptc_build_decode_table(&dm, a.lut)) != FPTC_OK) return st;
+  SegDev &sg = a.seg;
   sg.word_offset = 0;
   sg.n_words = n_words;
   sg.n_samples = n_samples;
@@ -168,27 +163,14 @@ extern "C" fptc_status fptc_decode_stream_noalloc(const fptc_domain *domain, con
     set_error("too many tiles for the allocation-free decode");
     return FPTC_ERR_UNSUPPORTED;
   }
-  const DevStatus st0{0u, 0u, ~0ull};
-  const uint32_t zero = 0;
 
-  // ---- upload (copies only; the status word and segment flag start cleared)
-  e = cudaMemcpyAsync(scr + kOffStatus, &st0, sizeof(st0), cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(scr + kOffSegBad, &zero, sizeof(zero), cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(scr + kOffSeg, &sg, sizeof(sg), cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(scr + kOffDom, &dd, sizeof(dd), cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(scr + kOffLut, lut, sizeof(uint16_t) << dm.lmax, cudaMemcpyHostToDevice, s);
-  // Copies from pageable host memory are staged before cudaMemcpyAsync returns,
-  // so the local buffers below may be reused or go out of scope right away.
-  if (e == cudaSuccess) {
-    float basis[128 * 128];
-    for (uint32_t k = 0; k < dm.E; ++k)
-      for (uint32_t n = 0; n < dm.N; ++n)
-        basis[k * dm.N + n] = k == 0 ? 0.5f : static_cast<float>(std::cos(M_PI * (2.0 * n + 1.0) * k / (2.0 * dm.N)));
-    e = cudaMemcpyAsync(scr + kOffBasis, basis, (size_t)dm.E * dm.N * sizeof(float), cudaMemcpyHostToDevice, s);
+  // ---- set-up kernel: the scratch array's records, tables and cleared status
+  {
+    void *args[] = {&a};
+    e = cudaLaunchKernel(reinterpret_cast<const void *>(&k_na_setup), dim3(1), dim3(256), args, 0, s);
   }
   if (e != cudaSuccess) {
-    set_error("allocation-free decode upload: %s", cudaGetErrorString(e));
+    set_error("allocation-free decode set-up launch: %s", cudaGetErrorString(e));
     return FPTC_ERR_CUDA;
   }
 

@@ -7,6 +7,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <memory>
 #include <new>
 #include <numeric>
 #include <string>
@@ -96,6 +97,14 @@ cudaError_t upload(T **dst, const std::vector<T> &src, size_t *bytes) {
   return e;
 }
 
+void free_device(fptc_plan *p);
+
+// Frees a plan and the device memory, streams and events it holds, on its
+// device (a plan that never reached the device holds none).
+struct PlanDeleter {
+  void operator()(fptc_plan *p) const;
+};
+
 void free_device(fptc_plan *p) {
   cudaFree(p->d_domains);
   cudaFree(p->d_segs);
@@ -118,6 +127,17 @@ void free_device(fptc_plan *p) {
   if (p->ev_start) cudaEventDestroy(p->ev_start);
 }
 
+void PlanDeleter::operator()(fptc_plan *p) const {
+  if (!p) return;
+  if (p->d_domains || p->d_segs || p->d_luts || p->d_basis || p->d_chunk_sum || p->d_chunk_off || p->d_seg_bad ||
+      p->d_word_off || p->d_lev_scratch || p->d_tiles || p->d_status || p->up || p->ev_start || p->aux[0] ||
+      p->ev[0] || p->evh[0]) {
+    DeviceGuard g(p->device);
+    free_device(p);
+  }
+  delete p;
+}
+
 // Reconstruction at A_z = 1 (the inverse zone maps of Sec. 3.2), FP64 then FP32.
 void unit_tables(const fptc_domain &d, float unit[2][256]) {
   const double mu = d.mu, a = d.alpha1, span = 1.0 - d.alpha1;
@@ -134,6 +154,25 @@ void unit_tables(const fptc_domain &d, float unit[2][256]) {
     unit[1][L] = static_cast<float>(u1);
   }
 }
+
+}  // namespace
+
+void fptc::fill_domain_dev(const fptc_domain &dm, DomainDev *dd) {
+  std::memset(dd, 0, sizeof(*dd));
+  dd->N = dm.N;
+  dd->E = dm.E;
+  dd->B1 = dm.B1;
+  dd->B2 = dm.B2;
+  dd->lmax = dm.lmax;
+  for (int z = 0; z < 3; ++z) dd->scale[z] = static_cast<float>(dm.scale[z]);
+  uint64_t kraft = 0;
+  for (int sy = 0; sy < 256; ++sy)
+    if (dm.code_len[sy]) kraft += uint64_t(1) << (dm.lmax - dm.code_len[sy]);
+  dd->complete = kraft == (uint64_t(1) << dm.lmax);
+  unit_tables(dm, dd->unit);
+}
+
+namespace {
 
 // Layout of the tile queue for a tile size (target samples per tile).
 void layout_tiles(fptc_plan *p, uint32_t tile_samples) {
@@ -368,7 +407,7 @@ DecodeParams decode_params(const fptc_plan *p, const uint64_t *d_words, const ui
 
 // Index + decode of queue segments [s0, s1) (tiles and chunks of those segments).
 cudaError_t run_range(const fptc_plan *p, const IndexParams &ip0, const DecodeParams &dp0, uint32_t s0, uint32_t s1,
-                      bool index, cudaStream_t st, bool decode = true) {
+                      bool index, cudaStream_t st, bool decode = true, uint32_t halves = 3u) {
   if (s1 <= s0) return cudaSuccess;
   const SegDev &a = p->segs[s0];
   const SegDev &b = p->segs[s1 - 1];
@@ -390,7 +429,7 @@ cudaError_t run_range(const fptc_plan *p, const IndexParams &ip0, const DecodePa
   dp.tile_end = b.tile_base + b.n_tiles;
   if (p->opts.schedule == FPTC_SCHEDULE_THREE_KERNEL)
     return launch_three_kernel(dp, p->d_word_off, dp.levels ? dp.levels : p->d_lev_scratch, a.chunk_base,
-                               b.chunk_base + b.n_chunks, st);
+                               b.chunk_base + b.n_chunks, halves, st);
   const uint64_t tiles = dp.tile_end - dp.tile_begin;
   const uint32_t grid = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(p->grid, tiles));
   if (p->kind == FPTC_KERNEL_BLOCK_TILE) return launch_fixed(dp, p->threads, grid, p->smem, st);
@@ -555,8 +594,11 @@ fptc_status fptc_plan_create(fptc_plan **out, int device, const fptc_domain *dom
       }
     }
 
-    fptc_plan *p = new (std::nothrow) fptc_plan();
-    if (!p) return FPTC_ERR_OUT_OF_MEMORY;
+    // the plan under construction: released into *out only on success, so that
+    // an error return or an exception frees what it holds
+    std::unique_ptr<fptc_plan, PlanDeleter> owner(new (std::nothrow) fptc_plan());
+    if (!owner) return FPTC_ERR_OUT_OF_MEMORY;
+    fptc_plan *const p = owner.get();
     p->device = device;
     p->opts = o;
     p->domains.assign(domains, domains + n_domains);
@@ -568,7 +610,6 @@ fptc_status fptc_plan_create(fptc_plan **out, int device, const fptc_domain *dom
       const fptc_segment &s = segments[i];
       if (s.domain >= n_domains || s.reserved != 0) {
         set_error("segment %llu: domain %u out of range", (unsigned long long)i, s.domain);
-        delete p;
         return FPTC_ERR_INVALID_ARGUMENT;
       }
       const fptc_domain &d = domains[s.domain];
@@ -579,12 +620,10 @@ fptc_status fptc_plan_create(fptc_plan **out, int device, const fptc_domain *dom
       if (s.n_words < min_words || s.n_words > L) {
         set_error("segment %llu: %llu words cannot hold %llu symbols", (unsigned long long)i,
                   (unsigned long long)s.n_words, (unsigned long long)L);
-        delete p;
         return FPTC_ERR_INVALID_ARGUMENT;
       }
       if (s.word_offset + s.n_words < s.word_offset || s.out_offset + s.n_samples < s.out_offset) {
         set_error("segment %llu: offset overflow", (unsigned long long)i);
-        delete p;
         return FPTC_ERR_INVALID_ARGUMENT;
       }
       p->words_extent = std::max(p->words_extent, s.word_offset + s.n_words);
@@ -597,7 +636,6 @@ fptc_status fptc_plan_create(fptc_plan **out, int device, const fptc_domain *dom
     for (size_t i = 1; i < out_ranges.size(); ++i) {
       if (out_ranges[i].first < out_ranges[i - 1].second) {
         set_error("segment output ranges overlap");
-        delete p;
         return FPTC_ERR_INVALID_ARGUMENT;
       }
     }
@@ -611,20 +649,7 @@ fptc_status fptc_plan_create(fptc_plan **out, int device, const fptc_domain *dom
     for (uint32_t d = 0; d < n_domains; ++d) {
       const fptc_domain &dm = domains[d];
       DomainDev &dd = p->dom_dev[d];
-      std::memset(&dd, 0, sizeof(dd));
-      dd.N = dm.N;
-      dd.E = dm.E;
-      dd.B1 = dm.B1;
-      dd.B2 = dm.B2;
-      dd.lmax = dm.lmax;
-      for (int z = 0; z < 3; ++z) dd.scale[z] = static_cast<float>(dm.scale[z]);
-      {
-        uint64_t kraft = 0;
-        for (int sy = 0; sy < 256; ++sy)
-          if (dm.code_len[sy]) kraft += uint64_t(1) << (dm.lmax - dm.code_len[sy]);
-        dd.complete = kraft == (uint64_t(1) << dm.lmax);
-      }
-      unit_tables(dm, dd.unit);
+      fill_domain_dev(dm, &dd);
       max_lmax = std::max(max_lmax, dm.lmax);
       while (luts.size() % 8) luts.push_back(0);  // 16-byte aligned table starts
       dd.lut_offset = (uint32_t)luts.size();
@@ -633,9 +658,7 @@ fptc_status fptc_plan_create(fptc_plan **out, int device, const fptc_domain *dom
       while (basis.size() % 4) basis.push_back(0.f);
       dd.basis_offset = (uint32_t)basis.size();
       for (uint32_t k = 0; k < dm.E; ++k)
-        for (uint32_t n = 0; n < dm.N; ++n)
-          basis.push_back(k == 0 ? 0.5f
-                                 : static_cast<float>(std::cos(M_PI * (2.0 * n + 1.0) * k / (2.0 * dm.N))));
+        for (uint32_t n = 0; n < dm.N; ++n) basis.push_back(basis_value(dm.N, n, k));
       p->basis_cap = std::max(p->basis_cap, dm.N * dm.E);
     }
     p->lut_cap = 1u << max_lmax;
@@ -687,13 +710,11 @@ fptc_status fptc_plan_create(fptc_plan **out, int device, const fptc_domain *dom
       DeviceGuard g(device);
       if (!g.ok) {
         set_error("cannot select device %d", device);
-        delete p;
         return FPTC_ERR_CUDA;
       }
       cudaError_t e = cudaDeviceGetAttribute(&p->sm_count, cudaDevAttrMultiProcessorCount, device);
       if (e != cudaSuccess) {
         st = cuda_fail(e, "device query");
-        delete p;
         return st;
       }
       size_t b = 0;
@@ -737,13 +758,9 @@ fptc_status fptc_plan_create(fptc_plan **out, int device, const fptc_domain *dom
         if (e != cudaSuccess)
           st = cuda_fail(e, "plan streams");
       }
-      if (st != FPTC_OK) {
-        free_device(p);
-        delete p;
-        return st;
-      }
+      if (st != FPTC_OK) return st;
     }
-    *out = p;
+    *out = owner.release();
     return FPTC_OK;
   });
 }
@@ -753,9 +770,8 @@ void fptc_plan_destroy(fptc_plan *p) {
   {
     DeviceGuard g(p->device);
     cudaDeviceSynchronize();
-    free_device(p);
   }
-  delete p;
+  PlanDeleter()(p);
 }
 
 fptc_status fptc_plan_get_info(const fptc_plan *p, fptc_plan_info *info) {
@@ -810,12 +826,19 @@ fptc_status fptc_decode_stages(fptc_plan *p, const uint64_t *d_words, const uint
   clear_error();
   fptc_status st = check_plan(p);
   if (st != FPTC_OK) return st;
-  if (stages & ~(FPTC_STAGE_INDEX | FPTC_STAGE_DECODE)) {
+  if (stages & ~(FPTC_STAGE_INDEX | FPTC_STAGE_DECODE | FPTC_STAGE_LOSSLESS | FPTC_STAGE_LOSSY)) {
     set_error("unknown stage bits 0x%x", stages);
     return FPTC_ERR_INVALID_ARGUMENT;
   }
+  if ((stages & (FPTC_STAGE_LOSSLESS | FPTC_STAGE_LOSSY)) && p->opts.schedule != FPTC_SCHEDULE_THREE_KERNEL) {
+    set_error("the lossless and lossy stages run on their own only in the three-kernel schedule");
+    return FPTC_ERR_UNSUPPORTED;
+  }
   if (p->segs.empty() || !stages) return FPTC_OK;
-  const bool idx = stages & FPTC_STAGE_INDEX, dec = stages & FPTC_STAGE_DECODE;
+  // decode halves of the three-kernel schedule: bit 0 lossless, bit 1 lossy
+  const uint32_t halves = (stages & FPTC_STAGE_DECODE ? 3u : 0u) | (stages & FPTC_STAGE_LOSSLESS ? 1u : 0u) |
+                          (stages & FPTC_STAGE_LOSSY ? 2u : 0u);
+  const bool idx = stages & FPTC_STAGE_INDEX, dec = halves != 0;
   if ((st = check_ptr(d_words, 8, dec && p->words_extent > 0, "d_words")) != FPTC_OK ||
       (st = check_ptr(d_symlen, 1, p->words_extent > 0, "d_symlen")) != FPTC_OK ||
       (st = check_ptr(d_out, 16, dec && p->out_extent > 0, "d_out")) != FPTC_OK ||
@@ -828,7 +851,7 @@ fptc_status fptc_decode_stages(fptc_plan *p, const uint64_t *d_words, const uint
   const DecodeParams dp = decode_params(p, d_words, d_symlen, d_out, d_levels, d_scale);
   cudaError_t e = cudaSuccess;
   if (p->opts.schedule != FPTC_SCHEDULE_PER_SEGMENT) {
-    e = run_range(p, ip, dp, 0, (uint32_t)p->segs.size(), idx, s, dec);
+    e = run_range(p, ip, dp, 0, (uint32_t)p->segs.size(), idx, s, dec, halves);
   } else {
     for (uint32_t i = 0; i < p->segs.size() && e == cudaSuccess; ++i) e = run_range(p, ip, dp, i, i + 1, idx, s, dec);
   }

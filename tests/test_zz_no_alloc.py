@@ -4,8 +4,9 @@ That entry point serves callers that cannot allocate device memory at decode
 time (inside a framework's memory pool or allocator callback, serving paths that
 forbid allocation after start-up): all of its working memory is one file-scope
 device array.  Here it is called through the C ABI and its samples are compared
-with those of the plan entry point (fptc_decode_batch) on the same stream, within
-the FP32 tolerance of the other tests, on two calls in a row; the second stream
+with those of the plan entry point (fptc_decode_batch) on the same stream, and
+with the FP64 oracle's decode, within the FP32 tolerance of the other tests, on
+two calls in a row; the second stream
 is shorter and of another domain, so anything left over from the first call in
 the shared array would show.  This file sorts last so that a run that stops at
 the first failure has run every other test before it.
@@ -76,6 +77,10 @@ def test_noalloc_matches_plan_on_two_calls():
         got = _noalloc(b)
         rel = np.linalg.norm(got - ref) / np.linalg.norm(ref)
         assert rel <= FP32_REL_L2, rel
+        # and against the FP64 oracle's decode of the same stream
+        x64, _ = oracle.decode_stream(b.words, b.symlen, int(b.lengths[0]), b.domains[0])
+        rel64 = np.linalg.norm(got - x64) / np.linalg.norm(x64)
+        assert rel64 <= FP32_REL_L2, rel64
 
 
 def test_noalloc_rejects_oversize():
