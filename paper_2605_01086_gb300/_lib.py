@@ -15,6 +15,7 @@ OK, INVALID_ARGUMENT, UNSUPPORTED, OUT_OF_MEMORY, CUDA_ERROR, CORRUPT_STREAM = r
 FLAG_SYMLEN_RANGE, FLAG_BIT_OVERRUN, FLAG_INVALID_CODE, FLAG_SYMBOL_COUNT, FLAG_TIMEOUT = 1, 2, 4, 8, 16
 ENC_FLAG_NO_CODE, ENC_FLAG_ROOM = 1, 2
 STAGE_INDEX, STAGE_DECODE = 1, 2
+STAGE_LOSSLESS, STAGE_LOSSY = 4, 8  # three-kernel schedule only: the decode stage's two kernels
 IDCT = {"fp32": 0, "tf32": 1, "bf16x3": 2, "tf32x3": 3}
 SCHEDULE = {"persistent": 0, "per_segment": 1, "three_kernel": 2}
 KERNEL = {"auto": 0, "generic": 1, "block_tile": 2, "warp_tile": 3, "tensor": 4}

@@ -110,12 +110,12 @@ __global__ void __launch_bounds__(kLossyThreads) k_lossy(const DecodeParams p, c
 }  // namespace
 
 cudaError_t launch_three_kernel(const DecodeParams &p, const uint32_t *word_off, uint8_t *levels,
-                                uint64_t chunk_begin, uint64_t chunk_end, cudaStream_t stream) {
-  if (chunk_end > chunk_begin) {
+                                uint64_t chunk_begin, uint64_t chunk_end, uint32_t halves, cudaStream_t stream) {
+  if ((halves & 1u) && chunk_end > chunk_begin) {
     if (chunk_end - chunk_begin > 0x7FFFFFFFull) return cudaErrorInvalidConfiguration;
     k_lossless<<<(unsigned)(chunk_end - chunk_begin), kLosslessThreads, 0, stream>>>(p, word_off, levels, chunk_begin);
   }
-  if (p.tile_end > p.tile_begin) {
+  if ((halves & 2u) && p.tile_end > p.tile_begin) {
     if (p.tile_end - p.tile_begin > 0x7FFFFFFFull) return cudaErrorInvalidConfiguration;
     k_lossy<<<(unsigned)(p.tile_end - p.tile_begin), kLossyThreads, 0, stream>>>(p, levels);
   }

@@ -127,7 +127,8 @@ class Plan:
         return out
 
     def decode_stages(self, words, symlen, out, stages: int, levels=None, scale=None, stream=None):
-        """fptc_decode_stages: stages = STAGE_INDEX (1) | STAGE_DECODE (2)."""
+        """fptc_decode_stages: stages = STAGE_INDEX (1) | STAGE_DECODE (2); the three-kernel schedule also
+        takes STAGE_LOSSLESS (4) and STAGE_LOSSY (8), the decode stage's two kernels on their own."""
         self._check_inputs(words, symlen)
         _require(out, torch.float32, self.device, "out", self.info["out_extent"])
         check(lib().fptc_decode_stages(self._h, _dptr(words), _dptr(symlen), _dptr(out), _dptr(levels), _dptr(scale),

@@ -395,3 +395,26 @@ def test_three_kernel_matches_fused():
     _, _, out_p, _ = gpu_decode(paper, b, want_levels=False, out_fill=0.0)
     rel = float(torch.linalg.vector_norm((out_f - out_p).double()) / torch.linalg.vector_norm(out_f.double()))
     assert rel < 1e-6, rel  # both within FP32 rounding of the same sums
+
+
+def test_three_kernel_stages_apart():
+    """The paper's lossless and lossy kernels run on their own (the stage split that
+    the runtime breakdown of Sec. 6 times): index, then lossless, then lossy gives
+    the samples of one whole decode; the fused schedules refuse these stages."""
+    from paper_2605_01086_gb300 import STAGE_DECODE, STAGE_INDEX, STAGE_LOSSLESS, STAGE_LOSSY, FptcError
+    wl = siggen.mixed_10000_logu(n=24, lo=4096, hi=200000)
+    b = encode_workload(wl)
+    paper = make_plan(b, schedule="three_kernel")
+    w, s = paper.to_device(b.words, b.symlen)
+    whole = paper.empty_out().fill_(float("nan"))
+    paper.decode_stages(w, s, whole, STAGE_INDEX | STAGE_DECODE)
+    apart = paper.empty_out().fill_(float("nan"))
+    paper.decode_stages(w, s, apart, STAGE_INDEX)
+    paper.decode_stages(w, s, apart, STAGE_LOSSLESS)
+    paper.decode_stages(w, s, apart, STAGE_LOSSY)
+    torch.cuda.synchronize()
+    assert torch.equal(torch.nan_to_num(whole, 7.0), torch.nan_to_num(apart, 7.0))  # NaN: outside every segment
+    compare_with_oracle(paper, b, apart, None)
+    fused = make_plan(b)
+    with pytest.raises(FptcError):
+        fused.decode_stages(w, s, fused.empty_out(), STAGE_LOSSLESS)
