@@ -40,6 +40,8 @@ L2_BYTES = 129 * 2 ** 20
 
 
 def workload(name: str, rank: int = 0) -> siggen.Workload:
+    """The named workload; rank r > 0 gets a copy of the same shape with other seeds
+    (weak scaling: every rank decodes a batch of its own)."""
     if name == "mixed":
         wl = siggen.mixed_10000_logu()
     elif name == "eeg2048":
@@ -60,6 +62,32 @@ def workload(name: str, rank: int = 0) -> siggen.Workload:
         wl.seeds = np.array([siggen.splitmix64(int(s) + 0x9E3779B97F4A7C15 * rank & (2 ** 64 - 1))
                              for s in wl.seeds], dtype=np.uint64)
     return wl
+
+
+def workload_config(wl: siggen.Workload) -> dict:
+    """The workload as both arms report it (the same keys and values in each)."""
+    n = int(wl.n_samples)
+    return {"workload": wl.name, "n_streams": int(wl.n_streams), "n_samples": n, "out_bytes": 4 * n,
+            "params": PARAMS, "domains": "eeg,seismic,power,met",
+            "l2": (f"no flush: the output alone is {4 * n / 2 ** 30:.1f} GiB >> L2 129 MB" if 4 * n > 8 * L2_BYTES
+                   else f"output {4 * n / 2 ** 20:.0f} MiB, not far above the 129 MB L2: not a roofline size")}
+
+
+def subset_batch(batch, idx):
+    """The streams idx of a batch, words packed again from 0 and outputs packed at 128 bytes."""
+    from paper_2605_01086_gb300 import codec
+    segs = batch.segments[np.asarray(idx, dtype=np.int64)]
+    nw = segs["n_words"].astype(np.uint64)
+    woff = np.zeros(len(segs), np.uint64)
+    if len(segs) > 1:
+        woff[1:] = np.cumsum(nw[:-1])
+    words = np.concatenate([batch.words[int(a):int(a) + int(b)] for a, b in zip(segs["word_offset"], nw)]) \
+        if len(segs) else np.zeros(0, np.uint64)
+    symlen = np.concatenate([batch.symlen[int(a):int(a) + int(b)] for a, b in zip(segs["word_offset"], nw)]) \
+        if len(segs) else np.zeros(0, np.uint8)
+    lengths = segs["n_samples"].astype(np.uint64)
+    out = codec.segments_array(woff, nw, lengths, codec.packed_out_offsets(lengths), segs["domain"])
+    return codec.Batch(words, symlen, out, batch.domains)
 
 
 def train_tables():
@@ -214,27 +242,61 @@ def cpu_sample(batch, target_s: float, seed: int = 0):
     return order[:min(m, len(order))], n_threads
 
 
+def oracle_encode(wl: siggen.Workload, idx, odoms):
+    """Generates the streams idx of a workload and encodes them with the oracle's encoder."""
+    import oracle
+    sub = wl.subset(np.asarray(idx))
+    flat, offs = siggen.signals(sub.domains, sub.seeds, sub.lengths)
+    return oracle.encode_many(flat, offs, sub.lengths, sub.domains, odoms)
+
+
 def run_reference(args):
-    """Reference arm: the FP64 CPU oracle on the host cores, bounded sample per step."""
+    """Reference arm: the FP64 CPU oracle (its own trainer, encoder and decoder;
+    nothing of the library) on the host cores, a bounded random sample of the
+    workload's streams per step."""
+    import oracle
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
     wl = workload(args.workload)
-    doms = train_tables()
-    batch = encode(wl, doms)
-    idx, n_threads = cpu_sample(batch, target_s=args.ref_seconds)
-    samples = int(batch.segments["n_samples"][idx].sum())
+    p = PARAMS
+    odoms = [oracle.trained_domain(d, p["N"], p["E"], p["B1"], p["B2"], p["mu"], p["alpha1"], p["lmax"],
+                                   p["percentile"]) for d in range(4)]
+    n_threads = os.cpu_count() or 1
+    rng = np.random.default_rng(0)
+    order = rng.permutation(wl.n_streams)
+    S = wl.lengths.astype(np.float64)
+    # calibrate the oracle's decode rate on ~1/400 of the samples, then size the sample
+    k = 1
+    while k < len(order) and S[order[:k]].sum() < S.sum() / 400:
+        k += 1
+    cal = oracle_encode(wl, order[:k], odoms)
+    t = time.perf_counter()
+    oracle.decode_many(cal, n_threads=n_threads)
+    rate = S[order[:k]].sum() / max(time.perf_counter() - t, 1e-6)
+    m = int(np.searchsorted(np.cumsum(S[order]), rate * args.ref_seconds)) + 1
+    idx = np.sort(order[:min(m, len(order))])
+    ob = oracle_encode(wl, idx, odoms)
+    samples = int(ob.lengths.sum())
+
+    def step(sel=None):
+        t0 = time.perf_counter()
+        oracle.decode_many(ob, sel, n_threads=n_threads)
+        return time.perf_counter() - t0
+
     for _ in range(args.warmup):
-        oracle_sample_time(batch, idx[: max(1, len(idx) // 8)], n_threads)
-    ts = [oracle_sample_time(batch, idx, n_threads) for _ in range(args.steps)]
+        step(np.arange(max(1, len(idx) // 8)))
+    ts = [step() for _ in range(args.steps)]
     ms = 1000 * statistics.mean(ts)
     value = 4.0 * samples / (ms / 1000) / 1e9
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": wl.name, "n_streams": wl.n_streams, "n_samples": wl.n_samples},
+            "scaling": args.scaling, "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(wl),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": n_threads, "kind": "oracle",
-                             "sample": f"{len(idx)} of {wl.n_streams} streams, {samples} samples per step"},
+                             "sample": f"{len(idx)} random streams of the {wl.n_streams}, {samples} samples per "
+                                       "step, encoded by the oracle's own encoder with its own trained tables; "
+                                       "FP64 bit-serial decode, OpenMP over streams"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -253,7 +315,7 @@ def time_steps(fn, steps, stream, torch):
 def run(args):
     import torch
 
-    from paper_2605_01086_gb300 import STAGE_DECODE, STAGE_INDEX, Plan
+    from paper_2605_01086_gb300 import STAGE_DECODE, STAGE_INDEX, STAGE_LOSSLESS, STAGE_LOSSY, Plan
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -268,13 +330,25 @@ def run(args):
         dist.init_process_group("nccl", device_id=dev)
 
     t_setup = time.perf_counter()
-    wl = workload(args.workload, rank)
+    # weak scaling: every rank decodes a batch of the workload's shape of its own;
+    # strong scaling: the one batch, cut by LPT on each stream's bytes (4 S + 9 n_words)
+    wl = workload(args.workload, rank if args.scaling == "weak" else 0)
     doms = train_tables()
     batch = encode(wl, doms)
+    mine = np.arange(wl.n_streams)  # workload index of each stream of this rank's batch
+    if world > 1 and args.scaling == "strong":
+        from paper_2605_01086_gb300.shard import decode_cost, shard_streams
+        mine = shard_streams(decode_cost(batch.segments["n_samples"], batch.segments["n_words"]), world, rank)
+        batch = subset_batch(batch, mine)
     t_encode = time.perf_counter() - t_setup
     n_samples = batch.n_samples
     out_bytes = 4 * n_samples
     in_bytes = 9 * int(batch.segments["n_words"].sum())
+    job_out_bytes = out_bytes  # summed over ranks below
+    if dist:
+        t = torch.tensor([float(out_bytes)], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        job_out_bytes = int(t.item())
 
     t0 = time.perf_counter()
     plan = Plan(doms, batch.segments, device=local, kernel=args.kernel or "auto", threads=args.threads,
@@ -340,15 +414,17 @@ def run(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_ms = float(t.item())
     ms_per_step = total_ms / args.steps
-    value = world * out_bytes / (ms_per_step / 1e3) / 1e9
+    value = job_out_bytes / (ms_per_step / 1e3) / 1e9
+    rank_value = out_bytes / (ms_per_step / 1e3) / 1e9  # this rank's own batch
     if plan.device_status()[0] != 0:
         raise SystemExit("device reported a corrupt stream")
 
     # accuracy: PRD of a few streams against their original signals
-    idx = np.random.default_rng(1).choice(wl.n_streams, size=min(8, wl.n_streams), replace=False)
+    idx = np.random.default_rng(1).choice(len(mine), size=min(8, len(mine)), replace=False)
     num = den = 0.0
     for i in idx:
-        x = siggen.signal(int(wl.domains[i]), int(wl.seeds[i]), int(wl.lengths[i])).astype(np.float64)
+        j = int(mine[i])
+        x = siggen.signal(int(wl.domains[j]), int(wl.seeds[j]), int(wl.lengths[j])).astype(np.float64)
         xh = plan.segment_view(out, int(i)).double().cpu().numpy()
         num += float(np.sum((x - xh) ** 2))
         den += float(np.sum(x ** 2))
@@ -367,15 +443,15 @@ def run(args):
                 "index_ms": statistics.mean(idx_ms), "nominal_frac": achieved / 7900.0}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": args.scaling,
             "vs_baseline": None, "dtype": "f32" if args.idct == "fp32" else "f32 (%s products)" % args.idct,
             "data": "synthetic",
-            "config": {"workload": wl.name, "n_streams": wl.n_streams, "n_samples": n_samples,
-                       "out_bytes": out_bytes, "compressed_bytes": in_bytes, "params": PARAMS,
-                       "domains": "eeg,seismic,power,met", "schedule": "persistent, CUDA graph",
-                       "tuning": tuned, "l2": "no flush: inputs + outputs "
-                       f"{(out_bytes + in_bytes) / 2 ** 30:.1f} GiB >> L2 129 MB",
-                       "setup_s": {"generate_encode": round(t_encode, 1), "plan": round(t_plan, 3)}},
+            "config": workload_config(wl),
+            "run": {"streams_on_rank0": int(len(mine)), "samples_on_rank0": int(n_samples),
+                    "compressed_bytes_rank0": in_bytes, "schedule": "persistent, CUDA graph", "tuning": tuned,
+                    "sharding": ("LPT on 4 S + 9 n_words of the one batch" if args.scaling == "strong" and world > 1
+                                 else "one batch of the workload's shape per rank" if world > 1 else "one GPU"),
+                    "setup_s": {"generate_encode": round(t_encode, 1), "plan": round(t_plan, 3)}},
             "trials_ms": {"median": statistics.median(trials), "mean": statistics.mean(trials), "min": min(trials),
                           "max": max(trials), "n": len(trials)},
             "roofline": roofline, "gpu_launches": args.steps * plan.launches_per_decode, "clocks": clk,
@@ -483,13 +559,20 @@ def run(args):
             tms = time_steps(lambda: tplan.decode(w, s, out=out4, stream=stream), 3, stream, torch)
             tix = time_steps(lambda: tplan.decode_stages(w, s, out4, STAGE_INDEX, stream=stream), 3, stream, torch)
             tdc = time_steps(lambda: tplan.decode_stages(w, s, out4, STAGE_DECODE, stream=stream), 3, stream, torch)
+            # the paper's runtime breakdown (Sec. 6, Fig. 13): its lossless and lossy kernels timed apart
+            tll = time_steps(lambda: tplan.decode_stages(w, s, out4, STAGE_LOSSLESS, stream=stream), 3, stream, torch)
+            tly = time_steps(lambda: tplan.decode_stages(w, s, out4, STAGE_LOSSY, stream=stream), 3, stream, torch)
         torch.cuda.synchronize()
         rel = float(torch.linalg.vector_norm((out4 - out).double()) / torch.linalg.vector_norm(out.double()))
         tv = out_bytes / (statistics.median(tms) / 1e3) / 1e9
+        ll, ly, ix = statistics.median(tll), statistics.median(tly), statistics.median(tix)
         line["three_kernel"] = {"value": tv, "unit": UNIT, "ms_per_step": statistics.median(tms),
-                                "index_ms": statistics.median(tix), "decode_ms": statistics.median(tdc),
+                                "index_ms": ix, "decode_ms": statistics.median(tdc),
+                                "lossless_ms": ll, "lossy_ms": ly,
+                                "share": {"index": ix / (ix + ll + ly), "lossless": ll / (ix + ll + ly),
+                                          "lossy": ly / (ix + ll + ly)},
                                 "launches_per_step": tplan.launches_per_decode, "rel_l2_vs_fused": rel,
-                                "fused_over_three_kernel": value / world / tv}
+                                "fused_over_three_kernel": rank_value / tv}
         tplan.close()
         del out4
 
@@ -505,7 +588,7 @@ def run(args):
         pv = out_bytes / (statistics.mean(pms) / 1e3) / 1e9
         line["plain"] = {"value": pv, "unit": UNIT, "ms_per_step": statistics.mean(pms),
                          "launches_per_step": pplan.launches_per_decode, "identical_output": same,
-                         "batched_over_plain": value / world / pv}
+                         "batched_over_plain": rank_value / pv}
         pplan.close()
         del out2
 
@@ -527,7 +610,7 @@ def run(args):
             tt = torch.tensor([e_s], device=dev, dtype=torch.float64)
             dist.all_reduce(tt, op=dist.ReduceOp.MAX)
             e_s = float(tt.item())
-        line["e2e"] = {"value": world * out_bytes / e_s / 1e9, "unit": UNIT, "h2d_bytes_per_step": in_bytes,
+        line["e2e"] = {"value": job_out_bytes / e_s / 1e9, "unit": UNIT, "h2d_bytes_per_step": in_bytes,
                        "d2h_bytes_per_step": 4 * plan.info["out_extent"], "steps": args.e2e_steps,
                        "api": "fptc_decode_host (pinned host buffers)"}
         del h_w, h_s, h_o
@@ -603,6 +686,9 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="fptc", choices=["fptc", "reference"])
+    ap.add_argument("--scaling", default="weak", choices=["weak", "strong"],
+                    help="N > 1: a batch of the workload's shape per rank (weak), or the one batch cut across "
+                         "ranks by LPT on each stream's bytes (strong)")
     ap.add_argument("--workload", default="mixed")
     ap.add_argument("--traffic", type=float, default=None, help="ncu DRAM bytes per decode launch, if measured")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)

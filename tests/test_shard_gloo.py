@@ -19,7 +19,7 @@ import siggen
 torch = pytest.importorskip("torch")
 mp = pytest.importorskip("torch.multiprocessing")
 
-from paper_2605_01086_gb300.shard import shard_assignment, shard_streams  # noqa: E402
+from paper_2605_01086_gb300.shard import decode_cost, shard_assignment, shard_streams  # noqa: E402
 
 N_STREAMS = 9
 
@@ -45,6 +45,15 @@ def _streams():
     return wl, doms, items
 
 
+def _costs(wl, doms, items):
+    """Decode cost of every stream from its length and its encoded word count."""
+    nw = []
+    for i in range(wl.n_streams):
+        x = siggen.signal(int(wl.domains[i]), int(wl.seeds[i]), int(wl.lengths[i]))
+        nw.append(oracle.encode_stream(x, doms[int(wl.domains[i])])[0].size)
+    return decode_cost(wl.lengths, np.array(nw))
+
+
 def _grad_of(idx, doms, items):
     gA = np.zeros((4, 3), np.float64)
     for i in idx:
@@ -62,7 +71,7 @@ def _worker(rank, world, port, q):
     dist.init_process_group("gloo", rank=rank, world_size=world)
     try:
         wl, doms, items = _streams()
-        mine = shard_streams(wl.lengths, world, rank)
+        mine = shard_streams(_costs(wl, doms, items), world, rank)
         every = [None] * world
         dist.all_gather_object(every, [int(i) for i in mine])
         g = torch.from_numpy(_grad_of(mine, doms, items))
@@ -122,3 +131,18 @@ def test_partition_edge_cases():
         shard_assignment([1, -1], 2)
     with pytest.raises(ValueError):
         shard_assignment([1], 0)
+
+
+def test_decode_cost_is_bytes_moved():
+    # 4 bytes per float32 sample written, 9 bytes per SymLen word read (8 + 1)
+    np.testing.assert_array_equal(decode_cost([0, 1, 1000], [0, 1, 70]), [0, 13, 4630])
+    with pytest.raises(ValueError):
+        decode_cost([1, 2], [1])
+    # a stream that compresses worse costs more than one of the same length
+    c = decode_cost([4096, 4096], [200, 900])
+    assert c[1] > c[0]
+    # the partition balances bytes, not samples: two equal-length streams with
+    # very different word counts and two short ones
+    costs = decode_cost([1000, 1000, 10, 10], [10, 400, 1, 1])
+    loads, parts = shard_assignment(costs, 2)
+    assert sorted(loads.tolist()) == sorted([int(costs[1]), int(costs[0] + costs[2] + costs[3])])
