@@ -111,3 +111,18 @@ def crafted_batch(domains, levels_list, lengths, dom_idx):
         off[1:] = np.cumsum(nw[:-1])
     return oracle.EncodedBatch(np.concatenate(words), np.concatenate(symlen), off, nw,
                                np.array(lengths, np.uint64), np.array(dom_idx, np.int32), list(domains))
+
+
+def near_level_boundary(d: oracle.Domain, x_win, k: int, level: int) -> bool:
+    """True if `level` is what the zone quantizer (Eq. 2, Eq. 3) gives for some
+    coefficient within the FP64 rounding bound of the oracle's Eq. 1 coefficient
+    of bin k of the window x_win, and another level is too: i.e. that coefficient
+    sits on a level boundary.  Two FP64 evaluations of the same N-term sum (with
+    cosine arguments written in two algebraically equal ways) differ by a few
+    ulp per term, so delta = 2 N ulp of (2/N) sum |x| bounds their distance."""
+    x_win = np.asarray(x_win, dtype=np.float64)
+    c = float(oracle.dct2(x_win, d.N, d.E)[k])
+    delta = 2.0 * d.N * 2.0 ** -52 * float(np.abs(x_win).sum()) * 2.0 / d.N
+    z = d.zone(k)
+    lo, hi = oracle.quantize(d, z, c - delta), oracle.quantize(d, z, c + delta)
+    return lo <= level <= hi and lo != hi
