@@ -21,112 +21,17 @@
 // rows, per zone, scales it by 1 / A_z and adds it to an FP64 accumulator; the
 // warp reduces its accumulators (FP64) and adds them to grad_scale with one
 // FP64 atomic per zone whenever its domain changes and at the end.
+#include "dct32.cuh"
 #include "warp_tile.cuh"
 
 namespace fptc {
 namespace {
 
 using namespace wt;
+using namespace dct32;
 
-constexpr uint32_t kWaitLimit = 1u << 26;
 constexpr int kGxTile = kStepWin * kN * 4;  // bytes of one step's gradient rows
 
-// The odd/even cosine groups of the forward transform, read transposed here.
-struct AdjK {
-  float eee[4];     // cos(pi (2n+1) / 8), n < 4                 (bin 8)
-  float eeo[4][2];  // cos(pi (2n+1)(2j+1) / 16)                 (bins 4, 12)
-  float eo[8][4];   // cos(pi (2n+1)(2j+1) / 32)                 (bins 2, 6, 10, 14)
-  float o[16][8];   // cos(pi (2n+1)(2j+1) / 64)                 (odd bins)
-};
-__host__ __device__ constexpr double cos_taylor_b(double x) {
-  double x2 = x * x, term = 1.0, sum = 1.0;
-  for (int i = 1; i < 24; ++i) {
-    term *= -x2 / ((2.0 * i - 1.0) * (2.0 * i));
-    sum += term;
-  }
-  return sum;
-}
-__host__ __device__ constexpr float cospi_b(int num, int den) {
-  int r = num % (2 * den);
-  if (r > den) r = 2 * den - r;
-  const double pi = 3.14159265358979323846;
-  return 2 * r <= den ? (float)cos_taylor_b(pi * r / den) : (float)-cos_taylor_b(pi * (den - r) / den);
-}
-__host__ __device__ constexpr AdjK make_adj_k() {
-  AdjK K{};
-  for (int n = 0; n < 4; ++n) K.eee[n] = cospi_b(2 * n + 1, 8);
-  for (int n = 0; n < 4; ++n)
-    for (int j = 0; j < 2; ++j) K.eeo[n][j] = cospi_b((2 * n + 1) * (2 * j + 1), 16);
-  for (int n = 0; n < 8; ++n)
-    for (int j = 0; j < 4; ++j) K.eo[n][j] = cospi_b((2 * n + 1) * (2 * j + 1), 32);
-  for (int n = 0; n < 16; ++n)
-    for (int j = 0; j < 8; ++j) K.o[n][j] = cospi_b((2 * n + 1) * (2 * j + 1), 64);
-  return K;
-}
-
-// g_C[0..15] of one window from its 32 sample gradients.
-__device__ __forceinline__ void dct2_16(const float (&g)[32], float (&gc)[16]) {
-  constexpr AdjK K = make_adj_k();
-  float u[16], v[16];
-#pragma unroll
-  for (int n = 0; n < 16; ++n) {
-    u[n] = g[n] + g[31 - n];
-    v[n] = g[n] - g[31 - n];
-  }
-#pragma unroll
-  for (int j = 0; j < 8; ++j) {  // odd bins 2j + 1
-    float a = v[0] * K.o[0][j];
-#pragma unroll
-    for (int n = 1; n < 16; ++n) a = fmaf(v[n], K.o[n][j], a);
-    gc[2 * j + 1] = a;
-  }
-  float uu[8], uv[8];
-#pragma unroll
-  for (int n = 0; n < 8; ++n) {
-    uu[n] = u[n] + u[15 - n];
-    uv[n] = u[n] - u[15 - n];
-  }
-#pragma unroll
-  for (int j = 0; j < 4; ++j) {  // bins 4j + 2
-    float a = uv[0] * K.eo[0][j];
-#pragma unroll
-    for (int n = 1; n < 8; ++n) a = fmaf(uv[n], K.eo[n][j], a);
-    gc[4 * j + 2] = a;
-  }
-  float uuu[4], uuv[4];
-#pragma unroll
-  for (int n = 0; n < 4; ++n) {
-    uuu[n] = uu[n] + uu[7 - n];
-    uuv[n] = uu[n] - uu[7 - n];
-  }
-  gc[0] = 0.5f * ((uuu[0] + uuu[1]) + (uuu[2] + uuu[3]));
-  {
-    float a = uuu[0] * K.eee[0];
-#pragma unroll
-    for (int n = 1; n < 4; ++n) a = fmaf(uuu[n], K.eee[n], a);
-    gc[8] = a;
-  }
-#pragma unroll
-  for (int j = 0; j < 2; ++j) {  // bins 4, 12
-    float a = uuv[0] * K.eeo[0][j];
-#pragma unroll
-    for (int n = 1; n < 4; ++n) a = fmaf(uuv[n], K.eeo[n][j], a);
-    gc[8 * j + 4] = a;
-  }
-}
-
-__device__ __forceinline__ void mbar_init(uint32_t addr, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(addr), "r"(count) : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint32_t addr, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(addr), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
 // TMA load of rows [row, row + 32) of the gradient into a shared tile; the
 // mbarrier completes when the bytes have arrived.
 __device__ __forceinline__ void tma_load_rows(const CUtensorMap *map, void *smem_tile, uint32_t mbar, int32_t row) {
@@ -277,14 +182,7 @@ __global__ void __launch_bounds__(WARPS * 32, 1) k_backward_warp(const BackwardP
       issue(sn2);
       float gx[32];
       if (si.tma) {
-        uint32_t it = 0;
-        bool late = false;
-        while (!mbar_try_wait(smem_addr(mbar + si.buf), phase[si.buf])) {
-          if (++it >= kWaitLimit) {
-            late = true;
-            break;
-          }
-        }
+        const bool late = !mbar_wait(smem_addr(mbar + si.buf), phase[si.buf]);
         if (__any_sync(0xffffffffu, late)) {  // the load stays pending: waited for again below
           timeout = true;
           break;
@@ -358,9 +256,7 @@ __global__ void __launch_bounds__(WARPS * 32, 1) k_backward_warp(const BackwardP
   // nothing is pending here (a tile's last step issues no further load).
   for (uint32_t b = 0; b < 2; ++b) {
     if (!(pend & (1u << b))) continue;
-    uint32_t it = 0;
-    while (!mbar_try_wait(smem_addr(mbar + b), phase[b]) && ++it < kWaitLimit) {
-    }
+    mbar_wait(smem_addr(mbar + b), phase[b]);
   }
   flush();
   if (timeout && lane == 0) atomicOr(&p.status->flags, kFlagTimeout);

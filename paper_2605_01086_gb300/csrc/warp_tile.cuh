@@ -49,6 +49,38 @@ __device__ __forceinline__ void tma_store_rows(const CUtensorMap *map, const voi
                : "memory");
   asm volatile("cp.async.bulk.commit_group;" ::: "memory");
 }
+// ---- bounded mbarrier waits ---------------------------------------------------
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void mbar_init(uint32_t addr, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(addr), "r"(count) : "memory");
+}
+// One test of the phase of parity `parity`; the thread may be suspended up to
+// hint_ns until that phase completes (it does not spin meanwhile).
+__device__ __forceinline__ bool mbar_try_wait_for(uint32_t addr, uint32_t parity, uint32_t hint_ns) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(addr), "r"(parity), "r"(hint_ns)
+      : "memory");
+  return ok != 0;
+}
+constexpr uint64_t kWaitNs = 1000000000ull;  // a wait gives up after 1 s of global time
+// Waits for the phase of parity `parity` of the mbarrier at addr, sleeping in
+// try_wait between tests; false if it has not completed after kWaitNs.
+__device__ __forceinline__ bool mbar_wait(uint32_t addr, uint32_t parity) {
+  if (mbar_try_wait_for(addr, parity, 20000u)) return true;
+  const uint64_t t0 = global_ns();
+  do {
+    if (mbar_try_wait_for(addr, parity, 1000000u)) return true;
+  } while (global_ns() - t0 < kWaitNs);
+  return false;
+}
+
 __device__ __forceinline__ void tma_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
 __device__ __forceinline__ void tma_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 __device__ __forceinline__ void fence_async_shared() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }

@@ -3,7 +3,8 @@ FP64 oracle: decoded levels bit-exact in every form; samples within a relative
 L2 bound derived from each form's operand rounding:
   TF32    each operand rounded to 11 significant bits: ~2^-12 per product -> 1e-3
   BF16X3  hi/lo split, the lo*lo product (2^-16 relative) dropped   -> 2e-5
-  TF32X3  big/small split, the small*small product (2^-22) dropped  -> 1e-5 (the FP32 bound)
+  TF32X3  big/small split (big by truncation, small read as TF32: 2^-20), the small*small
+          product (2^-22) dropped                                     -> 1e-5 (the FP32 bound)
 """
 import numpy as np
 import pytest
@@ -27,9 +28,11 @@ def _built():
     build()
 
 
-@pytest.mark.parametrize("threads", [128, 256, 512])
+@pytest.mark.parametrize("threads", [128, 256, 512, 640, 768])
 @pytest.mark.parametrize("mode", ["tf32", "bf16x3", "tf32x3"])
 def test_mixed_batch(mode, threads):
+    if mode == "tf32x3" and threads == 768:
+        pytest.skip("six warpgroups of TF32x3 operands need more than the 512 tensor-memory columns")
     wl = siggen.mixed_10000_logu(n=40, lo=1, hi=150000)
     b = encode_workload(wl)
     plan = make_plan(b, idct=mode, threads=threads)
@@ -40,8 +43,9 @@ def test_mixed_batch(mode, threads):
     print(mode, threads, "worst rel L2", worst)
 
 
+@pytest.mark.parametrize("threads", [256, 512])
 @pytest.mark.parametrize("mode", ["bf16x3", "tf32x3"])
-def test_edges_misaligned_and_levels(mode):
+def test_edges_misaligned_and_levels(mode, threads):
     lengths = [0, 1, 5, 31, 32, 33, 1023, 1024, 1025, 4097, 131073, 7]
     n = len(lengths)
     wl = siggen.Workload("edges", 9, np.array([i % 4 for i in range(n)], np.int32),
@@ -49,7 +53,7 @@ def test_edges_misaligned_and_levels(mode):
                          np.array(lengths, np.uint64))
     b = encode_workload(wl)
     for align, base in ((4, 0), (1, 3)):
-        plan = make_plan(b, idct=mode, out_align=align, out_base=base)
+        plan = make_plan(b, idct=mode, out_align=align, out_base=base, threads=threads)
         _, _, out, lv = gpu_decode(plan, b, out_fill=float("nan"))
         compare_with_oracle(plan, b, out, lv, tol=TOL[mode])
         h = out.cpu().numpy()
@@ -59,13 +63,14 @@ def test_edges_misaligned_and_levels(mode):
         assert np.all(np.isnan(h[mask]))
 
 
-def test_corrupt_segment_flagged():
+@pytest.mark.parametrize("threads", [256, 512])
+def test_corrupt_segment_flagged(threads):
     from paper_2605_01086_gb300 import _lib
     wl = siggen.mixed_10000_logu(n=6, lo=5000, hi=20000)
     b = encode_workload(wl)
     bad_word = int(b.word_off[2]) + 5
     b.symlen[bad_word] -= 1
-    plan = make_plan(b, idct="tf32x3")
+    plan = make_plan(b, idct="tf32x3", threads=threads)
     w, s = plan.to_device(b.words, b.symlen)
     out = plan.empty_out().fill_(float("nan"))
     plan.decode(w, s, out=out)
