@@ -1,30 +1,41 @@
 // The FPTC encoder on the GPU (include/fptc_encoder.h): Eq. 1, the three-zone
 // quantizer of Sec. 3.2 and the SymLen packing of Alg. 1 for many streams.
 //
-//   k_enc_levels  one thread per (window, bin): the DCT-II bin of the
-//                 zero-padded window as a compensated FP32 dot product with a
-//                 bound on its error, and the zone quantizer.  Every zone map
-//                 is monotone in the coefficient, so when the levels at c - err
-//                 and c + err agree
-//                 the FP64 coefficient (which lies between) has that level too;
-//                 otherwise the bin goes to a list that k_enc_fallback computes
-//                 again in FP64 (products and sums rounded separately, in
-//                 sample order, then scaled by 2/N, as the host encoder does),
-//                 one bin per lane, and quantizes from that.
-//   k_enc_scan    one thread per stream: Alg. 1's state (word, bits used,
-//                 codewords in the word) over the code lengths alone, recorded
-//                 at every block of kPackBlock symbols; zeroes the words two
+//   k_enc_levels_w32  (every domain N = 32, E = 16) one thread per window: the
+//                 window's 16 bins of Eq. 1 by the even/odd butterfly in FP32
+//                 (dct32.cuh) with a bound on its error, and the zone
+//                 quantizer bracketed by that bound.
+//   k_enc_levels  (other shapes) one thread per (window, bin): the bin as a
+//                 compensated FP32 dot product with a bound on its error.
+//                 In both, every zone map is monotone in the coefficient, so
+//                 when the levels at c - err and c + err agree the FP64
+//                 coefficient (which lies between) has that level too;
+//                 otherwise the bin goes to a list that k_enc_fallback
+//                 computes again in FP64 (products and sums rounded
+//                 separately, in sample order, then scaled by 2/N, as the host
+//                 encoder does), one bin per lane, and quantizes from that.
+//   k_enc_ref     one thread per packing block of kPackBlock symbols: Alg. 1
+//                 on the block alone, entered with a word that starts at its
+//                 first symbol (the reference packing): where its words start
+//                 (a bitmap) and the state it ends in.
+//   k_enc_chain   one warp per stream: block after block, Alg. 1 from the
+//                 true state until a word starts where the reference's does
+//                 (from there on the two coincide: the rest comes from the
+//                 reference); each block's entry state; zeroes the words two
 //                 blocks share; the stream's word count, room and code checks.
-//   k_enc_pack    one thread per block: Alg. 1 from the recorded state, whole
-//                 words with plain stores, the words shared with the previous
-//                 or next block with 64-bit atomicOr (their codeword bits are
-//                 disjoint), each word's symbol count by the block that closes it.
+//   k_enc_pack    one thread per block: Alg. 1 from the block's entry state,
+//                 whole words with plain stores, the words shared with the
+//                 previous or next block with 64-bit atomicOr (their codeword
+//                 bits are disjoint), each word's symbol count by the block
+//                 that closes it.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <memory>
 #include <vector>
 
+#include "dct32.cuh"
+#include "device_util.cuh"
 #include "fptc_codec.h"
 #include "fptc_encoder.h"
 #include "fptc_internal.h"
@@ -44,6 +55,7 @@ struct EncDomain {
   float A0f, A1f, muf, d1f, inv_A0f, inv_span1f, inv_log1pmuf;
   double d1;             // alpha1 A1 as the FP64 quantizer computes it
   float slack0, slack1;  // per zone: an input width that covers the FP32 evaluation error
+  uint32_t on0, on1;     // A0 > 1e-30, A1 > 1e-30 (as the FP64 quantizer tests them): the zone is in use
 };
 
 struct EncSeg {
@@ -71,6 +83,13 @@ struct EncStatus {
   unsigned long long first_bad;
 };
 
+struct RefEnd {
+  uint32_t words;  // words the reference packing closes in the block (its last word stays open)
+  uint32_t bits;   // bits used in that open word
+  uint32_t count;  // its codewords
+  uint32_t bad;    // a level of the block has no codeword
+};
+
 struct EncParams {
   const float *x;
   uint64_t *words;
@@ -84,6 +103,8 @@ struct EncParams {
   const uint32_t *codes;
   const uint8_t *lens;
   PackState *blocks;
+  unsigned long long *ref_map;  // per packing block, kPackBlock bits: word starts of its reference packing
+  RefEnd *ref_end;       // per packing block: the reference packing's end state
   uint32_t *seg_bad;
   unsigned long long *fb_list;   // bins whose level the FP64 coefficient decides
   unsigned int *fb_count;
@@ -129,7 +150,7 @@ __device__ __forceinline__ uint32_t bin_level(uint32_t k, double c, const EncDom
 // evaluation by less than the zone's slack in the coefficient (both are close
 // to the exact monotone map), so used only to bracket it.
 __device__ __forceinline__ uint32_t zone0_level32(float c, const EncDomain &d) {
-  if (!(d.A0 > 1e-30) || isnan(c)) return 128u;
+  if (!d.on0 || isnan(c)) return 128u;
   const float a = fminf(fabsf(c), d.A0f);
   const float q = log1pf(d.muf * (a * d.inv_A0f)) * d.inv_log1pmuf;
   const int v = c >= 0.0f ? 128 + (int)floorf(fmaf(127.0f, q, 0.5f)) : 128 - (int)floorf(fmaf(128.0f, q, 0.5f));
@@ -164,6 +185,32 @@ __device__ __forceinline__ bool zone1_decide(float c, double cd, double err_d, f
 }
 
 
+// Zone 1 decided in FP32 alone from c with |c - c64| <= m - slack1 (the first
+// tier of k_enc_levels_w32): the deadzone test against d1 rounded to FP32
+// (|d1f - d1| <= 2^-24 A1, far inside the slack A1 2^-18 that m carries), then
+// the linear map bracketed as in zone1_decide.  Returns false when the bin has
+// to be decided more closely.
+__device__ __forceinline__ bool zone1_decide32(float c, float m, const EncDomain &d, uint32_t &L) {
+  if (!d.on1 || isnan(c)) {
+    L = 128u;
+    return true;
+  }
+  const float a = fabsf(c);
+  if (a + m < d.d1f) {
+    L = 128u;
+    return true;
+  }
+  if (a - m <= d.d1f) return false;  // at the deadzone edge
+  const float k = c > 0.0f ? 126.0f : 127.0f;
+  const float r0 = fmaxf((fminf(a - m, d.A1f) - d.d1f) * d.inv_span1f, 0.0f);
+  const float r1 = fmaxf((fminf(a + m, d.A1f) - d.d1f) * d.inv_span1f, 0.0f);
+  const int v0 = (int)floorf(fmaf(r0, k, 0.5f)), v1 = (int)floorf(fmaf(r1, k, 0.5f));
+  if (v0 != v1) return false;
+  const int v = c > 0.0f ? 129 + v0 : 127 - v0;
+  L = (uint32_t)(v < 0 ? 0 : (v > 255 ? 255 : v));
+  return true;
+}
+
 // Index i of the last entry with base(i) <= g over n ascending entries.
 template <class F>
 __device__ __forceinline__ uint64_t last_leq(uint64_t n, uint64_t g, F base) {
@@ -178,11 +225,10 @@ __device__ __forceinline__ uint64_t last_leq(uint64_t n, uint64_t g, F base) {
   return lo;
 }
 
-// Level of bin g (global level index) from the FP64 coefficient, computed as
-// the host encoder does: products and sums rounded separately, in sample order,
-// then scaled by 2/N.
-__device__ __forceinline__ uint32_t level_fp64(const EncParams &p, uint64_t g) {
-  const uint64_t s = last_leq(p.n_segs, g, [&](uint64_t i) { return p.segs[i].level_offset; });
+// Level of bin g (global level index) of segment s from the FP64 coefficient,
+// computed as the host encoder does: products and sums rounded separately, in
+// sample order, then scaled by 2/N.
+__device__ __forceinline__ uint32_t level_fp64_seg(const EncParams &p, uint64_t g, uint64_t s) {
   const EncSeg sg = p.segs[s];
   const EncDomain d = p.doms[sg.domain];
   const uint64_t local = g - sg.level_offset;
@@ -194,6 +240,23 @@ __device__ __forceinline__ uint32_t level_fp64(const EncParams &p, uint64_t g) {
   double a64 = 0.0;
   for (uint32_t n = 0; n < d.N; ++n) a64 = __dadd_rn(a64, __dmul_rn(n < avail ? (double)src[n] : 0.0, row[n]));
   return bin_level(k, __dmul_rn(a64, 2.0 / (double)d.N), d);
+}
+
+// FP64 list entries: level index (bits 0-39) and segment (bits 40-63).
+__device__ __forceinline__ unsigned long long fb_entry(uint64_t g, uint64_t s) {
+  return (unsigned long long)(g | (s << 40));
+}
+// A slot of the FP64 list for this thread, one atomic per warp (the lanes
+// that call it at the same time share it); ~0u when the list is full.
+__device__ __forceinline__ unsigned int fb_slot(const EncParams &p) {
+  const uint32_t am = __activemask();
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t leader = (uint32_t)(__ffs(am) - 1);
+  unsigned int base = 0;
+  if (lane == leader) base = atomicAdd(p.fb_count, (unsigned int)__popc(am));
+  base = __shfl_sync(am, base, leader);
+  const unsigned int slot = base + (unsigned int)__popc(am & ((1u << lane) - 1u));
+  return slot < p.fb_cap ? slot : ~0u;
 }
 
 // One thread per (window, bin): thread g writes level g of the level buffer
@@ -252,102 +315,366 @@ __global__ void __launch_bounds__(256) k_enc_levels(EncParams p) {
       decided = zone1_decide(c, cd, (double)err * 2.0, m, d, L);
     }
     if (!decided) {
-      const unsigned int slot = atomicAdd(p.fb_count, 1u);
-      if (slot < p.fb_cap) {
-        p.fb_list[slot] = g;
+      const unsigned int slot = fb_slot(p);
+      if (slot != ~0u) {
+        p.fb_list[slot] = fb_entry(g, s);
         return;  // k_enc_fallback writes the level
       }
-      L = level_fp64(p, g);
+      L = level_fp64_seg(p, g, s);
     }
   }
   p.levels[g] = (uint8_t)L;
+}
+
+// One thread per window, for encoders whose every domain has N = 32, E = 16:
+// the window's 16 Eq. 1 bins at once by the even/odd butterfly in FP32
+// (dct32.cuh: |error| <= 2^-19.5 sum |x| before the exact 2/N scale; bin 0
+// scales by 4/N), then the zone quantizer bracketed as in k_enc_levels with
+// err = (4/N) 2^-18 sum |x| (covering the butterfly, the FP64 encoder's own
+// rounding and the FP32 sum of |x|).  Undecided bins go to the FP64 list.
+// Inclusive warp scan.
+__device__ __forceinline__ uint32_t lane_prefix(uint32_t v, uint32_t lane) {
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= (uint32_t)o) v += y;
+  }
+  return v;  // inclusive
+}
+
+constexpr uint32_t kLvThreads = 128;  // threads per CTA of k_enc_levels_w32 (4 warps)
+
+__global__ void __launch_bounds__(kLvThreads) k_enc_levels_w32(EncParams p, uint64_t n_windows) {
+  // second-tier work shared by a warp's lanes: the samples of its windows that
+  // have undecided bins (rows padded to 33 floats: conflict-free), the list of
+  // (window lane, bin), the windows' levels, segments and sample sums
+  __shared__ float xs[kLvThreads / 32][32][33];
+  __shared__ uint16_t work[kLvThreads / 32][512];
+  __shared__ uint32_t lvs[kLvThreads / 32][32][4];
+  __shared__ uint32_t segs_s[kLvThreads / 32][32];
+  __shared__ float s1s[kLvThreads / 32][32];
+  const uint32_t lane = threadIdx.x & 31u, wid = threadIdx.x >> 5;
+  const uint64_t gw = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool valid = gw < n_windows;  // every lane stays for the warp's shuffles
+  const uint64_t g0 = gw * 16u;       // first level of the window (E = 16 everywhere)
+  const uint64_t s =
+      valid ? last_leq(p.n_segs, g0, [&](uint64_t i) { return p.segs[i].level_offset; }) : 0u;
+  const EncSeg sg = p.segs[s];
+  const EncDomain d = p.doms[sg.domain];
+  const uint64_t w = valid ? (g0 - sg.level_offset) >> 4 : 0u;
+  const uint64_t i0 = w * 32u;
+  const uint64_t avail = valid ? sg.n_samples - i0 : 0u;  // >= 1 for a valid window
+  const float *src = p.x + sg.in_offset + i0;
+  float x[32];
+  if (avail >= 32 && (reinterpret_cast<uintptr_t>(src) & 15u) == 0) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const float4 v = __ldg(reinterpret_cast<const float4 *>(src) + j);
+      x[4 * j] = v.x;
+      x[4 * j + 1] = v.y;
+      x[4 * j + 2] = v.z;
+      x[4 * j + 3] = v.w;
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < 32; ++j) x[j] = (uint64_t)j < avail ? __ldg(src + j) : 0.0f;  // zero padding past S
+  }
+  float s1 = 0.0f;
+#pragma unroll
+  for (int j = 0; j < 32; ++j) s1 += fabsf(x[j]);
+  float a[16];
+  dct32::dct2_16(x, a);
+  // |c - c64| <= (4/N) 2^-19.5 sum |x| + the FP64 encoder's and the sum's own roundings
+  const float err = s1 * (4.0f / 32.0f) * 0x1p-18f + 1e-30f;
+  uint32_t lv[4] = {0u, 0u, 0u, 0u};
+  uint32_t undecided = 0;  // bins the butterfly's bound cannot settle
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    const float c = a[k] * (k == 0 ? 4.0f / 32.0f : 2.0f / 32.0f);
+    uint32_t L = 128u;
+    if ((uint32_t)k < d.B2) {
+      const float m = err + ((uint32_t)k < d.B1 ? d.slack0 : d.slack1) + fabsf(c) * 0x1p-21f;
+      bool decided;
+      if ((uint32_t)k < d.B1) {
+        const uint32_t l0 = zone0_level32(c - m, d), l1 = zone0_level32(c + m, d);
+        decided = l0 == l1;
+        L = l0;
+      } else {
+        decided = zone1_decide32(c, m, d, L);
+      }
+      if (!decided) {
+        undecided |= 1u << k;
+        L = 0u;
+      }
+    }
+    lv[k >> 2] |= L << (8 * (k & 3));
+  }
+  if (!valid) undecided = 0u;
+  // second tier, spread over the warp's lanes: each undecided bin again as a
+  // compensated FP32 dot product (|error| <= 2^-34 (2/N) sum |x|, as in
+  // k_enc_levels); what that cannot settle goes to the FP64 list
+  const uint32_t cnt = (uint32_t)__popc(undecided);
+  const uint32_t incl = lane_prefix(cnt, lane);
+  const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+  if (total) {  // the same for the whole warp
+    if (cnt) {
+#pragma unroll
+      for (int n = 0; n < 32; ++n) xs[wid][lane][n] = x[n];
+      segs_s[wid][lane] = (uint32_t)s;
+      s1s[wid][lane] = s1;
+      uint32_t u = undecided, o = incl - cnt;
+      while (u) {
+        work[wid][o++] = (uint16_t)((lane << 4) | (uint32_t)(__ffs(u) - 1));
+        u &= u - 1u;
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) lvs[wid][lane][q] = lv[q];
+    __syncwarp();
+    const uint64_t gw_base = gw - lane;
+    for (uint32_t t = lane; t < total; t += 32) {
+      const uint32_t e = work[wid][t], own = e >> 4, k = e & 15u;
+      const uint64_t so = segs_s[wid][own];
+      const EncDomain od = p.doms[p.segs[so].domain];
+      const float2 *ct = reinterpret_cast<const float2 *>(p.cosf) + od.cos_off + k;
+      const float *xo = xs[wid][own];
+      float hi = 0.0f, lo = 0.0f;
+#pragma unroll 8
+      for (int n = 0; n < 32; ++n) {
+        const float xv = xo[n];
+        const float2 cs = ct[(size_t)n * 16u];
+        const float pr = __fmul_rn(xv, cs.x);
+        const float pe = __fadd_rn(__fmaf_rn(xv, cs.x, -pr), __fmul_rn(xv, cs.y));
+        const float tt = __fadd_rn(hi, pr);
+        const float bp = __fsub_rn(tt, hi);
+        lo = __fadd_rn(lo, __fadd_rn(__fadd_rn(__fsub_rn(hi, __fsub_rn(tt, bp)), __fsub_rn(pr, bp)), pe));
+        hi = tt;
+      }
+      const float c = (hi + lo) * (2.0f / 32.0f);
+      const float err2 = s1s[wid][own] * (2.0f / 32.0f) * 0x1p-34f + 1e-30f;
+      const float m = err2 + (k < od.B1 ? od.slack0 : od.slack1) + fabsf(c) * 0x1p-21f;
+      uint32_t L = 0u;
+      bool decided;
+      if (k < od.B1) {
+        const uint32_t l0 = zone0_level32(c - m, od), l1 = zone0_level32(c + m, od);
+        decided = l0 == l1;
+        L = l0;
+      } else {
+        const double cd = ((double)hi + (double)lo) * (2.0 / 32.0);
+        decided = zone1_decide(c, cd, (double)err2 * 2.0, m, od, L);
+      }
+      const uint64_t g = (gw_base + own) * 16u + k;
+      if (!decided) {
+        const unsigned int slot = fb_slot(p);
+        if (slot != ~0u) {
+          p.fb_list[slot] = fb_entry(g, so);
+          L = 0u;  // k_enc_fallback writes this level after the window's store
+        } else {
+          L = level_fp64_seg(p, g, so);
+        }
+      }
+      reinterpret_cast<uint8_t *>(lvs[wid][own])[k] = (uint8_t)L;
+    }
+    __syncwarp();
+#pragma unroll
+    for (int q = 0; q < 4; ++q) lv[q] = lvs[wid][lane][q];
+  }
+  if (!valid) return;
+  uint8_t *const dst = p.levels + g0;
+  if ((reinterpret_cast<uintptr_t>(dst) & 15u) == 0) {
+    *reinterpret_cast<uint4 *>(dst) = make_uint4(lv[0], lv[1], lv[2], lv[3]);
+  } else {
+#pragma unroll
+    for (int k = 0; k < 16; ++k) dst[k] = (uint8_t)(lv[k >> 2] >> (8 * (k & 3)));
+  }
+}
+
+// ---- SymLen packing (Alg. 1) in parallel over blocks of kPackBlock symbols ----
+// Alg. 1 closes a word when the next codeword does not fit, so where words
+// start inside a block depends only on the state the block is entered with
+// (the bits already used in the open word).  Greedy packings entered with
+// different states soon start a word at the same symbol, and from there on
+// they coincide.  k_enc_ref packs every block on its own, entered with a word
+// that starts at its first symbol, and keeps where its words start (a bitmap)
+// and the state it ends in.  k_enc_chain walks each stream block by block with
+// the true state: it packs only until one of its word starts is one of the
+// reference's, then takes the rest of the block from the reference.
+constexpr uint32_t kRefWords = kPackBlock / 64;  // bitmap words per block
+
+
+__device__ __forceinline__ void load16(const uint8_t *lv, uint64_t i, uint64_t n, const uint8_t *len, uint32_t (&cl)[16]) {
+  if (i + 16 <= n && (reinterpret_cast<uintptr_t>(lv + i) & 15u) == 0) {
+    const uint4 v = *reinterpret_cast<const uint4 *>(lv + i);
+    const uint32_t vw[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int j = 0; j < 16; ++j) cl[j] = __ldg(len + ((vw[j >> 2] >> (8 * (j & 3))) & 0xffu));
+  } else {
+#pragma unroll
+    for (int j = 0; j < 16; ++j) cl[j] = i + j < n ? __ldg(len + lv[i + j]) : 0u;
+  }
+}
+
+// One thread per packing block: the reference packing of the block.
+__global__ void __launch_bounds__(128) k_enc_ref(EncParams p) {
+  const uint64_t b = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= p.n_blocks) return;
+  const uint64_t s = last_leq(p.n_segs, b, [&](uint64_t i) { return p.segs[i].block_base; });
+  const EncSeg sg = p.segs[s];
+  const EncDomain d = p.doms[sg.domain];
+  const uint64_t L = sg.n_windows * d.E;
+  const uint64_t i0 = (b - sg.block_base) * kPackBlock;
+  const uint32_t nb = (uint32_t)(L - i0 < kPackBlock ? L - i0 : kPackBlock);
+  const uint8_t *lv = p.levels + sg.level_offset + i0;
+  const uint8_t *len = p.lens + d.code_off;
+  unsigned long long *const map = p.ref_map + b * kRefWords;
+  uint32_t words = 0, bits = 0, count = 0;
+  bool bad = false;
+  uint64_t cur = 0;  // bitmap word being filled
+  for (uint32_t i = 0; i < nb; i += 16) {
+    uint32_t cl[16];
+    load16(lv, i, nb, len, cl);
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      if (i + j >= nb) break;
+      const uint32_t c = cl[j];
+      bad = bad || c == 0u;
+      if (count == 0 || bits + c > 64) {  // a word starts at symbol i + j
+        if (count) ++words;
+        bits = 0;
+        count = 0;
+        cur |= 1ull << ((i + j) & 63u);
+      }
+      bits += c;
+      ++count;
+    }
+    if (((i + 16) & 63u) == 0 || i + 16 >= nb) {
+      map[i >> 6] = cur;
+      cur = 0;
+    }
+  }
+  for (uint32_t w = (nb + 63) >> 6; w < kRefWords; ++w) map[w] = 0;
+  p.ref_end[b] = RefEnd{words, bits, count, bad ? 1u : 0u};
+}
+
+// One warp per stream: the true packing state block after block, packing each
+// block from its entry state until a word starts where the reference's does;
+// each block's entry state for k_enc_pack; the words two blocks share are
+// zeroed for the blocks' atomicOr; code and room checks; the stream's word
+// count.  The warp takes 32 symbols at a time: a warp scan of their code
+// lengths, then each word break is one ballot (the first symbol whose bits no
+// longer fit the open word), so the walk costs a few instructions per word
+// with no divergence.  Levels arrive 128 per round trip (a 4-byte load per
+// lane), the next 128 in flight.
+
+__global__ void __launch_bounds__(128) k_enc_chain(EncParams p) {
+  const uint64_t s = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint32_t lane = threadIdx.x & 31u;
+  if (s >= p.n_segs) return;  // the whole warp
+  const EncSeg sg = p.segs[s];
+  const EncDomain d = p.doms[sg.domain];
+  const uint64_t L = sg.n_windows * d.E;
+  const uint64_t nblk = (L + kPackBlock - 1) / kPackBlock;
+  const uint8_t *len = p.lens + d.code_off;
+  uint64_t w = 0;  // the open word (words closed so far)
+  uint32_t bits = 0, count = 0;
+  bool bad = false;
+  for (uint64_t jb = 0; jb < nblk; ++jb) {
+    const uint64_t b = sg.block_base + jb;
+    if (lane == 0) {
+      p.blocks[b] = PackState{w, bits, count};
+      if (bits > 0 && w < sg.room) p.words[sg.word_offset + w] = 0;  // shared with the previous block
+    }
+    const RefEnd re = p.ref_end[b];
+    if (re.bad) {
+      bad = true;
+      break;
+    }
+    const uint64_t i0 = jb * kPackBlock;
+    const uint32_t nb = (uint32_t)(L - i0 < kPackBlock ? L - i0 : kPackBlock);
+    const uint8_t *lv = p.levels + sg.level_offset + i0;
+    const unsigned long long *map = p.ref_map + b * kRefWords;
+    int32_t mpos = -1;  // where the packing meets the reference's word starts
+    const bool open_word = count != 0;  // entered with a word open (every block but a stream's first)
+    if (!open_word) {
+      mpos = 0;  // the stream's first symbol starts a word, as the reference's does
+    } else {
+      auto fetch = [&](uint32_t at) -> uint32_t {  // levels at .. at + 127, four per lane
+        const uint32_t o = at + 4 * lane;
+        if (o + 4 <= nb && (reinterpret_cast<uintptr_t>(lv + o) & 3u) == 0) return *reinterpret_cast<const uint32_t *>(lv + o);
+        uint32_t t = 0;
+        for (uint32_t r = 0; r < 4 && o + r < nb; ++r) t |= (uint32_t)lv[o + r] << (8 * r);
+        return t;
+      };
+      uint32_t cur = fetch(0);
+      for (uint32_t at = 0; at < nb && mpos < 0; at += 128) {
+        const uint32_t nxt = at + 128 < nb ? fetch(at + 128) : 0u;
+        const unsigned long long m0 = map[at >> 6], m1 = at + 64 < nb ? map[(at >> 6) + 1] : 0ull;
+#pragma unroll 1
+        for (uint32_t k = 0; k < 4 && mpos < 0; ++k) {
+          const uint32_t c = at + 32 * k;
+          if (c >= nb) break;
+          const uint32_t valid = nb - c < 32 ? nb - c : 32;
+          const uint32_t vw = __shfl_sync(0xffffffffu, cur, 8 * k + (lane >> 2));
+          const uint32_t cl = lane < valid ? __ldg(len + ((vw >> (8 * (lane & 3))) & 0xffu)) : 0u;
+          const uint32_t S = lane_prefix(cl, lane);  // bits of symbols c .. c + lane
+          const unsigned long long mk = (k < 2 ? m0 : m1) >> (32 * (k & 1));  // reference starts of c .. c + 31
+          uint32_t from = 0;  // first symbol of the chunk not yet placed
+          while (from < valid) {
+            const uint32_t pre = from ? __shfl_sync(0xffffffffu, S, from - 1) : 0u;
+            const uint32_t over = __ballot_sync(0xffffffffu, lane >= from && lane < valid && bits + (S - pre) > 64u);
+            if (over == 0) {  // the rest of the chunk fits the open word
+              bits += __shfl_sync(0xffffffffu, S, valid - 1) - pre;
+              count += valid - from;
+              break;
+            }
+            const uint32_t t = (uint32_t)(__ffs(over) - 1);  // a word starts at symbol c + t
+            if ((mk >> t) & 1ull) {
+              mpos = (int32_t)(c + t);
+              break;
+            }
+            ++w;  // the open word closes before symbol c + t
+            bits = 0;
+            count = 0;
+            from = t;
+          }
+        }
+        cur = nxt;
+      }
+    }
+    if (mpos >= 0) {  // from symbol mpos on the block packs as the reference does
+      // the reference's word starts before mpos (a warp popcount over the bitmap)
+      uint32_t r = 0;
+      const uint32_t full = (uint32_t)mpos >> 6;
+      for (uint32_t q = lane; q < full; q += 32) r += __popcll(map[q]);
+      if (lane == 0 && (mpos & 63)) r += __popcll(map[full] & ((1ull << (mpos & 63)) - 1ull));
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+      if (open_word) ++w;  // the word open before symbol mpos (never empty mid-stream) closes there
+      w += re.words - r;  // the reference's words from symbol mpos on, but its open one
+      bits = re.bits;
+      count = re.count;
+    }
+  }
+  if (lane == 0) {
+    if (bad) enc_flag(p.status, FPTC_ENC_FLAG_NO_CODE, s);
+    const uint64_t total = w + (count > 0 ? 1u : 0u);
+    if (!bad && total > sg.room) {
+      enc_flag(p.status, FPTC_ENC_FLAG_ROOM, s);
+      bad = true;
+    }
+    p.seg_bad[s] = bad ? 1u : 0u;
+    p.n_words[s] = bad ? 0u : total;
+  }
 }
 
 // The listed bins, one per thread, from their FP64 coefficients.
 __global__ void __launch_bounds__(256) k_enc_fallback(EncParams p) {
   const unsigned int n = min(*p.fb_count, p.fb_cap);
   for (unsigned int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    const uint64_t g = p.fb_list[i];
-    p.levels[g] = (uint8_t)level_fp64(p, g);
+    const unsigned long long e = p.fb_list[i];
+    const uint64_t g = e & ((1ull << 40) - 1ull);
+    p.levels[g] = (uint8_t)level_fp64_seg(p, g, e >> 40);
   }
-}
-
-// One thread per stream: Alg. 1's state over the code lengths, recorded at the
-// start of every packing block; the words two blocks share are zeroed for the
-// blocks' atomicOr; code and room checks; the stream's word count.
-__global__ void __launch_bounds__(128) k_enc_scan(EncParams p) {
-  const uint64_t s = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= p.n_segs) return;
-  const EncSeg sg = p.segs[s];
-  const EncDomain d = p.doms[sg.domain];
-  const uint8_t *lv = p.levels + sg.level_offset;
-  const uint64_t L = sg.n_windows * d.E;
-  const uint8_t *len = p.lens + d.code_off;
-  PackState *const bs = p.blocks + sg.block_base;
-  uint64_t w = 0;
-  uint32_t bits = 0, count = 0;
-  bool bad = false;
-  // state update for symbol i of code length cl (> 0)
-  auto step = [&](uint64_t i, uint32_t cl) {
-    if ((i & (kPackBlock - 1)) == 0) {
-      bs[i / kPackBlock] = PackState{w, bits, count};
-      if (bits > 0 && w < sg.room) p.words[sg.word_offset + w] = 0;  // shared with the previous block
-    }
-    if (bits + cl > 64) {  // the codeword does not fit: the next word
-      ++w;
-      bits = 0;
-      count = 0;
-    }
-    bits += cl;
-    ++count;
-  };
-  // levels before the first 16-byte boundary one at a time
-  uint64_t i = 0;
-  const uint64_t to16 = (16u - (reinterpret_cast<uintptr_t>(lv) & 15u)) & 15u;
-  const uint64_t head = to16 < L ? to16 : L;
-  for (; i < head && !bad; ++i) {
-    const uint32_t cl = __ldg(len + lv[i]);
-    if (cl == 0)
-      bad = true;
-    else
-      step(i, cl);
-  }
-  // then 16 at a time, the next chunk's load in flight while the current one is walked
-  const uint64_t n16 = bad ? 0 : (L - i) / 16;
-  uint4 nxt = n16 ? *reinterpret_cast<const uint4 *>(lv + i) : make_uint4(0u, 0u, 0u, 0u);
-  for (uint64_t c = 0; c < n16 && !bad; ++c, i += 16) {
-    const uint4 v = nxt;
-    if (c + 1 < n16) nxt = *reinterpret_cast<const uint4 *>(lv + i + 16);
-    const uint32_t vw[4] = {v.x, v.y, v.z, v.w};
-    uint32_t cl[16];
-    bool zero = false;
-#pragma unroll
-    for (int j = 0; j < 16; ++j) {
-      cl[j] = __ldg(len + ((vw[j >> 2] >> (8 * (j & 3))) & 0xffu));
-      zero = zero || cl[j] == 0;
-    }
-    if (zero) {
-      bad = true;
-      break;
-    }
-#pragma unroll
-    for (int j = 0; j < 16; ++j) step(i + j, cl[j]);
-  }
-  for (; i < L && !bad; ++i) {  // the tail
-    const uint32_t cl = __ldg(len + lv[i]);
-    if (cl == 0)
-      bad = true;
-    else
-      step(i, cl);
-  }
-  if (bad) enc_flag(p.status, FPTC_ENC_FLAG_NO_CODE, s);
-  const uint64_t total = w + (count > 0 ? 1u : 0u);
-  if (!bad && total > sg.room) {
-    enc_flag(p.status, FPTC_ENC_FLAG_ROOM, s);
-    bad = true;
-  }
-  p.seg_bad[s] = bad ? 1u : 0u;
-  p.n_words[s] = bad ? 0u : total;
 }
 
 // One thread per packing block: Alg. 1 from the block's recorded state.
@@ -445,6 +772,9 @@ struct fptc_encoder {
   double *d_cos = nullptr;
   float *d_cosf = nullptr;
   PackState *d_blocks = nullptr;
+  unsigned long long *d_ref_map = nullptr;  // [n_blocks][kPackBlock / 64]
+  RefEnd *d_ref_end = nullptr;              // [n_blocks]
+  bool w32 = false;               // every domain N = 32, E = 16: the window-per-thread level kernel
   uint32_t *d_seg_bad = nullptr;
   unsigned long long *d_fb_list = nullptr;
   unsigned int *d_fb_count = nullptr;
@@ -465,6 +795,8 @@ void enc_free(fptc_encoder *e) {
   cudaFree(e->d_cos);
   cudaFree(e->d_cosf);
   cudaFree(e->d_blocks);
+  cudaFree(e->d_ref_map);
+  cudaFree(e->d_ref_end);
   cudaFree(e->d_seg_bad);
   cudaFree(e->d_fb_list);
   cudaFree(e->d_fb_count);
@@ -500,6 +832,8 @@ EncParams enc_params(const fptc_encoder *e, uint64_t *d_words, uint8_t *d_symlen
   p.cosv = e->d_cos;
   p.cosf = e->d_cosf;
   p.blocks = e->d_blocks;
+  p.ref_map = e->d_ref_map;
+  p.ref_end = e->d_ref_end;
   p.seg_bad = e->d_seg_bad;
   p.fb_list = e->d_fb_list;
   p.fb_count = e->d_fb_count;
@@ -565,6 +899,8 @@ fptc_status fptc_encoder_create(fptc_encoder **enc, int device, const fptc_domai
       // mu / log1p(mu) and 1 / (1 - alpha1) per scale)
       x.slack0 = (float)(std::fabs(dm.scale[0]) * 0x1p-18);
       x.slack1 = (float)(std::fabs(dm.scale[1]) * 0x1p-18);
+      x.on0 = dm.scale[0] > 1e-30 ? 1u : 0u;
+      x.on1 = dm.scale[1] > 1e-30 ? 1u : 0u;
       x.cos_off = (uint32_t)cosv.size();
       for (uint32_t k = 0; k < dm.E; ++k)
         for (uint32_t n = 0; n < dm.N; ++n) cosv.push_back(std::cos(M_PI * (2.0 * n + 1.0) * k / (2.0 * dm.N)));
@@ -624,6 +960,10 @@ fptc_status fptc_encoder_create(fptc_encoder **enc, int device, const fptc_domai
         set_error("segment rooms overlap at word %llu", (unsigned long long)rooms[i].first);
         return FPTC_ERR_INVALID_ARGUMENT;
       }
+    if (lv >= (uint64_t(1) << 40) || n_segments >= (uint64_t(1) << 24)) {  // the FP64 list packs both in 64 bits
+      set_error("an encoder takes at most 2^40 levels and 2^24 segments");
+      return FPTC_ERR_UNSUPPORTED;
+    }
     DevGuard g(device);
     if (!g.ok) return enc_cuda_fail(cudaGetLastError(), "set device");
     // the encoder under construction: released into *enc only on success, so
@@ -642,10 +982,16 @@ fptc_status fptc_encoder_create(fptc_encoder **enc, int device, const fptc_domai
     if (err == cudaSuccess) err = enc_upload(&e->d_cos, cosv.data(), cosv.size());
     if (err == cudaSuccess) err = enc_upload(&e->d_cosf, cosf.data(), cosf.size());
     if (err == cudaSuccess) err = cudaMalloc(&e->d_blocks, std::max<uint64_t>(blocks, 1) * sizeof(PackState));
+    if (err == cudaSuccess)
+      err = cudaMalloc(&e->d_ref_map, std::max<uint64_t>(blocks, 1) * kRefWords * sizeof(unsigned long long));
+    if (err == cudaSuccess) err = cudaMalloc(&e->d_ref_end, std::max<uint64_t>(blocks, 1) * sizeof(RefEnd));
+    e->w32 = true;
+    for (uint32_t d = 0; d < n_domains; ++d) e->w32 = e->w32 && domains[d].N == 32 && domains[d].E == 16;
     if (err == cudaSuccess) err = cudaMalloc(&e->d_seg_bad, std::max<uint64_t>(n_segments, 1) * sizeof(uint32_t));
-    // room for the bins decided in FP64 (a few percent of them at most on signals; when it
-    // fills, the level kernel decides the rest itself)
-    e->fb_cap = (uint32_t)std::min<uint64_t>(std::max<uint64_t>(lv / 16, 4096), uint64_t(1) << 24);
+    // room for the bins decided in FP64: 0.2 % of them on signals, a few percent when
+    // decoded signals are encoded again (their levels 127 and 129 reconstruct on the
+    // deadzone edge); when it fills, the level kernels decide the rest themselves
+    e->fb_cap = (uint32_t)std::min<uint64_t>(std::max<uint64_t>(lv / 16, 4096), uint64_t(1) << 28);
     if (err == cudaSuccess) err = cudaMalloc(&e->d_fb_list, (size_t)e->fb_cap * sizeof(unsigned long long));
     if (err == cudaSuccess) err = cudaMalloc(&e->d_fb_count, sizeof(unsigned int));
     if (err == cudaSuccess) err = cudaDeviceGetAttribute(&e->sm_count, cudaDevAttrMultiProcessorCount, device);
@@ -722,7 +1068,11 @@ static fptc_status enc_run(fptc_encoder *enc, const float *d_x, bool levels_give
     const uint64_t blocks = (enc->n_levels + 255) / 256;
     e = cudaMemsetAsync(enc->d_fb_count, 0, sizeof(unsigned int), s);
     if (e == cudaSuccess) {
-      k_enc_levels<<<(unsigned)blocks, 256, 0, s>>>(p);
+      if (enc->w32)
+        k_enc_levels_w32<<<(unsigned)((enc->n_windows + kLvThreads - 1) / kLvThreads), kLvThreads, 0, s>>>(
+            p, enc->n_windows);
+      else
+        k_enc_levels<<<(unsigned)blocks, 256, 0, s>>>(p);
       e = cudaGetLastError();
     }
     if (e == cudaSuccess) {
@@ -730,8 +1080,12 @@ static fptc_status enc_run(fptc_encoder *enc, const float *d_x, bool levels_give
       e = cudaGetLastError();
     }
   }
+  if (e == cudaSuccess && enc->n_blocks) {
+    k_enc_ref<<<(unsigned)((enc->n_blocks + 127) / 128), 128, 0, s>>>(p);
+    e = cudaGetLastError();
+  }
   if (e == cudaSuccess) {
-    k_enc_scan<<<(unsigned)((enc->n_segs + 127) / 128), 128, 0, s>>>(p);
+    k_enc_chain<<<(unsigned)((enc->n_segs * 32 + 127) / 128), 128, 0, s>>>(p);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess && enc->n_blocks) {

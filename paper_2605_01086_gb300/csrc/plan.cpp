@@ -245,7 +245,7 @@ fptc_status configure_launch(fptc_plan *p) {
     e = fixed_occupancy(threads, p->smem, &occ);
   } else if (p->kind == FPTC_KERNEL_TENSOR) {
     if (p->opts.threads == 0) {
-      // as many warpgroups as one CTA's shared memory allows (4 at most)
+      // as many warpgroups as one CTA's shared memory allows (6 at most)
       int dev = 0, optin = 0;
       cudaGetDevice(&dev);
       cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);

@@ -57,7 +57,9 @@ def test_pack_matches_oracle(case):
             lmax, pool = 16, np.arange(128, 256)
         d = oracle.Domain(32, 16, 2, 16, 50.0, 0.004, (1.0, 1.0, 0.0), lmax, cl)
         doms = [d]
-        lens = [0, 5, 3200, 32 * 999 + 7]
+        # 32 * 257 samples: a last packing block of 16 symbols, which (one-bit codes)
+        # may fit the word left open by the block before it
+        lens = [0, 5, 3200, 32 * 999 + 7, 32 * 257, 32 * 256 + 1, 32 * 4096 * 3]
         idx = [0] * len(lens)
         levels = []
         for S in lens:
