@@ -102,8 +102,9 @@ def train_tables():
     return doms
 
 
-def encode(wl: siggen.Workload, doms, chunk_samples: int = 1 << 29):
-    """Generate + encode in chunks of about chunk_samples samples (bounded host memory)."""
+def encode(wl: siggen.Workload, doms, chunk_samples: int = 1 << 29, keep=None):
+    """Generate + encode in chunks of about chunk_samples samples (bounded host memory);
+    keep(first, last, flat, offsets), if given, receives each chunk's signals."""
     from paper_2605_01086_gb300 import codec
     parts = []
     i = 0
@@ -117,6 +118,8 @@ def encode(wl: siggen.Workload, doms, chunk_samples: int = 1 << 29):
         sub = wl.subset(np.arange(i, j))
         flat, offs = siggen.signals(sub.domains, sub.seeds, sub.lengths)
         parts.append(codec.encode_batch(doms, flat, offs, sub.lengths, sub.domains.astype(np.uint32)))
+        if keep is not None:
+            keep(i, j, flat, offs)
         del flat
         i = j
     words = np.concatenate([p.words for p in parts])
@@ -334,7 +337,23 @@ def run(args):
     # strong scaling: the one batch, cut by LPT on each stream's bytes (4 S + 9 n_words)
     wl = workload(args.workload, rank if args.scaling == "weak" else 0)
     doms = train_tables()
-    batch = encode(wl, doms)
+    # the original signals at the decoder's output layout, for the GPU encoder's line
+    x_orig = None
+    keep = None
+    if not args.no_encode and rank == 0 and not (world > 1 and args.scaling == "strong"):
+        from paper_2605_01086_gb300 import codec as _codec
+        x_off = _codec.packed_out_offsets(wl.lengths)
+        x_orig = torch.zeros(int(x_off[-1] + wl.lengths[-1]) if wl.n_streams else 1, dtype=torch.float32,
+                             device=dev)
+
+        def keep(i, j, flat, offs):
+            base = int(x_off[i])
+            span = np.zeros(int(x_off[j - 1] + wl.lengths[j - 1]) - base, np.float32)
+            for t in range(i, j):
+                o, n = int(x_off[t]) - base, int(wl.lengths[t])
+                span[o:o + n] = flat[int(offs[t - i]):int(offs[t - i]) + n]
+            x_orig[base:base + span.size].copy_(torch.from_numpy(span))
+    batch = encode(wl, doms, keep=keep)
     mine = np.arange(wl.n_streams)  # workload index of each stream of this rank's batch
     if world > 1 and args.scaling == "strong":
         from paper_2605_01086_gb300.shard import decode_cost, shard_streams
@@ -519,35 +538,63 @@ def run(args):
                          "kernel": "k_backward_warp (adjoint)"}}
         del lv, gco, sc
 
-    # the GPU encoder (Eq. 1, zone quantizer, Alg. 1) re-encoding the decoded batch in place:
-    # same streams and domains, samples read from the decoder's output layout
-    if not args.no_encode and rank == 0:
+    # the GPU encoder (Eq. 1, zone quantizer, Alg. 1) on the original signals, whose words
+    # must equal the host encoder's (those the decoder read) bit for bit; and on the decoded
+    # batch (re-encoding: every level-127/129 bin then sits on the deadzone edge)
+    if x_orig is not None:
         from paper_2605_01086_gb300 import Encoder
         enc = Encoder(doms, wl.lengths, wl.domains, device=local, in_offsets=batch.segments["out_offset"])
         ew, es, enw = enc.buffers()
         elv = torch.empty(max(1, enc.n_levels), dtype=torch.uint8, device=dev)
+        with torch.cuda.stream(stream):
+            enc.encode(x_orig, ew, es, enw, levels=elv, stream=stream)
+            ems = time_steps(lambda: enc.encode(x_orig, ew, es, enw, levels=elv, stream=stream), 5, stream, torch)
+            pms = time_steps(lambda: enc.pack(elv, ew, es, enw, stream=stream), 5, stream, torch)
+        torch.cuda.synchronize()
+        est = enc.status()[0]
+        # words against the host encoder's: the same counts, then every word and symbol count
+        nw_host = torch.from_numpy(batch.segments["n_words"].astype(np.int64)).to(dev)
+        same_counts = bool(torch.equal(enw[:wl.n_streams], nw_host))
+        same_words = False
+        if same_counts:
+            shift = torch.from_numpy((enc.room_offsets.astype(np.int64) -
+                                      batch.segments["word_offset"].astype(np.int64))).to(dev)
+            idx = torch.repeat_interleave(shift, nw_host) + torch.arange(int(nw_host.sum()), device=dev)
+            same_words = bool(torch.equal(ew[idx], w[:idx.numel()])) and bool(torch.equal(es[idx], s[:idx.numel()]))
+            del idx, shift
+        n_enc_words = int(enw[:wl.n_streams].sum())
+        # algorithmic bytes: samples read (4 B), levels written and read back by the
+        # packing's reference and packing passes (3 x 1 B per level), words and symbol counts written (9 B)
+        n_lev = int(enc.n_levels)
+        enc_bytes = 4 * n_samples + 3 * n_lev + 9 * n_enc_words
+        e_ms = statistics.median(ems)
+        # re-encoding the decoded batch
         lvd = torch.empty_like(elv)  # the original streams' levels, same layout (caller order, packed)
         with torch.cuda.stream(stream):
             plan.decode(w, s, out=out, levels=lvd, stream=stream)
             enc.encode(out, ew, es, enw, levels=elv, stream=stream)
-            ems = time_steps(lambda: enc.encode(out, ew, es, enw, levels=elv, stream=stream), 3, stream, torch)
-            pms = time_steps(lambda: enc.pack(elv, ew, es, enw, stream=stream), 3, stream, torch)
+            rms = time_steps(lambda: enc.encode(out, ew, es, enw, levels=elv, stream=stream), 3, stream, torch)
         torch.cuda.synchronize()
-        est = enc.status()[0]
-        n_enc_words = int(enw[:wl.n_streams].sum())
         same = float((lvd[:enc.n_levels] == elv[:enc.n_levels]).double().mean())
         del lvd
-        line["gpu_encode"] = {"value": 4.0 * n_samples / (statistics.median(ems) / 1e3) / 1e9,
-                              "unit": "GB/s of float32 input", "ms_per_step": statistics.median(ems),
-                              "pack_ms": statistics.median(pms),
-                              "levels_ms": statistics.median(ems) - statistics.median(pms),
+        line["gpu_encode"] = {"value": 4.0 * n_samples / (e_ms / 1e3) / 1e9,
+                              "unit": "GB/s of float32 input", "ms_per_step": e_ms,
+                              "pack_ms": statistics.median(pms), "levels_ms": e_ms - statistics.median(pms),
                               "compressed_bytes": 9 * n_enc_words, "status": est,
-                              "levels_equal_to_decoded_fraction": same,
-                              "input": "the decoded batch (re-encoding)",
-                              "arithmetic": "compensated FP32 transform and FP32 quantizer, FP64 where a bin is near a "
-                                            "level boundary (levels equal to the FP64 encoder's)"}
+                              "input": "the original signals",
+                              "words_equal_to_host_encoder": same_words, "word_counts_equal": same_counts,
+                              "roofline": {"bound": "hbm", "achieved": enc_bytes / (e_ms / 1e3) / 1e9, "peak": peak,
+                                           "unit": "GB/s", "frac": enc_bytes / (e_ms / 1e3) / 1e9 / peak,
+                                           "algorithmic_bytes_per_step": enc_bytes},
+                              "reencode": {"ms_per_step": statistics.median(rms),
+                                           "value": 4.0 * n_samples / (statistics.median(rms) / 1e3) / 1e9,
+                                           "input": "the decoded batch",
+                                           "levels_equal_to_decoded_fraction": same},
+                              "arithmetic": "FP32 butterfly with per-bin error bounds, compensated FP32 where a bin "
+                                            "is near a level boundary, FP64 where that cannot settle it (levels "
+                                            "equal to the FP64 encoder's)"}
         enc.close()
-        del ew, es, enw, elv
+        del ew, es, enw, elv, x_orig
 
     # the paper's three-kernel GPU design on the same streams (global per-word offsets and
     # level array, one thread per output sample), for comparison with the fused kernels

@@ -15,6 +15,7 @@
 // sum_n |x[n]|.
 #pragma once
 
+#include <cmath>
 #include <cstdint>
 
 namespace fptc {
@@ -101,6 +102,85 @@ __device__ __forceinline__ void dct2_16(const float (&g)[32], float (&gc)[16]) {
 #pragma unroll
     for (int n = 1; n < 4; ++n) a = fmaf(uuv[n], K.eeo[n][j], a);
     gc[8 * j + 4] = a;
+  }
+}
+
+
+// dct2_16 with a bound on each output's rounding error from the butterfly's
+// own intermediate sums (u = 2^-24; K rounded to FP32: |K~ - K| <= 2^-25):
+//   odd bins      from v (16-term FMA chains):    18.1 u sum|v|
+//   bins 4j + 2   from uv (8-term chains):        u (9.6 sum|uv| + sum|u|)
+//   bins 4, 12    from uuv (4-term chains):       u (5.6 sum|uuv| + sum|uu| + sum|u|)
+//   bin 8         from uuu (4-term chain):        u (5.6 sum|uuu| + sum|uu| + sum|u|)
+//   bin 0         1/2 of three sums of uuu:       u (1.5 sum|uuu| + sum|uu| + sum|u|) / 2 + ...
+// Each intermediate w = fl(p +- q) carries |w~ - w| <= u |w| plus the errors
+// of p and q; a chain of m fused multiply-adds adds at most 1.01 m u sum |input|
+// and the cosines' rounding 0.5 u sum |input|.  For signals with an offset the
+// DC cancels in v and uv, so these are much tighter than a multiple of
+// sum |x|.  e[k] bounds |a_fp32[k] - a[k]| with 2 % to spare (the sums are
+// themselves rounded).
+__device__ __forceinline__ void dct2_16_bounded(const float (&g)[32], float (&gc)[16], float (&e)[16]) {
+  constexpr AdjK K = make_adj_k();
+  constexpr float u = 0x1p-24f * 1.02f;
+  float uu_[16], v[16];
+  float su = 0.0f, sv = 0.0f;
+#pragma unroll
+  for (int n = 0; n < 16; ++n) {
+    uu_[n] = g[n] + g[31 - n];
+    v[n] = g[n] - g[31 - n];
+    su += fabsf(uu_[n]);
+    sv += fabsf(v[n]);
+  }
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {  // odd bins 2j + 1
+    float a = v[0] * K.o[0][j];
+#pragma unroll
+    for (int n = 1; n < 16; ++n) a = fmaf(v[n], K.o[n][j], a);
+    gc[2 * j + 1] = a;
+    e[2 * j + 1] = 18.1f * u * sv;
+  }
+  float uu[8], uv[8];
+  float suu = 0.0f, suv = 0.0f;
+#pragma unroll
+  for (int n = 0; n < 8; ++n) {
+    uu[n] = uu_[n] + uu_[15 - n];
+    uv[n] = uu_[n] - uu_[15 - n];
+    suu += fabsf(uu[n]);
+    suv += fabsf(uv[n]);
+  }
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {  // bins 4j + 2
+    float a = uv[0] * K.eo[0][j];
+#pragma unroll
+    for (int n = 1; n < 8; ++n) a = fmaf(uv[n], K.eo[n][j], a);
+    gc[4 * j + 2] = a;
+    e[4 * j + 2] = u * (9.6f * suv + su);
+  }
+  float uuu[4], uuv[4];
+  float suuu = 0.0f, suuv = 0.0f;
+#pragma unroll
+  for (int n = 0; n < 4; ++n) {
+    uuu[n] = uu[n] + uu[7 - n];
+    uuv[n] = uu[n] - uu[7 - n];
+    suuu += fabsf(uuu[n]);
+    suuv += fabsf(uuv[n]);
+  }
+  gc[0] = 0.5f * ((uuu[0] + uuu[1]) + (uuu[2] + uuu[3]));
+  e[0] = 0.5f * u * (3.0f * suuu + suu + su);
+  {
+    float a = uuu[0] * K.eee[0];
+#pragma unroll
+    for (int n = 1; n < 4; ++n) a = fmaf(uuu[n], K.eee[n], a);
+    gc[8] = a;
+    e[8] = u * (5.6f * suuu + suu + su);
+  }
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {  // bins 4, 12
+    float a = uuv[0] * K.eeo[0][j];
+#pragma unroll
+    for (int n = 1; n < 4; ++n) a = fmaf(uuv[n], K.eeo[n][j], a);
+    gc[8 * j + 4] = a;
+    e[8 * j + 4] = u * (5.6f * suuv + suu + su);
   }
 }
 

@@ -44,7 +44,7 @@
 namespace fptc {
 namespace {
 
-constexpr uint32_t kPackBlock = 4096;  // symbols per packing block
+constexpr uint32_t kPackBlock = 8192;  // symbols per packing block
 
 struct EncDomain {
   uint32_t N, E, B1, B2;
@@ -56,6 +56,7 @@ struct EncDomain {
   double d1;             // alpha1 A1 as the FP64 quantizer computes it
   float slack0, slack1;  // per zone: an input width that covers the FP32 evaluation error
   uint32_t on0, on1;     // A0 > 1e-30, A1 > 1e-30 (as the FP64 quantizer tests them): the zone is in use
+  float d1_hi, d1_lo;    // d1 as a float pair: d1_hi + d1_lo = d1 to 2^-48 d1
 };
 
 struct EncSeg {
@@ -211,6 +212,40 @@ __device__ __forceinline__ bool zone1_decide32(float c, float m, const EncDomain
   return true;
 }
 
+// Zone 1 decided from a compensated coefficient c = hi + lo (scaled, |hi + lo -
+// c64| <= e) in FP32 alone (the second tier of k_enc_levels_w32): the
+// deadzone test by the sign of |c| - d1 with d1 as a float pair, where
+// |hi| - d1_hi is exact near the edge (Sterbenz) and the rest is rounded once
+// or twice (2^-22 of the difference covers it, 2^-46 d1 the pair's own
+// error); outside the deadzone the linear map bracketed in FP32 with m.
+__device__ __forceinline__ bool zone1_decide_pair(float hi, float lo, float e, float m, const EncDomain &d,
+                                                  uint32_t &L) {
+  const float c = hi + lo;
+  if (!d.on1 || isnan(c)) {
+    L = 128u;
+    return true;
+  }
+  const float sgn = hi < 0.0f ? -1.0f : 1.0f;
+  const float a = fabsf(hi) - d.d1_hi;
+  const float b = sgn * lo - d.d1_lo;
+  const float t = a + b;  // |c| - d1
+  const float margin = e + fabsf(t) * 0x1p-22f + d.d1_hi * 0x1p-46f + 1e-30f;
+  if (t + margin < 0.0f) {
+    L = 128u;
+    return true;
+  }
+  if (t - margin <= 0.0f) return false;  // at the deadzone edge: FP64 decides
+  const float ac = fabsf(c);
+  const float k = c > 0.0f ? 126.0f : 127.0f;
+  const float r0 = fmaxf((fminf(ac - m, d.A1f) - d.d1f) * d.inv_span1f, 0.0f);
+  const float r1 = fmaxf((fminf(ac + m, d.A1f) - d.d1f) * d.inv_span1f, 0.0f);
+  const int v0 = (int)floorf(fmaf(r0, k, 0.5f)), v1 = (int)floorf(fmaf(r1, k, 0.5f));
+  if (v0 != v1) return false;
+  const int v = c > 0.0f ? 129 + v0 : 127 - v0;
+  L = (uint32_t)(v < 0 ? 0 : (v > 255 ? 255 : v));
+  return true;
+}
+
 // Index i of the last entry with base(i) <= g over n ascending entries.
 template <class F>
 __device__ __forceinline__ uint64_t last_leq(uint64_t n, uint64_t g, F base) {
@@ -327,11 +362,46 @@ __global__ void __launch_bounds__(256) k_enc_levels(EncParams p) {
 }
 
 // One thread per window, for encoders whose every domain has N = 32, E = 16:
-// the window's 16 Eq. 1 bins at once by the even/odd butterfly in FP32
-// (dct32.cuh: |error| <= 2^-19.5 sum |x| before the exact 2/N scale; bin 0
-// scales by 4/N), then the zone quantizer bracketed as in k_enc_levels with
-// err = (4/N) 2^-18 sum |x| (covering the butterfly, the FP64 encoder's own
-// rounding and the FP32 sum of |x|).  Undecided bins go to the FP64 list.
+// the window's 16 Eq. 1 bins at once by the even/odd butterfly in FP32, with
+// a bound on each bin's error from the butterfly's own intermediate sums
+// (dct32.cuh dct2_16_bounded; the exact scale 2/N, 4/N for bin 0), plus the
+// FP64 encoder's own rounding; the zone quantizer is bracketed by that bound
+// as in k_enc_levels.  Bins it cannot settle are computed again, spread over
+// the warp's lanes, as compensated dot products; what those cannot settle goes
+// to the FP64 list.
+// First tier of k_enc_levels_w32 for the 16 bins of a window: levels into lv,
+// the bins the bound cannot settle into the mask undecided (their level 0).
+// T1: the zones of Table 1 (B1 = 2, B2 = 16), fixed per bin at compile time.
+template <bool T1>
+__device__ __forceinline__ void tier1_bins(const float (&a)[16], const float (&eb)[16], float err64,
+                                           const EncDomain &d, uint32_t (&lv)[4], uint32_t &undecided) {
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    const float sc = k == 0 ? 4.0f / 32.0f : 2.0f / 32.0f;
+    const float c = a[k] * sc;
+    const bool z2 = T1 ? false : (uint32_t)k >= d.B2;
+    const bool z0 = T1 ? k < 2 : (uint32_t)k < d.B1;
+    uint32_t L = 128u;
+    if (!z2) {
+      const float err = eb[k] * sc + err64;
+      const float m = err + (z0 ? d.slack0 : d.slack1) + fabsf(c) * 0x1p-21f;
+      bool decided;
+      if (z0) {
+        const uint32_t l0 = zone0_level32(c - m, d), l1 = zone0_level32(c + m, d);
+        decided = l0 == l1;
+        L = l0;
+      } else {
+        decided = zone1_decide32(c, m, d, L);
+      }
+      if (!decided) {
+        undecided |= 1u << k;
+        L = 0u;
+      }
+    }
+    lv[k >> 2] |= L << (8 * (k & 3));
+  }
+}
+
 // Inclusive warp scan.
 __device__ __forceinline__ uint32_t lane_prefix(uint32_t v, uint32_t lane) {
 #pragma unroll
@@ -343,8 +413,9 @@ __device__ __forceinline__ uint32_t lane_prefix(uint32_t v, uint32_t lane) {
 }
 
 constexpr uint32_t kLvThreads = 128;  // threads per CTA of k_enc_levels_w32 (4 warps)
+constexpr uint32_t kTier2Inline = 8;  // a warp with more undecided bins settles them itself
 
-__global__ void __launch_bounds__(kLvThreads) k_enc_levels_w32(EncParams p, uint64_t n_windows) {
+__global__ void __launch_bounds__(kLvThreads, 6) k_enc_levels_w32(EncParams p, uint64_t n_windows) {
   // second-tier work shared by a warp's lanes: the samples of its windows that
   // have undecided bins (rows padded to 33 floats: conflict-free), the list of
   // (window lane, bin), the windows' levels, segments and sample sums
@@ -357,8 +428,16 @@ __global__ void __launch_bounds__(kLvThreads) k_enc_levels_w32(EncParams p, uint
   const uint64_t gw = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const bool valid = gw < n_windows;  // every lane stays for the warp's shuffles
   const uint64_t g0 = gw * 16u;       // first level of the window (E = 16 everywhere)
-  const uint64_t s =
-      valid ? last_leq(p.n_segs, g0, [&](uint64_t i) { return p.segs[i].level_offset; }) : 0u;
+  // the segment: one search per CTA (its first window), then a step forward per
+  // window (a CTA's 128 windows span few segments)
+  __shared__ uint32_t s_first;
+  if (threadIdx.x == 0)
+    s_first = (uint32_t)last_leq(p.n_segs, (uint64_t)blockIdx.x * blockDim.x * 16u,
+                                 [&](uint64_t i) { return p.segs[i].level_offset; });
+  __syncthreads();
+  uint64_t s = s_first;
+  if (valid)
+    while (s + 1 < p.n_segs && p.segs[s + 1].level_offset <= g0) ++s;
   const EncSeg sg = p.segs[s];
   const EncDomain d = p.doms[sg.domain];
   const uint64_t w = valid ? (g0 - sg.level_offset) >> 4 : 0u;
@@ -382,33 +461,16 @@ __global__ void __launch_bounds__(kLvThreads) k_enc_levels_w32(EncParams p, uint
   float s1 = 0.0f;
 #pragma unroll
   for (int j = 0; j < 32; ++j) s1 += fabsf(x[j]);
-  float a[16];
-  dct32::dct2_16(x, a);
-  // |c - c64| <= (4/N) 2^-19.5 sum |x| + the FP64 encoder's and the sum's own roundings
-  const float err = s1 * (4.0f / 32.0f) * 0x1p-18f + 1e-30f;
+  float a[16], eb[16];
+  dct32::dct2_16_bounded(x, a, eb);
+  // |c - c64| <= the butterfly's bound for bin k (scaled like c) + the FP64 encoder's own rounding
+  const float err64 = s1 * (2.0f / 32.0f) * 0x1p-40f + 1e-30f;
   uint32_t lv[4] = {0u, 0u, 0u, 0u};
   uint32_t undecided = 0;  // bins the butterfly's bound cannot settle
-#pragma unroll
-  for (int k = 0; k < 16; ++k) {
-    const float c = a[k] * (k == 0 ? 4.0f / 32.0f : 2.0f / 32.0f);
-    uint32_t L = 128u;
-    if ((uint32_t)k < d.B2) {
-      const float m = err + ((uint32_t)k < d.B1 ? d.slack0 : d.slack1) + fabsf(c) * 0x1p-21f;
-      bool decided;
-      if ((uint32_t)k < d.B1) {
-        const uint32_t l0 = zone0_level32(c - m, d), l1 = zone0_level32(c + m, d);
-        decided = l0 == l1;
-        L = l0;
-      } else {
-        decided = zone1_decide32(c, m, d, L);
-      }
-      if (!decided) {
-        undecided |= 1u << k;
-        L = 0u;
-      }
-    }
-    lv[k >> 2] |= L << (8 * (k & 3));
-  }
+  if (d.B1 == 2u && d.B2 == 16u)  // Table 1's zones: the zone of every bin known at compile time
+    tier1_bins<true>(a, eb, err64, d, lv, undecided);
+  else
+    tier1_bins<false>(a, eb, err64, d, lv, undecided);
   if (!valid) undecided = 0u;
   // second tier, spread over the warp's lanes: each undecided bin again as a
   // compensated FP32 dot product (|error| <= 2^-34 (2/N) sum |x|, as in
@@ -416,7 +478,28 @@ __global__ void __launch_bounds__(kLvThreads) k_enc_levels_w32(EncParams p, uint
   const uint32_t cnt = (uint32_t)__popc(undecided);
   const uint32_t incl = lane_prefix(cnt, lane);
   const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
-  if (total) {  // the same for the whole warp
+  if (total && total <= kTier2Inline) {  // a few: k_enc_fallback settles them (compensated, then FP64)
+    uint64_t lo8 = ((uint64_t)lv[1] << 32) | lv[0], hi8 = ((uint64_t)lv[3] << 32) | lv[2];
+    uint32_t u = undecided;
+    while (u) {
+      const uint32_t k = (uint32_t)(__ffs(u) - 1);
+      u &= u - 1u;
+      const unsigned int slot = fb_slot(p);
+      if (slot != ~0u) {
+        p.fb_list[slot] = fb_entry(g0 + k, s);  // its level (0 here) is written after the window's store
+      } else {
+        const uint64_t L = level_fp64_seg(p, g0 + k, s);
+        if (k < 8)
+          lo8 |= L << (8 * k);
+        else
+          hi8 |= L << (8 * (k - 8));
+      }
+    }
+    lv[0] = (uint32_t)lo8;
+    lv[1] = (uint32_t)(lo8 >> 32);
+    lv[2] = (uint32_t)hi8;
+    lv[3] = (uint32_t)(hi8 >> 32);
+  } else if (total) {  // many (re-encoded signals): settled here, spread over the warp's lanes
     if (cnt) {
 #pragma unroll
       for (int n = 0; n < 32; ++n) xs[wid][lane][n] = x[n];
@@ -460,8 +543,7 @@ __global__ void __launch_bounds__(kLvThreads) k_enc_levels_w32(EncParams p, uint
         decided = l0 == l1;
         L = l0;
       } else {
-        const double cd = ((double)hi + (double)lo) * (2.0 / 32.0);
-        decided = zone1_decide(c, cd, (double)err2 * 2.0, m, od, L);
+        decided = zone1_decide_pair(hi * (2.0f / 32.0f), lo * (2.0f / 32.0f), err2 * 2.0f, m, od, L);
       }
       const uint64_t g = (gw_base + own) * 16u + k;
       if (!decided) {
@@ -502,15 +584,18 @@ __global__ void __launch_bounds__(kLvThreads) k_enc_levels_w32(EncParams p, uint
 constexpr uint32_t kRefWords = kPackBlock / 64;  // bitmap words per block
 
 
-__device__ __forceinline__ void load16(const uint8_t *lv, uint64_t i, uint64_t n, const uint8_t *len, uint32_t (&cl)[16]) {
-  if (i + 16 <= n && (reinterpret_cast<uintptr_t>(lv + i) & 15u) == 0) {
-    const uint4 v = *reinterpret_cast<const uint4 *>(lv + i);
-    const uint32_t vw[4] = {v.x, v.y, v.z, v.w};
+// 64 levels from lv + i (zero past n) as four 16-byte vectors.
+__device__ __forceinline__ void load_raw64(const uint8_t *lv, uint64_t i, uint64_t n, uint4 (&v)[4]) {
 #pragma unroll
-    for (int j = 0; j < 16; ++j) cl[j] = __ldg(len + ((vw[j >> 2] >> (8 * (j & 3))) & 0xffu));
-  } else {
-#pragma unroll
-    for (int j = 0; j < 16; ++j) cl[j] = i + j < n ? __ldg(len + lv[i + j]) : 0u;
+  for (int q = 0; q < 4; ++q) {
+    const uint64_t o = i + 16 * q;
+    if (o + 16 <= n && (reinterpret_cast<uintptr_t>(lv + o) & 15u) == 0) {
+      v[q] = *reinterpret_cast<const uint4 *>(lv + o);
+    } else {
+      uint32_t t[4] = {0u, 0u, 0u, 0u};
+      for (uint32_t r = 0; r < 16 && o + r < n; ++r) t[r >> 2] |= (uint32_t)lv[o + r] << (8 * (r & 3));
+      v[q] = make_uint4(t[0], t[1], t[2], t[3]);
+    }
   }
 }
 
@@ -529,28 +614,38 @@ __global__ void __launch_bounds__(128) k_enc_ref(EncParams p) {
   unsigned long long *const map = p.ref_map + b * kRefWords;
   uint32_t words = 0, bits = 0, count = 0;
   bool bad = false;
-  uint64_t cur = 0;  // bitmap word being filled
-  for (uint32_t i = 0; i < nb; i += 16) {
-    uint32_t cl[16];
-    load16(lv, i, nb, len, cl);
+  // 64 levels (one bitmap word) per step, the next 64 in flight
+  uint4 v[4], vn[4];
+  load_raw64(lv, 0, nb, v);
+  for (uint32_t i = 0; i < nb; i += 64) {
+    if (i + 64 < nb) load_raw64(lv, i + 64, nb, vn);
+    uint64_t cur = 0;  // word starts among symbols i .. i + 63
 #pragma unroll
-    for (int j = 0; j < 16; ++j) {
-      if (i + j >= nb) break;
-      const uint32_t c = cl[j];
-      bad = bad || c == 0u;
-      if (count == 0 || bits + c > 64) {  // a word starts at symbol i + j
-        if (count) ++words;
-        bits = 0;
-        count = 0;
-        cur |= 1ull << ((i + j) & 63u);
+    for (int q = 0; q < 4; ++q) {
+      const uint32_t i16 = i + 16 * q;
+      if (i16 >= nb) break;
+      const uint32_t vw[4] = {v[q].x, v[q].y, v[q].z, v[q].w};
+      uint32_t cl[16];
+#pragma unroll
+      for (int j = 0; j < 16; ++j) cl[j] = __ldg(len + ((vw[j >> 2] >> (8 * (j & 3))) & 0xffu));
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        if (i16 + j >= nb) break;
+        const uint32_t c = cl[j];
+        bad = bad || c == 0u;
+        if (count == 0 || bits + c > 64) {  // a word starts at symbol i16 + j
+          if (count) ++words;
+          bits = 0;
+          count = 0;
+          cur |= 1ull << (16 * q + j);
+        }
+        bits += c;
+        ++count;
       }
-      bits += c;
-      ++count;
     }
-    if (((i + 16) & 63u) == 0 || i + 16 >= nb) {
-      map[i >> 6] = cur;
-      cur = 0;
-    }
+    map[i >> 6] = cur;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) v[q] = vn[q];
   }
   for (uint32_t w = (nb + 63) >> 6; w < kRefWords; ++w) map[w] = 0;
   p.ref_end[b] = RefEnd{words, bits, count, bad ? 1u : 0u};
@@ -667,13 +762,57 @@ __global__ void __launch_bounds__(128) k_enc_chain(EncParams p) {
   }
 }
 
-// The listed bins, one per thread, from their FP64 coefficients.
+// Level of listed bin g of segment s from its compensated FP32 coefficient (as
+// in k_enc_levels: |error| <= 2^-34 (2/N) sum |x|); false when that bound
+// cannot settle it.
+__device__ __forceinline__ bool level_compensated(const EncParams &p, uint64_t g, uint64_t s, uint32_t &L) {
+  const EncSeg sg = p.segs[s];
+  const EncDomain d = p.doms[sg.domain];
+  const uint64_t local = g - sg.level_offset;
+  const uint64_t w = local / d.E;
+  const uint32_t k = (uint32_t)(local - w * d.E);
+  const uint64_t avail = sg.n_samples - w * d.N;
+  const uint32_t nn = avail < d.N ? (uint32_t)avail : d.N;
+  const float *src = p.x + sg.in_offset + w * d.N;
+  const float2 *ct = reinterpret_cast<const float2 *>(p.cosf) + d.cos_off + k;
+  float hi = 0.0f, lo = 0.0f, s1 = 0.0f;
+  for (uint32_t n = 0; n < nn; ++n) {
+    const float xv = __ldg(src + n);
+    const float2 cs = ct[(size_t)n * d.E];
+    const float pr = __fmul_rn(xv, cs.x);
+    const float pe = __fadd_rn(__fmaf_rn(xv, cs.x, -pr), __fmul_rn(xv, cs.y));
+    const float t = __fadd_rn(hi, pr);
+    const float bp = __fsub_rn(t, hi);
+    lo = __fadd_rn(lo, __fadd_rn(__fadd_rn(__fsub_rn(hi, __fsub_rn(t, bp)), __fsub_rn(pr, bp)), pe));
+    hi = t;
+    s1 += fabsf(xv);
+  }
+  const float sc = 2.0f / (float)d.N;
+  const float c = (hi + lo) * sc;
+  const float err2 = s1 * sc * 0x1p-34f + 1e-30f;
+  const float m = err2 + (k < d.B1 ? d.slack0 : d.slack1) + fabsf(c) * 0x1p-21f;
+  if (k >= d.B2) {
+    L = 128u;
+    return true;
+  }
+  if (k < d.B1) {
+    const uint32_t l0 = zone0_level32(c - m, d), l1 = zone0_level32(c + m, d);
+    L = l0;
+    return l0 == l1;
+  }
+  return zone1_decide_pair(hi * sc, lo * sc, err2 * 2.0f, m, d, L);
+}
+
+// The listed bins, one per thread: from their compensated FP32 coefficient
+// where its bound settles the level, else from their FP64 coefficient.
 __global__ void __launch_bounds__(256) k_enc_fallback(EncParams p) {
   const unsigned int n = min(*p.fb_count, p.fb_cap);
   for (unsigned int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const unsigned long long e = p.fb_list[i];
-    const uint64_t g = e & ((1ull << 40) - 1ull);
-    p.levels[g] = (uint8_t)level_fp64_seg(p, g, e >> 40);
+    const uint64_t g = e & ((1ull << 40) - 1ull), s = e >> 40;
+    uint32_t L;
+    if (!level_compensated(p, g, s, L)) L = level_fp64_seg(p, g, s);
+    p.levels[g] = (uint8_t)L;
   }
 }
 
@@ -719,17 +858,26 @@ __global__ void __launch_bounds__(128) k_enc_pack(EncParams p) {
     bits += cl;
     ++count;
   };
-  for (uint64_t i = i0; i < i1;) {
-    if ((reinterpret_cast<uintptr_t>(lv + i) & 15u) == 0 && i + 16 <= i1) {  // 16 levels in one load
-      const uint4 v = *reinterpret_cast<const uint4 *>(lv + i);
-      const uint32_t vw[4] = {v.x, v.y, v.z, v.w};
+  // 64 levels per step, the next 64 in flight
+  const uint8_t *const lvb = lv + i0;
+  const uint64_t nbk = i1 - i0;
+  uint4 v[4], vn[4];
+  load_raw64(lvb, 0, nbk, v);
+  for (uint64_t i = 0; i < nbk; i += 64) {
+    if (i + 64 < nbk) load_raw64(lvb, i + 64, nbk, vn);
 #pragma unroll
-      for (int j = 0; j < 16; ++j) step((vw[j >> 2] >> (8 * (j & 3))) & 0xffu);
-      i += 16;
-    } else {
-      step(lv[i]);
-      ++i;
+    for (int q = 0; q < 4; ++q) {
+      const uint64_t i16 = i + 16 * q;
+      if (i16 >= nbk) break;
+      const uint32_t vw[4] = {v[q].x, v[q].y, v[q].z, v[q].w};
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        if (i16 + j >= nbk) break;
+        step((vw[j >> 2] >> (8 * (j & 3))) & 0xffu);
+      }
     }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) v[q] = vn[q];
   }
   if (i1 == L) {  // the stream's last word
     if (count > 0) {
@@ -899,6 +1047,8 @@ fptc_status fptc_encoder_create(fptc_encoder **enc, int device, const fptc_domai
       // mu / log1p(mu) and 1 / (1 - alpha1) per scale)
       x.slack0 = (float)(std::fabs(dm.scale[0]) * 0x1p-18);
       x.slack1 = (float)(std::fabs(dm.scale[1]) * 0x1p-18);
+      x.d1_hi = (float)x.d1;
+      x.d1_lo = (float)(x.d1 - (double)x.d1_hi);
       x.on0 = dm.scale[0] > 1e-30 ? 1u : 0u;
       x.on1 = dm.scale[1] > 1e-30 ? 1u : 0u;
       x.cos_off = (uint32_t)cosv.size();

@@ -123,3 +123,98 @@ def test_zone0_slack_brackets_the_fp64_map(A0):
     for c in cs:
         lo, hi = _zone0_32(c - slack, A0, mu), _zone0_32(c + slack, A0, mu)
         assert lo <= _zone0_64(c, A0, mu) <= hi, (c, lo, hi)
+
+
+# ---- the window kernel's first tier: the DCT-II butterfly with per-bin bounds ----
+
+def _round_f32(fr):
+    """float32 nearest to the exact rational fr (ties to even), as one rounding."""
+    from fractions import Fraction
+    y = np.float32(float(fr))
+    best = None
+    for c in (np.nextafter(y, np.float32(-np.inf)), y, np.nextafter(y, np.float32(np.inf))):
+        dist = abs(Fraction(float(c)) - fr)
+        key = (dist, int(np.array(c, np.float32).view(np.uint32)) & 1)
+        if best is None or key < best[0]:
+            best = (key, c)
+    return np.float32(best[1])
+
+
+def _fma(a, b, c):
+    from fractions import Fraction
+    return _round_f32(Fraction(float(a)) * Fraction(float(b)) + Fraction(float(c)))
+
+
+def _cos32(num, den):
+    return f32(np.cos(np.pi * num / den))
+
+
+def _butterfly_bounded(x):
+    """The device's dct2_16_bounded in float32, operation by operation: outputs and bounds."""
+    u = 2.0 ** -24 * 1.02
+    uu_ = [f32(x[n] + x[31 - n]) for n in range(16)]
+    v = [f32(x[n] - x[31 - n]) for n in range(16)]
+    su, sv = sum(abs(float(t)) for t in uu_), sum(abs(float(t)) for t in v)
+    a, e = [0.0] * 16, [0.0] * 16
+    for j in range(8):
+        acc = f32(v[0] * _cos32(2 * j + 1, 64))
+        for n in range(1, 16):
+            acc = _fma(v[n], _cos32((2 * n + 1) * (2 * j + 1), 64), acc)
+        a[2 * j + 1], e[2 * j + 1] = acc, 18.1 * u * sv
+    uu = [f32(uu_[n] + uu_[15 - n]) for n in range(8)]
+    uv = [f32(uu_[n] - uu_[15 - n]) for n in range(8)]
+    suu, suv = sum(abs(float(t)) for t in uu), sum(abs(float(t)) for t in uv)
+    for j in range(4):
+        acc = f32(uv[0] * _cos32(2 * j + 1, 32))
+        for n in range(1, 8):
+            acc = _fma(uv[n], _cos32((2 * n + 1) * (2 * j + 1), 32), acc)
+        a[4 * j + 2], e[4 * j + 2] = acc, u * (9.6 * suv + su)
+    uuu = [f32(uu[n] + uu[7 - n]) for n in range(4)]
+    uuv = [f32(uu[n] - uu[7 - n]) for n in range(4)]
+    suuu, suuv = sum(abs(float(t)) for t in uuu), sum(abs(float(t)) for t in uuv)
+    a[0] = f32(f32(0.5) * f32(f32(uuu[0] + uuu[1]) + f32(uuu[2] + uuu[3])))
+    e[0] = 0.5 * u * (3 * suuu + suu + su)
+    acc = f32(uuu[0] * _cos32(1, 8))
+    for n in range(1, 4):
+        acc = _fma(uuu[n], _cos32(2 * n + 1, 8), acc)
+    a[8], e[8] = acc, u * (5.6 * suuu + suu + su)
+    for j in range(2):
+        acc = f32(uuv[0] * _cos32(2 * j + 1, 16))
+        for n in range(1, 4):
+            acc = _fma(uuv[n], _cos32((2 * n + 1) * (2 * j + 1), 16), acc)
+        a[8 * j + 4], e[8 * j + 4] = acc, u * (5.6 * suuv + suu + su)
+    return a, e
+
+
+def test_butterfly_bins_within_their_bounds():
+    import math
+    rng = np.random.default_rng(11)
+    worst = 0.0
+    tighter = []
+    for trial in range(120):
+        kind = trial % 6
+        if kind == 0:
+            x = rng.normal(0, 1, 32)
+        elif kind == 1:
+            x = 1e4 + rng.normal(0, 1e-2, 32)              # large offset, small variation
+        elif kind == 2:
+            x = rng.choice([-1, 1], 32) * 10.0 ** rng.uniform(-20, 6, 32)
+        elif kind == 3:
+            x = np.full(32, 3.0) + rng.integers(-1, 2, 32) * 2.0 ** -20
+        elif kind == 4:
+            x = rng.normal(100, 5, 32) * rng.choice([1, -1], 32)
+        else:
+            x = 100.0 + 30 * np.sin(np.arange(32) / 9.0) + rng.normal(0, 2, 32)   # power-like
+        x = x.astype(f32)
+        a, e = _butterfly_bounded(x)
+        s1 = float(np.sum(np.abs(x.astype(np.float64))))
+        for k in range(16):
+            exact = math.fsum(float(x[n]) * (0.5 if k == 0 else math.cos(math.pi / 32 * (n + 0.5) * k))
+                              for n in range(32))
+            err = abs(float(a[k]) - exact)
+            assert err <= e[k] + 1e-30, (trial, k, err, e[k])
+            worst = max(worst, err / (e[k] + 1e-300))
+            tighter.append(e[k] / (2.0 ** -19.5 * s1 + 1e-300))
+    assert worst < 1.0
+    # on the offset windows the bounds are far below the uniform 2^-19.5 sum |x|
+    assert np.median(tighter) < 0.5
