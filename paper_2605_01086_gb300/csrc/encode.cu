@@ -16,18 +16,21 @@
 //                 encoder does), one bin per lane, and quantizes from that.
 //   k_enc_ref     one thread per packing block of kPackBlock symbols: Alg. 1
 //                 on the block alone, entered with a word that starts at its
-//                 first symbol (the reference packing): where its words start
-//                 (a bitmap) and the state it ends in.
-//   k_enc_chain   one warp per stream: block after block, Alg. 1 from the
-//                 true state until a word starts where the reference's does
-//                 (from there on the two coincide: the rest comes from the
-//                 reference); each block's entry state; zeroes the words two
-//                 blocks share; the stream's word count, room and code checks.
+//                 first symbol (the reference packing): the words it closes
+//                 and the state it ends in; then the next block of the stream
+//                 packed from that state beside the next block's reference
+//                 until the two start a word at the same symbol (from there
+//                 on they coincide): the next block's transfer.
+//   k_enc_scan    one warp per stream: the word counts added up block after
+//                 block (a block entered in another state is walked again
+//                 from the true one); each block's entry state; zeroes the
+//                 words two blocks share; the stream's word count, room and
+//                 code checks.
 //   k_enc_pack    one thread per block: Alg. 1 from the block's entry state,
-//                 whole words with plain stores, the words shared with the
-//                 previous or next block with 64-bit atomicOr (their codeword
-//                 bits are disjoint), each word's symbol count by the block
-//                 that closes it.
+//                 whole words staged in shared memory and written out per
+//                 warp, the words shared with the previous or next block with
+//                 64-bit atomicOr (their codeword bits are disjoint), each
+//                 word's symbol count by the block that closes it.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -91,6 +94,15 @@ struct RefEnd {
   uint32_t bad;    // a level of the block has no codeword
 };
 
+// What Alg. 1 does over one packing block entered in a given state.
+struct BlockTrans {
+  int32_t adj;     // met: the words it closes are the reference's plus adj; else the words it closes
+  uint32_t bits;   // not met: the state it leaves the block in (bits of the open word
+  uint32_t count;  // and its codewords); met: the reference's end state
+  uint32_t flags;  // kTransMerged: it met the block's reference packing
+};
+constexpr uint32_t kTransMerged = 1u;
+
 struct EncParams {
   const float *x;
   uint64_t *words;
@@ -104,8 +116,10 @@ struct EncParams {
   const uint32_t *codes;
   const uint8_t *lens;
   PackState *blocks;
-  unsigned long long *ref_map;  // per packing block, kPackBlock bits: word starts of its reference packing
   RefEnd *ref_end;       // per packing block: the reference packing's end state
+  BlockTrans *trans;     // per packing block: Alg. 1 over it from the state its predecessor's reference ends in
+  const uint32_t *block_seg;  // per packing block: its segment
+  const uint32_t *code_tab;   // per domain, 256 entries: codeword | length << 16
   uint32_t *seg_bad;
   unsigned long long *fb_list;   // bins whose level the FP64 coefficient decides
   unsigned int *fb_count;
@@ -361,14 +375,6 @@ __global__ void __launch_bounds__(256) k_enc_levels(EncParams p) {
   p.levels[g] = (uint8_t)L;
 }
 
-// One thread per window, for encoders whose every domain has N = 32, E = 16:
-// the window's 16 Eq. 1 bins at once by the even/odd butterfly in FP32, with
-// a bound on each bin's error from the butterfly's own intermediate sums
-// (dct32.cuh dct2_16_bounded; the exact scale 2/N, 4/N for bin 0), plus the
-// FP64 encoder's own rounding; the zone quantizer is bracketed by that bound
-// as in k_enc_levels.  Bins it cannot settle are computed again, spread over
-// the warp's lanes, as compensated dot products; what those cannot settle goes
-// to the FP64 list.
 // First tier of k_enc_levels_w32 for the 16 bins of a window: levels into lv,
 // the bins the bound cannot settle into the mask undecided (their level 0).
 // T1: the zones of Table 1 (B1 = 2, B2 = 16), fixed per bin at compile time.
@@ -414,161 +420,232 @@ __device__ __forceinline__ uint32_t lane_prefix(uint32_t v, uint32_t lane) {
 
 constexpr uint32_t kLvThreads = 128;  // threads per CTA of k_enc_levels_w32 (4 warps)
 constexpr uint32_t kTier2Inline = 8;  // a warp with more undecided bins settles them itself
+constexpr uint32_t kLvGroups = 4;     // groups of 32 windows per warp, each loaded while the previous is computed
+constexpr uint32_t kRowPitch = 36;    // floats per window row in shared memory (144 bytes: 16-byte reads conflict-free)
 
-__global__ void __launch_bounds__(kLvThreads, 6) k_enc_levels_w32(EncParams p, uint64_t n_windows) {
-  // second-tier work shared by a warp's lanes: the samples of its windows that
-  // have undecided bins (rows padded to 33 floats: conflict-free), the list of
-  // (window lane, bin), the windows' levels, segments and sample sums
-  __shared__ float xs[kLvThreads / 32][32][33];
+__device__ __forceinline__ uint32_t lds_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+// 16 bytes, or src_bytes of them with zeros after (0: all zeros; src is not read)
+__device__ __forceinline__ void cp_async_16(void *dst, const void *src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(lds_addr(dst)), "l"(__cvta_generic_to_global(src))
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_4z(void *dst, const void *src, uint32_t src_bytes) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(lds_addr(dst)),
+               "l"(__cvta_generic_to_global(src)), "r"(src_bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit_group() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait_group() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// Where a window's samples are: its segment, the window within it, its first sample.
+struct LvWin {
+  uint64_t s = 0;           // segment
+  uint64_t g0 = 0;          // its first level
+  const float *src = nullptr;
+  uint64_t avail = 0;       // samples from src on in the stream (>= 1), 0 for no window
+};
+
+__device__ __forceinline__ LvWin lv_window(const EncParams &p, uint64_t gw, uint64_t n_windows, uint64_t s_from) {
+  LvWin r;
+  r.s = s_from;
+  if (gw >= n_windows) return r;
+  r.g0 = gw * 16u;
+  while (r.s + 1 < p.n_segs && p.segs[r.s + 1].level_offset <= r.g0) ++r.s;
+  const EncSeg &sg = p.segs[r.s];
+  const uint64_t i0 = ((r.g0 - sg.level_offset) >> 4) * 32u;
+  r.avail = sg.n_samples - i0;
+  r.src = p.x + sg.in_offset + i0;
+  return r;
+}
+
+// The window's 32 samples into its shared-memory row, asynchronously (zero
+// past the stream's end; no window: zeros).
+__device__ __forceinline__ void lv_load_async(const EncParams &p, const LvWin &wn, float *row) {
+  if (wn.avail >= 32 && (reinterpret_cast<uintptr_t>(wn.src) & 15u) == 0) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) cp_async_16(row + 4 * j, wn.src + 4 * j);
+  } else {
+    const float *base = wn.avail ? wn.src : p.x;  // a valid address where nothing is read
+#pragma unroll 8
+    for (int j = 0; j < 32; ++j)
+      cp_async_4z(row + j, (uint64_t)j < wn.avail ? wn.src + j : base, (uint64_t)j < wn.avail ? 4u : 0u);
+  }
+}
+
+// One thread per window, for encoders whose every domain has N = 32, E = 16:
+// the window's 16 Eq. 1 bins at once by the even/odd butterfly in FP32, with
+// a bound on each bin's error from the butterfly's own intermediate sums
+// (dct32.cuh dct2_16_bounded; the exact scale 2/N, 4/N for bin 0), plus the
+// FP64 encoder's own rounding; the zone quantizer is bracketed by that bound
+// as in k_enc_levels.  Bins it cannot settle are computed again, spread over
+// the warp's lanes, as compensated dot products; what those cannot settle goes
+// to the FP64 list.  A warp takes kLvGroups groups of 32 consecutive windows;
+// each group's samples come into shared memory by asynchronous copies while
+// the warp computes the group before.
+__global__ void __launch_bounds__(kLvThreads, 5) k_enc_levels_w32(EncParams p, uint64_t n_windows) {
+  // per warp: two groups' samples (one row per window), and the second tier's
+  // work list (window lane, bin), the windows' levels, segments, sample sums
+  __shared__ __align__(16) float rows[kLvThreads / 32][2][32 * kRowPitch];
   __shared__ uint16_t work[kLvThreads / 32][512];
   __shared__ uint32_t lvs[kLvThreads / 32][32][4];
   __shared__ uint32_t segs_s[kLvThreads / 32][32];
   __shared__ float s1s[kLvThreads / 32][32];
   const uint32_t lane = threadIdx.x & 31u, wid = threadIdx.x >> 5;
-  const uint64_t gw = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const bool valid = gw < n_windows;  // every lane stays for the warp's shuffles
-  const uint64_t g0 = gw * 16u;       // first level of the window (E = 16 everywhere)
-  // the segment: one search per CTA (its first window), then a step forward per
-  // window (a CTA's 128 windows span few segments)
+  const uint64_t first_group = ((uint64_t)blockIdx.x * (kLvThreads / 32) + wid) * kLvGroups;
+  // the segment: one search per CTA (its first window), then a step forward
+  // per window (a CTA's windows span few segments)
   __shared__ uint32_t s_first;
   if (threadIdx.x == 0)
-    s_first = (uint32_t)last_leq(p.n_segs, (uint64_t)blockIdx.x * blockDim.x * 16u,
+    s_first = (uint32_t)last_leq(p.n_segs, (uint64_t)blockIdx.x * (kLvThreads / 32) * kLvGroups * 32u * 16u,
                                  [&](uint64_t i) { return p.segs[i].level_offset; });
   __syncthreads();
-  uint64_t s = s_first;
-  if (valid)
-    while (s + 1 < p.n_segs && p.segs[s + 1].level_offset <= g0) ++s;
-  const EncSeg sg = p.segs[s];
-  const EncDomain d = p.doms[sg.domain];
-  const uint64_t w = valid ? (g0 - sg.level_offset) >> 4 : 0u;
-  const uint64_t i0 = w * 32u;
-  const uint64_t avail = valid ? sg.n_samples - i0 : 0u;  // >= 1 for a valid window
-  const float *src = p.x + sg.in_offset + i0;
-  float x[32];
-  if (avail >= 32 && (reinterpret_cast<uintptr_t>(src) & 15u) == 0) {
+  LvWin cur = lv_window(p, first_group * 32u + lane, n_windows, s_first);
+  lv_load_async(p, cur, rows[wid][0] + lane * kRowPitch);
+  cp_async_commit_group();
+#pragma unroll 1
+  for (uint32_t t = 0; t < kLvGroups; ++t) {
+    const uint64_t grp = first_group + t;
+    if (grp * 32u >= n_windows) break;  // the whole warp
+    // the next group's copies in flight
+    LvWin nxt = cur;
+    if (t + 1 < kLvGroups) {
+      nxt = lv_window(p, (grp + 1) * 32u + lane, n_windows, cur.s);
+      lv_load_async(p, nxt, rows[wid][(t + 1) & 1] + lane * kRowPitch);
+    }
+    cp_async_commit_group();
+    cp_async_wait_group<1>();
+    __syncwarp();
+    const float *const xr = rows[wid][t & 1];
+    const bool valid = cur.avail > 0;  // every lane stays for the warp's shuffles
+    const uint64_t s = cur.s;
+    const uint64_t g0 = cur.g0;
+    const EncDomain d = p.doms[p.segs[s].domain];
+    float x[32];
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
-      const float4 v = __ldg(reinterpret_cast<const float4 *>(src) + j);
+      const float4 v = *reinterpret_cast<const float4 *>(xr + lane * kRowPitch + 4 * j);
       x[4 * j] = v.x;
       x[4 * j + 1] = v.y;
       x[4 * j + 2] = v.z;
       x[4 * j + 3] = v.w;
     }
-  } else {
+    float s1 = 0.0f;
 #pragma unroll
-    for (int j = 0; j < 32; ++j) x[j] = (uint64_t)j < avail ? __ldg(src + j) : 0.0f;  // zero padding past S
-  }
-  float s1 = 0.0f;
-#pragma unroll
-  for (int j = 0; j < 32; ++j) s1 += fabsf(x[j]);
-  float a[16], eb[16];
-  dct32::dct2_16_bounded(x, a, eb);
-  // |c - c64| <= the butterfly's bound for bin k (scaled like c) + the FP64 encoder's own rounding
-  const float err64 = s1 * (2.0f / 32.0f) * 0x1p-40f + 1e-30f;
-  uint32_t lv[4] = {0u, 0u, 0u, 0u};
-  uint32_t undecided = 0;  // bins the butterfly's bound cannot settle
-  if (d.B1 == 2u && d.B2 == 16u)  // Table 1's zones: the zone of every bin known at compile time
-    tier1_bins<true>(a, eb, err64, d, lv, undecided);
-  else
-    tier1_bins<false>(a, eb, err64, d, lv, undecided);
-  if (!valid) undecided = 0u;
-  // second tier, spread over the warp's lanes: each undecided bin again as a
-  // compensated FP32 dot product (|error| <= 2^-34 (2/N) sum |x|, as in
-  // k_enc_levels); what that cannot settle goes to the FP64 list
-  const uint32_t cnt = (uint32_t)__popc(undecided);
-  const uint32_t incl = lane_prefix(cnt, lane);
-  const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
-  if (total && total <= kTier2Inline) {  // a few: k_enc_fallback settles them (compensated, then FP64)
-    uint64_t lo8 = ((uint64_t)lv[1] << 32) | lv[0], hi8 = ((uint64_t)lv[3] << 32) | lv[2];
-    uint32_t u = undecided;
-    while (u) {
-      const uint32_t k = (uint32_t)(__ffs(u) - 1);
-      u &= u - 1u;
-      const unsigned int slot = fb_slot(p);
-      if (slot != ~0u) {
-        p.fb_list[slot] = fb_entry(g0 + k, s);  // its level (0 here) is written after the window's store
-      } else {
-        const uint64_t L = level_fp64_seg(p, g0 + k, s);
-        if (k < 8)
-          lo8 |= L << (8 * k);
-        else
-          hi8 |= L << (8 * (k - 8));
-      }
-    }
-    lv[0] = (uint32_t)lo8;
-    lv[1] = (uint32_t)(lo8 >> 32);
-    lv[2] = (uint32_t)hi8;
-    lv[3] = (uint32_t)(hi8 >> 32);
-  } else if (total) {  // many (re-encoded signals): settled here, spread over the warp's lanes
-    if (cnt) {
-#pragma unroll
-      for (int n = 0; n < 32; ++n) xs[wid][lane][n] = x[n];
-      segs_s[wid][lane] = (uint32_t)s;
-      s1s[wid][lane] = s1;
-      uint32_t u = undecided, o = incl - cnt;
+    for (int j = 0; j < 32; ++j) s1 += fabsf(x[j]);
+    float a[16], eb[16];
+    dct32::dct2_16_bounded(x, a, eb);
+    // |c - c64| <= the butterfly's bound for bin k (scaled like c) + the FP64 encoder's own rounding
+    const float err64 = s1 * (2.0f / 32.0f) * 0x1p-40f + 1e-30f;
+    uint32_t lv[4] = {0u, 0u, 0u, 0u};
+    uint32_t undecided = 0;  // bins the butterfly's bound cannot settle
+    if (d.B1 == 2u && d.B2 == 16u)  // Table 1's zones: the zone of every bin known at compile time
+      tier1_bins<true>(a, eb, err64, d, lv, undecided);
+    else
+      tier1_bins<false>(a, eb, err64, d, lv, undecided);
+    if (!valid) undecided = 0u;
+    // second tier, spread over the warp's lanes: each undecided bin again as a
+    // compensated FP32 dot product (|error| <= 2^-34 (2/N) sum |x|, as in
+    // k_enc_levels); what that cannot settle goes to the FP64 list
+    const uint32_t cnt = (uint32_t)__popc(undecided);
+    const uint32_t incl = lane_prefix(cnt, lane);
+    const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+    if (total && total <= kTier2Inline) {  // a few: k_enc_fallback settles them (compensated, then FP64)
+      uint64_t lo8 = ((uint64_t)lv[1] << 32) | lv[0], hi8 = ((uint64_t)lv[3] << 32) | lv[2];
+      uint32_t u = undecided;
       while (u) {
-        work[wid][o++] = (uint16_t)((lane << 4) | (uint32_t)(__ffs(u) - 1));
+        const uint32_t k = (uint32_t)(__ffs(u) - 1);
         u &= u - 1u;
-      }
-    }
-#pragma unroll
-    for (int q = 0; q < 4; ++q) lvs[wid][lane][q] = lv[q];
-    __syncwarp();
-    const uint64_t gw_base = gw - lane;
-    for (uint32_t t = lane; t < total; t += 32) {
-      const uint32_t e = work[wid][t], own = e >> 4, k = e & 15u;
-      const uint64_t so = segs_s[wid][own];
-      const EncDomain od = p.doms[p.segs[so].domain];
-      const float2 *ct = reinterpret_cast<const float2 *>(p.cosf) + od.cos_off + k;
-      const float *xo = xs[wid][own];
-      float hi = 0.0f, lo = 0.0f;
-#pragma unroll 8
-      for (int n = 0; n < 32; ++n) {
-        const float xv = xo[n];
-        const float2 cs = ct[(size_t)n * 16u];
-        const float pr = __fmul_rn(xv, cs.x);
-        const float pe = __fadd_rn(__fmaf_rn(xv, cs.x, -pr), __fmul_rn(xv, cs.y));
-        const float tt = __fadd_rn(hi, pr);
-        const float bp = __fsub_rn(tt, hi);
-        lo = __fadd_rn(lo, __fadd_rn(__fadd_rn(__fsub_rn(hi, __fsub_rn(tt, bp)), __fsub_rn(pr, bp)), pe));
-        hi = tt;
-      }
-      const float c = (hi + lo) * (2.0f / 32.0f);
-      const float err2 = s1s[wid][own] * (2.0f / 32.0f) * 0x1p-34f + 1e-30f;
-      const float m = err2 + (k < od.B1 ? od.slack0 : od.slack1) + fabsf(c) * 0x1p-21f;
-      uint32_t L = 0u;
-      bool decided;
-      if (k < od.B1) {
-        const uint32_t l0 = zone0_level32(c - m, od), l1 = zone0_level32(c + m, od);
-        decided = l0 == l1;
-        L = l0;
-      } else {
-        decided = zone1_decide_pair(hi * (2.0f / 32.0f), lo * (2.0f / 32.0f), err2 * 2.0f, m, od, L);
-      }
-      const uint64_t g = (gw_base + own) * 16u + k;
-      if (!decided) {
         const unsigned int slot = fb_slot(p);
         if (slot != ~0u) {
-          p.fb_list[slot] = fb_entry(g, so);
-          L = 0u;  // k_enc_fallback writes this level after the window's store
+          p.fb_list[slot] = fb_entry(g0 + k, s);  // its level (0 here) is written after the window's store
         } else {
-          L = level_fp64_seg(p, g, so);
+          const uint64_t L = level_fp64_seg(p, g0 + k, s);
+          if (k < 8)
+            lo8 |= L << (8 * k);
+          else
+            hi8 |= L << (8 * (k - 8));
         }
       }
-      reinterpret_cast<uint8_t *>(lvs[wid][own])[k] = (uint8_t)L;
+      lv[0] = (uint32_t)lo8;
+      lv[1] = (uint32_t)(lo8 >> 32);
+      lv[2] = (uint32_t)hi8;
+      lv[3] = (uint32_t)(hi8 >> 32);
+    } else if (total) {  // many (re-encoded signals): settled here, spread over the warp's lanes
+      if (cnt) {
+        segs_s[wid][lane] = (uint32_t)s;
+        s1s[wid][lane] = s1;
+        uint32_t u = undecided, o = incl - cnt;
+        while (u) {
+          work[wid][o++] = (uint16_t)((lane << 4) | (uint32_t)(__ffs(u) - 1));
+          u &= u - 1u;
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) lvs[wid][lane][q] = lv[q];
+      __syncwarp();
+      const uint64_t gw_base = grp * 32u;
+      for (uint32_t i = lane; i < total; i += 32) {
+        const uint32_t e = work[wid][i], own = e >> 4, k = e & 15u;
+        const uint64_t so = segs_s[wid][own];
+        const EncDomain od = p.doms[p.segs[so].domain];
+        const float2 *ct = reinterpret_cast<const float2 *>(p.cosf) + od.cos_off + k;
+        const float *xo = xr + own * kRowPitch;
+        float hi = 0.0f, lo = 0.0f;
+#pragma unroll 8
+        for (int n = 0; n < 32; ++n) {
+          const float xv = xo[n];
+          const float2 cs = ct[(size_t)n * 16u];
+          const float pr = __fmul_rn(xv, cs.x);
+          const float pe = __fadd_rn(__fmaf_rn(xv, cs.x, -pr), __fmul_rn(xv, cs.y));
+          const float tt = __fadd_rn(hi, pr);
+          const float bp = __fsub_rn(tt, hi);
+          lo = __fadd_rn(lo, __fadd_rn(__fadd_rn(__fsub_rn(hi, __fsub_rn(tt, bp)), __fsub_rn(pr, bp)), pe));
+          hi = tt;
+        }
+        const float c = (hi + lo) * (2.0f / 32.0f);
+        const float err2 = s1s[wid][own] * (2.0f / 32.0f) * 0x1p-34f + 1e-30f;
+        const float m = err2 + (k < od.B1 ? od.slack0 : od.slack1) + fabsf(c) * 0x1p-21f;
+        uint32_t L = 0u;
+        bool decided;
+        if (k < od.B1) {
+          const uint32_t l0 = zone0_level32(c - m, od), l1 = zone0_level32(c + m, od);
+          decided = l0 == l1;
+          L = l0;
+        } else {
+          decided = zone1_decide_pair(hi * (2.0f / 32.0f), lo * (2.0f / 32.0f), err2 * 2.0f, m, od, L);
+        }
+        const uint64_t g = (gw_base + own) * 16u + k;
+        if (!decided) {
+          const unsigned int slot = fb_slot(p);
+          if (slot != ~0u) {
+            p.fb_list[slot] = fb_entry(g, so);
+            L = 0u;  // k_enc_fallback writes this level after the window's store
+          } else {
+            L = level_fp64_seg(p, g, so);
+          }
+        }
+        reinterpret_cast<uint8_t *>(lvs[wid][own])[k] = (uint8_t)L;
+      }
+      __syncwarp();
+#pragma unroll
+      for (int q = 0; q < 4; ++q) lv[q] = lvs[wid][lane][q];
     }
-    __syncwarp();
+    if (valid) {
+      uint8_t *const dst = p.levels + g0;
+      if ((reinterpret_cast<uintptr_t>(dst) & 15u) == 0) {
+        *reinterpret_cast<uint4 *>(dst) = make_uint4(lv[0], lv[1], lv[2], lv[3]);
+      } else {
 #pragma unroll
-    for (int q = 0; q < 4; ++q) lv[q] = lvs[wid][lane][q];
+        for (int k = 0; k < 16; ++k) dst[k] = (uint8_t)(lv[k >> 2] >> (8 * (k & 3)));
+      }
+    }
+    __syncwarp();  // every lane is done with this group's rows and tier-2 lists before they are refilled
+    cur = nxt;
   }
-  if (!valid) return;
-  uint8_t *const dst = p.levels + g0;
-  if ((reinterpret_cast<uintptr_t>(dst) & 15u) == 0) {
-    *reinterpret_cast<uint4 *>(dst) = make_uint4(lv[0], lv[1], lv[2], lv[3]);
-  } else {
-#pragma unroll
-    for (int k = 0; k < 16; ++k) dst[k] = (uint8_t)(lv[k >> 2] >> (8 * (k & 3)));
-  }
+  cp_async_wait_group<0>();
 }
 
 // ---- SymLen packing (Alg. 1) in parallel over blocks of kPackBlock symbols ----
@@ -576,92 +653,198 @@ __global__ void __launch_bounds__(kLvThreads, 6) k_enc_levels_w32(EncParams p, u
 // start inside a block depends only on the state the block is entered with
 // (the bits already used in the open word).  Greedy packings entered with
 // different states soon start a word at the same symbol, and from there on
-// they coincide.  k_enc_ref packs every block on its own, entered with a word
-// that starts at its first symbol, and keeps where its words start (a bitmap)
-// and the state it ends in.  k_enc_chain walks each stream block by block with
-// the true state: it packs only until one of its word starts is one of the
-// reference's, then takes the rest of the block from the reference.
-constexpr uint32_t kRefWords = kPackBlock / 64;  // bitmap words per block
+// they coincide.  Call the packing of a block entered with a word that starts
+// at its first symbol the block's reference packing.  A block whose packing
+// meets its reference ends in the reference's end state, whatever state it
+// was entered with; so in the usual case every block but a stream's first is
+// entered in the state its predecessor's reference ends in.  k_enc_ref packs
+// block b as its reference does (the words it closes, the state it ends in),
+// then walks block b + 1 from that end state beside block b + 1's reference
+// until the two start a word at the same symbol: the transfer of block b + 1,
+// from the state it is entered in when block b met its reference.  k_enc_scan
+// adds the word counts up along each stream; a block whose predecessor never
+// met its reference (constant code lengths can do that) was entered in
+// another state, and the scan walks it again from the true one.
 
+// 16 levels from lv + i (zero past n) as one 16-byte vector.
+__device__ __forceinline__ uint4 load_raw16(const uint8_t *lv, uint64_t i, uint64_t n) {
+  if (i + 16 <= n && (reinterpret_cast<uintptr_t>(lv + i) & 15u) == 0) return *reinterpret_cast<const uint4 *>(lv + i);
+  uint32_t t[4] = {0u, 0u, 0u, 0u};
+  for (uint32_t r = 0; r < 16 && i + r < n; ++r) t[r >> 2] |= (uint32_t)lv[i + r] << (8 * (r & 3));
+  return make_uint4(t[0], t[1], t[2], t[3]);
+}
 
 // 64 levels from lv + i (zero past n) as four 16-byte vectors.
 __device__ __forceinline__ void load_raw64(const uint8_t *lv, uint64_t i, uint64_t n, uint4 (&v)[4]) {
 #pragma unroll
+  for (int q = 0; q < 4; ++q) v[q] = load_raw16(lv, i + 16 * q, n);
+}
+
+// Alg. 1 over 64 levels of the reference packing (FULL: all 64 exist).
+template <bool FULL>
+__device__ __forceinline__ void ref_step64(const uint4 (&v)[4], uint32_t i, uint32_t nb, const uint8_t *len,
+                                           uint32_t &words, uint32_t &bits, uint32_t &count, bool &bad) {
+#pragma unroll
   for (int q = 0; q < 4; ++q) {
-    const uint64_t o = i + 16 * q;
-    if (o + 16 <= n && (reinterpret_cast<uintptr_t>(lv + o) & 15u) == 0) {
-      v[q] = *reinterpret_cast<const uint4 *>(lv + o);
-    } else {
-      uint32_t t[4] = {0u, 0u, 0u, 0u};
-      for (uint32_t r = 0; r < 16 && o + r < n; ++r) t[r >> 2] |= (uint32_t)lv[o + r] << (8 * (r & 3));
-      v[q] = make_uint4(t[0], t[1], t[2], t[3]);
+    const uint32_t vw[4] = {v[q].x, v[q].y, v[q].z, v[q].w};
+    uint32_t cl[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) cl[j] = __ldg(len + ((vw[j >> 2] >> (8 * (j & 3))) & 0xffu));
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      if (!FULL && i + 16 * q + j >= nb) break;
+      const uint32_t c = cl[j];
+      bad = bad || c == 0u;
+      const bool start = count == 0u || bits + c > 64u;  // a word starts here
+      words += (start && count) ? 1u : 0u;
+      bits = (start ? 0u : bits) + c;
+      count = (start ? 0u : count) + 1u;
     }
   }
 }
 
-// One thread per packing block: the reference packing of the block.
+// One thread per packing block b: its reference packing, then the transfer
+// of block b + 1 (when it is in the same stream) entered in the state the
+// reference of b ends in.
 __global__ void __launch_bounds__(128) k_enc_ref(EncParams p) {
   const uint64_t b = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= p.n_blocks) return;
-  const uint64_t s = last_leq(p.n_segs, b, [&](uint64_t i) { return p.segs[i].block_base; });
-  const EncSeg sg = p.segs[s];
+  const EncSeg sg = p.segs[p.block_seg[b]];
   const EncDomain d = p.doms[sg.domain];
   const uint64_t L = sg.n_windows * d.E;
   const uint64_t i0 = (b - sg.block_base) * kPackBlock;
   const uint32_t nb = (uint32_t)(L - i0 < kPackBlock ? L - i0 : kPackBlock);
   const uint8_t *lv = p.levels + sg.level_offset + i0;
   const uint8_t *len = p.lens + d.code_off;
-  unsigned long long *const map = p.ref_map + b * kRefWords;
   uint32_t words = 0, bits = 0, count = 0;
   bool bad = false;
-  // 64 levels (one bitmap word) per step, the next 64 in flight
+  // block b + 1 of the same stream, if any
+  const uint32_t nb2 = i0 + nb < L ? (uint32_t)(L - i0 - nb < kPackBlock ? L - i0 - nb : kPackBlock) : 0u;
+  // 64 levels per step, the next 64 in flight
   uint4 v[4], vn[4];
   load_raw64(lv, 0, nb, v);
   for (uint32_t i = 0; i < nb; i += 64) {
     if (i + 64 < nb) load_raw64(lv, i + 64, nb, vn);
-    uint64_t cur = 0;  // word starts among symbols i .. i + 63
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const uint32_t i16 = i + 16 * q;
-      if (i16 >= nb) break;
-      const uint32_t vw[4] = {v[q].x, v[q].y, v[q].z, v[q].w};
-      uint32_t cl[16];
-#pragma unroll
-      for (int j = 0; j < 16; ++j) cl[j] = __ldg(len + ((vw[j >> 2] >> (8 * (j & 3))) & 0xffu));
-#pragma unroll
-      for (int j = 0; j < 16; ++j) {
-        if (i16 + j >= nb) break;
-        const uint32_t c = cl[j];
-        bad = bad || c == 0u;
-        if (count == 0 || bits + c > 64) {  // a word starts at symbol i16 + j
-          if (count) ++words;
-          bits = 0;
-          count = 0;
-          cur |= 1ull << (16 * q + j);
-        }
-        bits += c;
-        ++count;
-      }
-    }
-    map[i >> 6] = cur;
+    if (i + 64 <= nb)
+      ref_step64<true>(v, i, nb, len, words, bits, count, bad);
+    else
+      ref_step64<false>(v, i, nb, len, words, bits, count, bad);
 #pragma unroll
     for (int q = 0; q < 4; ++q) v[q] = vn[q];
   }
-  for (uint32_t w = (nb + 63) >> 6; w < kRefWords; ++w) map[w] = 0;
   p.ref_end[b] = RefEnd{words, bits, count, bad ? 1u : 0u};
+  if (b == sg.block_base) p.trans[b] = BlockTrans{0, 0u, 0u, kTransMerged};  // a stream's first block packs as its reference
+  if (nb2 == 0) return;
+  // block b + 1: Alg. 1 from (bits, count) and from a fresh word side by side
+  const uint8_t *lv2 = lv + nb;
+  uint32_t rb = 0, rc = 0, closes = 0, r = 0;
+  bool met = false;
+  for (uint32_t i = 0; i < nb2 && !met; i += 16) {
+    const uint4 u = load_raw16(lv2, i, nb2);
+    const uint32_t vw[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      if (i + j >= nb2) break;
+      const uint32_t c = __ldg(len + ((vw[j >> 2] >> (8 * (j & 3))) & 0xffu));
+      const bool rs = rc == 0u || rb + c > 64u;  // the reference starts a word here
+      const bool ts = bits + c > 64u;            // so does the packing from (bits, count)
+      if (rs && ts) {
+        met = true;
+        break;
+      }
+      r += rs ? 1u : 0u;
+      closes += ts ? 1u : 0u;
+      rb = (rs ? 0u : rb) + c;
+      rc = (rs ? 0u : rc) + 1u;
+      bits = (ts ? 0u : bits) + c;
+      count = (ts ? 0u : count) + 1u;
+    }
+  }
+  // met: the word open before the meeting symbol closes there, then come the
+  // reference's words but the r that start before it
+  p.trans[b + 1] = met ? BlockTrans{(int32_t)(closes + 1u) - (int32_t)r, 0u, 0u, kTransMerged}
+                       : BlockTrans{(int32_t)closes, bits, count, 0u};
 }
 
-// One warp per stream: the true packing state block after block, packing each
-// block from its entry state until a word starts where the reference's does;
+// Word starts of Alg. 1 among symbols from .. valid - 1 of a chunk of 32
+// (S: inclusive prefix of the chunk's code lengths, per lane), entered in
+// (bits, count); a word that starts at the chunk's first symbol because none
+// is open (count == 0) is one too.  One ballot per word start; the state is
+// carried over.
+__device__ __forceinline__ uint32_t chunk_starts(uint32_t S, uint32_t lane, uint32_t valid, uint32_t &bits,
+                                                 uint32_t &count) {
+  uint32_t mask = count == 0u ? 1u : 0u;
+  uint32_t from = 0;
+  while (true) {
+    const uint32_t pre = from ? __shfl_sync(0xffffffffu, S, from - 1) : 0u;
+    const uint32_t over = __ballot_sync(0xffffffffu, lane >= from && lane < valid && bits + (S - pre) > 64u);
+    if (over == 0) {  // the rest of the chunk fits the open word
+      bits += __shfl_sync(0xffffffffu, S, valid - 1) - pre;
+      count += valid - from;
+      return mask;
+    }
+    from = (uint32_t)(__ffs(over) - 1);  // a word starts at symbol from
+    mask |= 1u << from;
+    bits = 0;
+    count = 0;
+  }
+}
+
+// The transfer of block b entered in (bits, count > 0), by the whole warp:
+// Alg. 1 from that state and the block's reference side by side, 32 symbols
+// at a time (a warp scan of their code lengths; each word start one ballot),
+// until both start a word at the same symbol.  Levels arrive 128 per round
+// trip (a 4-byte load per lane), the next 128 in flight.
+__device__ BlockTrans walk_block(const EncParams &p, const EncSeg &sg, const EncDomain &d, uint64_t b, uint32_t bits,
+                                 uint32_t count, uint32_t lane) {
+  const uint64_t L = sg.n_windows * d.E;
+  const uint64_t i0 = (b - sg.block_base) * kPackBlock;
+  const uint32_t nb = (uint32_t)(L - i0 < kPackBlock ? L - i0 : kPackBlock);
+  const uint8_t *lv = p.levels + sg.level_offset + i0;
+  const uint8_t *len = p.lens + d.code_off;
+  uint32_t rb = 0, rc = 0, closes = 0, r = 0;
+  auto fetch = [&](uint32_t at) -> uint32_t {  // levels at .. at + 127, four per lane
+    const uint32_t o = at + 4 * lane;
+    if (o + 4 <= nb && (reinterpret_cast<uintptr_t>(lv + o) & 3u) == 0) return *reinterpret_cast<const uint32_t *>(lv + o);
+    uint32_t t = 0;
+    for (uint32_t q = 0; q < 4 && o + q < nb; ++q) t |= (uint32_t)lv[o + q] << (8 * q);
+    return t;
+  };
+  uint32_t cur = fetch(0);
+  for (uint32_t at = 0; at < nb; at += 128) {
+    const uint32_t nxt = at + 128 < nb ? fetch(at + 128) : 0u;
+#pragma unroll 1
+    for (uint32_t k = 0; k < 4; ++k) {
+      const uint32_t c = at + 32 * k;
+      if (c >= nb) break;
+      const uint32_t valid = nb - c < 32 ? nb - c : 32;
+      const uint32_t vw = __shfl_sync(0xffffffffu, cur, 8 * k + (lane >> 2));
+      const uint32_t cl = lane < valid ? __ldg(len + ((vw >> (8 * (lane & 3))) & 0xffu)) : 0u;
+      const uint32_t S = lane_prefix(cl, lane);
+      const uint32_t rm = chunk_starts(S, lane, valid, rb, rc);
+      const uint32_t tm = chunk_starts(S, lane, valid, bits, count);
+      const uint32_t both = rm & tm;
+      if (both) {  // they meet at symbol c + t
+        const uint32_t before = (1u << (__ffs(both) - 1)) - 1u;
+        closes += __popc(tm & before);
+        r += __popc(rm & before);
+        return BlockTrans{(int32_t)(closes + 1u) - (int32_t)r, 0u, 0u, kTransMerged};
+      }
+      closes += __popc(tm);
+      r += __popc(rm);
+    }
+    cur = nxt;
+  }
+  return BlockTrans{(int32_t)closes, bits, count, 0u};
+}
+
+// One warp per stream: the true packing state block after block from the
+// blocks' transfers, 32 blocks at a time (a warp scan of their word counts);
 // each block's entry state for k_enc_pack; the words two blocks share are
 // zeroed for the blocks' atomicOr; code and room checks; the stream's word
-// count.  The warp takes 32 symbols at a time: a warp scan of their code
-// lengths, then each word break is one ballot (the first symbol whose bits no
-// longer fit the open word), so the walk costs a few instructions per word
-// with no divergence.  Levels arrive 128 per round trip (a 4-byte load per
-// lane), the next 128 in flight.
-
-__global__ void __launch_bounds__(128) k_enc_chain(EncParams p) {
+// count.  A block entered in another state than its transfer assumed (its
+// predecessor never met its reference) is walked again from the true state.
+__global__ void __launch_bounds__(128) k_enc_scan(EncParams p) {
   const uint64_t s = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const uint32_t lane = threadIdx.x & 31u;
   if (s >= p.n_segs) return;  // the whole warp
@@ -669,85 +852,72 @@ __global__ void __launch_bounds__(128) k_enc_chain(EncParams p) {
   const EncDomain d = p.doms[sg.domain];
   const uint64_t L = sg.n_windows * d.E;
   const uint64_t nblk = (L + kPackBlock - 1) / kPackBlock;
-  const uint8_t *len = p.lens + d.code_off;
   uint64_t w = 0;  // the open word (words closed so far)
   uint32_t bits = 0, count = 0;
+  bool assumed = true;  // the next block is entered in the state its transfer assumed
   bool bad = false;
-  for (uint64_t jb = 0; jb < nblk; ++jb) {
-    const uint64_t b = sg.block_base + jb;
-    if (lane == 0) {
-      p.blocks[b] = PackState{w, bits, count};
-      if (bits > 0 && w < sg.room) p.words[sg.word_offset + w] = 0;  // shared with the previous block
+  uint64_t jb = 0;
+  while (jb < nblk) {
+    const uint64_t b0 = sg.block_base + jb;
+    if (!assumed) {
+      if (lane == 0) {
+        p.blocks[b0] = PackState{w, bits, count};
+        if (bits > 0 && w < sg.room) p.words[sg.word_offset + w] = 0;  // shared with the previous block
+      }
+      const RefEnd re = p.ref_end[b0];
+      if (re.bad) {
+        bad = true;
+        break;
+      }
+      const BlockTrans t = walk_block(p, sg, d, b0, bits, count, lane);
+      const bool met = (t.flags & kTransMerged) != 0;
+      w += (uint64_t)((int64_t)t.adj + (met ? (int64_t)re.words : 0));
+      bits = met ? re.bits : t.bits;
+      count = met ? re.count : t.count;
+      assumed = met;
+      ++jb;
+      continue;
     }
-    const RefEnd re = p.ref_end[b];
-    if (re.bad) {
+    const uint32_t n = nblk - jb < 32 ? (uint32_t)(nblk - jb) : 32u;
+    BlockTrans t{0, 0u, 0u, 0u};
+    RefEnd re{0u, 0u, 0u, 0u};
+    if (lane < n) {
+      t = p.trans[b0 + lane];
+      re = p.ref_end[b0 + lane];
+    }
+    const bool met = (t.flags & kTransMerged) != 0;
+    const uint32_t delta = (uint32_t)(t.adj + (met ? (int32_t)re.words : 0));
+    const uint32_t xb = met ? re.bits : t.bits, xc = met ? re.count : t.count;  // the state it leaves
+    const uint32_t badm = __ballot_sync(0xffffffffu, lane < n && re.bad);
+    const uint32_t open = __ballot_sync(0xffffffffu, lane < n && !met);
+    // the blocks entered as assumed: up to the first that did not meet its
+    // reference (it is itself one), before the first bad one
+    uint32_t m = n;
+    if (open) m = min(m, (uint32_t)__ffs(open));
+    const uint32_t first_bad = badm ? (uint32_t)(__ffs(badm) - 1) : 32u;
+    m = min(m, first_bad);
+    uint32_t eb = __shfl_up_sync(0xffffffffu, xb, 1), ec = __shfl_up_sync(0xffffffffu, xc, 1);
+    if (lane == 0) {
+      eb = bits;
+      ec = count;
+    }
+    const uint32_t dl = lane < m ? delta : 0u;
+    const uint32_t incl = lane_prefix(dl, lane);
+    const uint64_t we = w + (incl - dl);
+    if (lane < m) {
+      p.blocks[b0 + lane] = PackState{we, eb, ec};
+      if (eb > 0 && we < sg.room) p.words[sg.word_offset + we] = 0;  // shared with the previous block
+    }
+    if (m > 0) {
+      w += __shfl_sync(0xffffffffu, incl, m - 1);
+      bits = __shfl_sync(0xffffffffu, xb, m - 1);
+      count = __shfl_sync(0xffffffffu, xc, m - 1);
+      assumed = ((open >> (m - 1)) & 1u) == 0u;
+    }
+    jb += m;
+    if (badm && m == first_bad) {
       bad = true;
       break;
-    }
-    const uint64_t i0 = jb * kPackBlock;
-    const uint32_t nb = (uint32_t)(L - i0 < kPackBlock ? L - i0 : kPackBlock);
-    const uint8_t *lv = p.levels + sg.level_offset + i0;
-    const unsigned long long *map = p.ref_map + b * kRefWords;
-    int32_t mpos = -1;  // where the packing meets the reference's word starts
-    const bool open_word = count != 0;  // entered with a word open (every block but a stream's first)
-    if (!open_word) {
-      mpos = 0;  // the stream's first symbol starts a word, as the reference's does
-    } else {
-      auto fetch = [&](uint32_t at) -> uint32_t {  // levels at .. at + 127, four per lane
-        const uint32_t o = at + 4 * lane;
-        if (o + 4 <= nb && (reinterpret_cast<uintptr_t>(lv + o) & 3u) == 0) return *reinterpret_cast<const uint32_t *>(lv + o);
-        uint32_t t = 0;
-        for (uint32_t r = 0; r < 4 && o + r < nb; ++r) t |= (uint32_t)lv[o + r] << (8 * r);
-        return t;
-      };
-      uint32_t cur = fetch(0);
-      for (uint32_t at = 0; at < nb && mpos < 0; at += 128) {
-        const uint32_t nxt = at + 128 < nb ? fetch(at + 128) : 0u;
-        const unsigned long long m0 = map[at >> 6], m1 = at + 64 < nb ? map[(at >> 6) + 1] : 0ull;
-#pragma unroll 1
-        for (uint32_t k = 0; k < 4 && mpos < 0; ++k) {
-          const uint32_t c = at + 32 * k;
-          if (c >= nb) break;
-          const uint32_t valid = nb - c < 32 ? nb - c : 32;
-          const uint32_t vw = __shfl_sync(0xffffffffu, cur, 8 * k + (lane >> 2));
-          const uint32_t cl = lane < valid ? __ldg(len + ((vw >> (8 * (lane & 3))) & 0xffu)) : 0u;
-          const uint32_t S = lane_prefix(cl, lane);  // bits of symbols c .. c + lane
-          const unsigned long long mk = (k < 2 ? m0 : m1) >> (32 * (k & 1));  // reference starts of c .. c + 31
-          uint32_t from = 0;  // first symbol of the chunk not yet placed
-          while (from < valid) {
-            const uint32_t pre = from ? __shfl_sync(0xffffffffu, S, from - 1) : 0u;
-            const uint32_t over = __ballot_sync(0xffffffffu, lane >= from && lane < valid && bits + (S - pre) > 64u);
-            if (over == 0) {  // the rest of the chunk fits the open word
-              bits += __shfl_sync(0xffffffffu, S, valid - 1) - pre;
-              count += valid - from;
-              break;
-            }
-            const uint32_t t = (uint32_t)(__ffs(over) - 1);  // a word starts at symbol c + t
-            if ((mk >> t) & 1ull) {
-              mpos = (int32_t)(c + t);
-              break;
-            }
-            ++w;  // the open word closes before symbol c + t
-            bits = 0;
-            count = 0;
-            from = t;
-          }
-        }
-        cur = nxt;
-      }
-    }
-    if (mpos >= 0) {  // from symbol mpos on the block packs as the reference does
-      // the reference's word starts before mpos (a warp popcount over the bitmap)
-      uint32_t r = 0;
-      const uint32_t full = (uint32_t)mpos >> 6;
-      for (uint32_t q = lane; q < full; q += 32) r += __popcll(map[q]);
-      if (lane == 0 && (mpos & 63)) r += __popcll(map[full] & ((1ull << (mpos & 63)) - 1ull));
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
-      if (open_word) ++w;  // the word open before symbol mpos (never empty mid-stream) closes there
-      w += re.words - r;  // the reference's words from symbol mpos on, but its open one
-      bits = re.bits;
-      count = re.count;
     }
   }
   if (lane == 0) {
@@ -816,76 +986,132 @@ __global__ void __launch_bounds__(256) k_enc_fallback(EncParams p) {
   }
 }
 
-// One thread per packing block: Alg. 1 from the block's recorded state.
-__global__ void __launch_bounds__(128) k_enc_pack(EncParams p) {
-  const uint64_t b = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (b >= p.n_blocks) return;
-  const uint64_t s = last_leq(p.n_segs, b, [&](uint64_t i) { return p.segs[i].block_base; });
-  if (p.seg_bad[s]) return;
-  const EncSeg sg = p.segs[s];
-  const EncDomain d = p.doms[sg.domain];
-  const uint64_t j = b - sg.block_base;
-  const uint64_t L = sg.n_windows * d.E;
-  const uint64_t i0 = j * kPackBlock, i1 = i0 + kPackBlock < L ? i0 + kPackBlock : L;
-  const uint8_t *lv = p.levels + sg.level_offset;
-  const uint32_t *code = p.codes + d.code_off;
-  const uint8_t *len = p.lens + d.code_off;
-  unsigned long long *const out = reinterpret_cast<unsigned long long *>(p.words + sg.word_offset);
-  uint8_t *const sl = p.symlen + sg.word_offset;
-  const PackState st = p.blocks[b];
-  uint64_t w = st.word;
-  uint32_t bits = st.bits, count = st.count;
-  const uint64_t first = w;
-  const bool first_shared = bits > 0;  // part of the word came from the previous block
-  uint64_t buffer = 0;
-  auto put = [&](uint64_t word, uint64_t v) {
-    if (word == first && first_shared)
-      atomicOr(out + word, (unsigned long long)v);
-    else
-      out[word] = v;
-  };
-  auto step = [&](uint32_t sym) {
-    const uint32_t cl = __ldg(len + sym);
-    if (bits + cl > 64) {  // close the word
-      put(w, buffer);
-      sl[w] = (uint8_t)count;
-      ++w;
-      buffer = 0;
-      bits = 0;
-      count = 0;
+// k_enc_pack: one thread per packing block, Alg. 1 from the block's entry
+// state, branch-free per codeword (one table load gives code and length).  A
+// word that closes is staged in shared memory; after every 64 codewords the
+// warp writes its lanes' staged words out together, two lanes' words per
+// round (16 lanes each), so that a store instruction writes one lane's
+// consecutive words instead of one word of each of 32 streams.  The first
+// word of a block entered with bits already used is shared with the previous
+// block and goes out with a 64-bit atomicOr (the two parts' bits are
+// disjoint; the scan zeroed it), as does the word a block leaves open for the
+// next.  Each word's symbol count is written by the block that closes it.
+constexpr uint32_t kStageWords = 16;  // words that can close in 64 codewords (>= 4 codewords each: lmax <= 16)
+constexpr uint32_t kStagePitch = 17;  // per lane, padded against bank conflicts
+constexpr uint32_t kPackWarps = 4;
+
+struct PackLane {
+  const uint8_t *lv = nullptr;    // the block's levels
+  const uint32_t *tab = nullptr;  // code | length << 16 per level
+  uint64_t g0 = 0;                // index in p.words of the block's first word
+  uint32_t n = 0;                 // codewords of the block (0: no work)
+  uint32_t bits = 0, count = 0;   // Alg. 1's state
+  uint32_t wf = 0, ns = 0;        // words of the block written out; staged
+  uint64_t buffer = 0;            // the open word's codewords, left-aligned
+  bool shared_first = false;      // the block's first word holds bits of the previous block
+};
+
+template <bool FULL>
+__device__ __forceinline__ void pack_step64(PackLane &t, const uint4 (&v)[4], uint32_t i, unsigned long long *sw,
+                                            uint8_t *sc) {
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const uint32_t vw[4] = {v[q].x, v[q].y, v[q].z, v[q].w};
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      if (!FULL && i + 16 * q + j >= t.n) break;
+      const uint32_t e = __ldg(t.tab + ((vw[j >> 2] >> (8 * (j & 3))) & 0xffu));
+      const uint32_t cl = e >> 16;
+      const bool close = t.bits + cl > 64u;
+      if (close) {
+        sw[t.ns] = t.buffer;
+        sc[t.ns] = (uint8_t)t.count;
+      }
+      t.ns += close ? 1u : 0u;
+      t.bits = (close ? 0u : t.bits) + cl;
+      t.count = (close ? 0u : t.count) + 1u;
+      t.buffer = (close ? 0ull : t.buffer) | ((uint64_t)(e & 0xffffu) << (64u - t.bits));
     }
-    buffer |= (uint64_t)__ldg(code + sym) << (64 - bits - cl);
-    bits += cl;
-    ++count;
-  };
-  // 64 levels per step, the next 64 in flight
-  const uint8_t *const lvb = lv + i0;
-  const uint64_t nbk = i1 - i0;
+  }
+}
+
+__global__ void __launch_bounds__(kPackWarps * 32) k_enc_pack(EncParams p) {
+  __shared__ unsigned long long stage_w[kPackWarps][32 * kStagePitch];
+  __shared__ uint8_t stage_c[kPackWarps][32 * kStageWords];
+  __shared__ uint4 stage_i[kPackWarps][32];  // per lane: first staged word (index in p.words), count, shared flag
+  const uint32_t lane = threadIdx.x & 31u, wid = threadIdx.x >> 5;
+  unsigned long long *const sw = stage_w[wid] + lane * kStagePitch;
+  uint8_t *const sc = stage_c[wid] + lane * kStageWords;
+  const uint64_t b = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  PackLane t;
+  bool last = false;  // the block ends its stream
+  if (b < p.n_blocks) {
+    const uint32_t s = p.block_seg[b];
+    if (!p.seg_bad[s]) {
+      const EncSeg sg = p.segs[s];
+      const EncDomain d = p.doms[sg.domain];
+      const uint64_t L = sg.n_windows * d.E;
+      const uint64_t i0 = (b - sg.block_base) * kPackBlock;
+      t.n = (uint32_t)(L - i0 < kPackBlock ? L - i0 : kPackBlock);
+      t.lv = p.levels + sg.level_offset + i0;
+      t.tab = p.code_tab + d.code_off;
+      const PackState st = p.blocks[b];
+      t.g0 = sg.word_offset + st.word;
+      t.bits = st.bits;
+      t.count = st.count;
+      t.shared_first = st.bits > 0;
+      last = i0 + t.n == L;
+    }
+  }
+  const uint32_t nmax = __reduce_max_sync(0xffffffffu, t.n);
   uint4 v[4], vn[4];
-  load_raw64(lvb, 0, nbk, v);
-  for (uint64_t i = 0; i < nbk; i += 64) {
-    if (i + 64 < nbk) load_raw64(lvb, i + 64, nbk, vn);
+  if (t.n) load_raw64(t.lv, 0, t.n, v);
+  for (uint32_t i = 0; i < nmax; i += 64) {
+    if (i < t.n) {
+      if (i + 64 < t.n) load_raw64(t.lv, i + 64, t.n, vn);
+      if (i + 64 <= t.n)
+        pack_step64<true>(t, v, i, sw, sc);
+      else
+        pack_step64<false>(t, v, i, sw, sc);
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const uint64_t i16 = i + 16 * q;
-      if (i16 >= nbk) break;
-      const uint32_t vw[4] = {v[q].x, v[q].y, v[q].z, v[q].w};
-#pragma unroll
-      for (int j = 0; j < 16; ++j) {
-        if (i16 + j >= nbk) break;
-        step((vw[j >> 2] >> (8 * (j & 3))) & 0xffu);
+      for (int q = 0; q < 4; ++q) v[q] = vn[q];
+    }
+    // the warp writes its staged words: round r, half h writes lane 2 r + h's
+    stage_i[wid][lane] = make_uint4((uint32_t)(t.g0 + t.wf), (uint32_t)((t.g0 + t.wf) >> 32), t.ns,
+                                    t.shared_first && t.wf == 0u ? 1u : 0u);
+    __syncwarp();
+    const uint32_t h = lane >> 4, j = lane & 15u;
+#pragma unroll 4
+    for (uint32_t r = 0; r < 16; ++r) {
+      const uint32_t src = 2u * r + h;
+      const uint4 si = stage_i[wid][src];
+      if (j < si.z) {
+        const uint64_t g = ((uint64_t)si.y << 32 | si.x) + j;
+        const unsigned long long wv = stage_w[wid][src * kStagePitch + j];
+        if (j == 0 && si.w)
+          atomicOr(reinterpret_cast<unsigned long long *>(p.words) + g, wv);
+        else
+          p.words[g] = wv;
+        p.symlen[g] = stage_c[wid][src * kStageWords + j];
       }
     }
-#pragma unroll
-    for (int q = 0; q < 4; ++q) v[q] = vn[q];
+    __syncwarp();
+    t.wf += t.ns;
+    t.ns = 0;
   }
-  if (i1 == L) {  // the stream's last word
-    if (count > 0) {
-      put(w, buffer);
-      sl[w] = (uint8_t)count;
+  if (t.n) {
+    unsigned long long *const wp = reinterpret_cast<unsigned long long *>(p.words) + t.g0 + t.wf;
+    if (last) {  // the stream's last word
+      if (t.count > 0) {
+        if (t.wf == 0 && t.shared_first)
+          atomicOr(wp, (unsigned long long)t.buffer);
+        else
+          *wp = t.buffer;
+        p.symlen[t.g0 + t.wf] = (uint8_t)t.count;
+      }
+    } else {  // the open word continues in the next block (zeroed by the scan)
+      atomicOr(wp, (unsigned long long)t.buffer);
     }
-  } else {  // the open word continues in the next block (zeroed by the scan)
-    atomicOr(out + w, (unsigned long long)buffer);
   }
 }
 
@@ -920,8 +1146,10 @@ struct fptc_encoder {
   double *d_cos = nullptr;
   float *d_cosf = nullptr;
   PackState *d_blocks = nullptr;
-  unsigned long long *d_ref_map = nullptr;  // [n_blocks][kPackBlock / 64]
   RefEnd *d_ref_end = nullptr;              // [n_blocks]
+  BlockTrans *d_trans = nullptr;            // [n_blocks]
+  uint32_t *d_block_seg = nullptr;          // [n_blocks]
+  uint32_t *d_code_tab = nullptr;           // [n_domains][256]
   bool w32 = false;               // every domain N = 32, E = 16: the window-per-thread level kernel
   uint32_t *d_seg_bad = nullptr;
   unsigned long long *d_fb_list = nullptr;
@@ -943,8 +1171,10 @@ void enc_free(fptc_encoder *e) {
   cudaFree(e->d_cos);
   cudaFree(e->d_cosf);
   cudaFree(e->d_blocks);
-  cudaFree(e->d_ref_map);
   cudaFree(e->d_ref_end);
+  cudaFree(e->d_trans);
+  cudaFree(e->d_block_seg);
+  cudaFree(e->d_code_tab);
   cudaFree(e->d_seg_bad);
   cudaFree(e->d_fb_list);
   cudaFree(e->d_fb_count);
@@ -980,8 +1210,10 @@ EncParams enc_params(const fptc_encoder *e, uint64_t *d_words, uint8_t *d_symlen
   p.cosv = e->d_cos;
   p.cosf = e->d_cosf;
   p.blocks = e->d_blocks;
-  p.ref_map = e->d_ref_map;
   p.ref_end = e->d_ref_end;
+  p.trans = e->d_trans;
+  p.block_seg = e->d_block_seg;
+  p.code_tab = e->d_code_tab;
   p.seg_bad = e->d_seg_bad;
   p.fb_list = e->d_fb_list;
   p.fb_count = e->d_fb_count;
@@ -1018,6 +1250,7 @@ fptc_status fptc_encoder_create(fptc_encoder **enc, int device, const fptc_domai
     std::vector<double> cosv;
     std::vector<uint32_t> codes;
     std::vector<uint8_t> lens;
+    std::vector<uint32_t> code_tab;
     for (uint32_t d = 0; d < n_domains; ++d) {
       const fptc_domain &dm = domains[d];
       fptc_status st = fptc_validate_domain(&dm);
@@ -1061,6 +1294,7 @@ fptc_status fptc_encoder_create(fptc_encoder **enc, int device, const fptc_domai
       for (int s = 0; s < 256; ++s) {
         codes.push_back(c[s]);
         lens.push_back(dm.code_len[s]);
+        code_tab.push_back(c[s] | (uint32_t)dm.code_len[s] << 16);  // codes have <= lmax <= 16 bits
       }
     }
     // the same cosines as FP32 high and low parts, transposed per domain:
@@ -1080,6 +1314,7 @@ fptc_status fptc_encoder_create(fptc_encoder **enc, int device, const fptc_domai
     std::vector<EncSeg> segs(n_segments);
     std::vector<uint64_t> level_off(n_segments);
     std::vector<std::pair<uint64_t, uint64_t>> rooms;
+    std::vector<uint32_t> block_seg;
     uint64_t win = 0, lv = 0, blocks = 0;
     for (uint64_t i = 0; i < n_segments; ++i) {
       const fptc_segment &s = segments[i];
@@ -1101,7 +1336,9 @@ fptc_status fptc_encoder_create(fptc_encoder **enc, int device, const fptc_domai
       level_off[i] = lv;
       win += e.n_windows;
       lv += e.n_windows * dm.E;
-      blocks += (e.n_windows * dm.E + kPackBlock - 1) / kPackBlock;
+      const uint64_t nb = (e.n_windows * dm.E + kPackBlock - 1) / kPackBlock;
+      blocks += nb;
+      block_seg.insert(block_seg.end(), nb, (uint32_t)i);
       if (s.n_words) rooms.push_back({s.word_offset, s.word_offset + s.n_words});
     }
     std::sort(rooms.begin(), rooms.end());
@@ -1132,11 +1369,16 @@ fptc_status fptc_encoder_create(fptc_encoder **enc, int device, const fptc_domai
     if (err == cudaSuccess) err = enc_upload(&e->d_cos, cosv.data(), cosv.size());
     if (err == cudaSuccess) err = enc_upload(&e->d_cosf, cosf.data(), cosf.size());
     if (err == cudaSuccess) err = cudaMalloc(&e->d_blocks, std::max<uint64_t>(blocks, 1) * sizeof(PackState));
-    if (err == cudaSuccess)
-      err = cudaMalloc(&e->d_ref_map, std::max<uint64_t>(blocks, 1) * kRefWords * sizeof(unsigned long long));
     if (err == cudaSuccess) err = cudaMalloc(&e->d_ref_end, std::max<uint64_t>(blocks, 1) * sizeof(RefEnd));
+    if (err == cudaSuccess) err = cudaMalloc(&e->d_trans, std::max<uint64_t>(blocks, 1) * sizeof(BlockTrans));
+    if (err == cudaSuccess) err = enc_upload(&e->d_block_seg, block_seg.data(), block_seg.size());
+    if (err == cudaSuccess) err = enc_upload(&e->d_code_tab, code_tab.data(), code_tab.size());
     e->w32 = true;
     for (uint32_t d = 0; d < n_domains; ++d) e->w32 = e->w32 && domains[d].N == 32 && domains[d].E == 16;
+    // the window kernel's shared memory (two groups of rows per warp) fits five CTAs per SM
+    if (err == cudaSuccess && e->w32)
+      err = cudaFuncSetAttribute(k_enc_levels_w32, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared);
     if (err == cudaSuccess) err = cudaMalloc(&e->d_seg_bad, std::max<uint64_t>(n_segments, 1) * sizeof(uint32_t));
     // room for the bins decided in FP64: 0.2 % of them on signals, a few percent when
     // decoded signals are encoded again (their levels 127 and 129 reconstruct on the
@@ -1219,8 +1461,8 @@ static fptc_status enc_run(fptc_encoder *enc, const float *d_x, bool levels_give
     e = cudaMemsetAsync(enc->d_fb_count, 0, sizeof(unsigned int), s);
     if (e == cudaSuccess) {
       if (enc->w32)
-        k_enc_levels_w32<<<(unsigned)((enc->n_windows + kLvThreads - 1) / kLvThreads), kLvThreads, 0, s>>>(
-            p, enc->n_windows);
+        k_enc_levels_w32<<<(unsigned)((enc->n_windows + kLvThreads * kLvGroups - 1) / (kLvThreads * kLvGroups)),
+                           kLvThreads, 0, s>>>(p, enc->n_windows);
       else
         k_enc_levels<<<(unsigned)blocks, 256, 0, s>>>(p);
       e = cudaGetLastError();
@@ -1235,11 +1477,11 @@ static fptc_status enc_run(fptc_encoder *enc, const float *d_x, bool levels_give
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) {
-    k_enc_chain<<<(unsigned)((enc->n_segs * 32 + 127) / 128), 128, 0, s>>>(p);
+    k_enc_scan<<<(unsigned)((enc->n_segs * 32 + 127) / 128), 128, 0, s>>>(p);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess && enc->n_blocks) {
-    k_enc_pack<<<(unsigned)((enc->n_blocks + 127) / 128), 128, 0, s>>>(p);
+    k_enc_pack<<<(unsigned)((enc->n_blocks + kPackWarps * 32 - 1) / (kPackWarps * 32)), kPackWarps * 32, 0, s>>>(p);
     e = cudaGetLastError();
   }
   if (e != cudaSuccess) return enc_cuda_fail(e, "encode launch");

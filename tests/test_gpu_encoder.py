@@ -35,7 +35,7 @@ def _room_words(enc, words, symlen, n_words, i):
     return words[a:a + n], symlen[a:a + n]
 
 
-@pytest.mark.parametrize("case", ["trained", "one_bit", "max_length"])
+@pytest.mark.parametrize("case", ["trained", "one_bit", "max_length", "runs"])
 def test_pack_matches_oracle(case):
     from paper_2605_01086_gb300 import Encoder
     rng = np.random.default_rng(5)
@@ -47,6 +47,32 @@ def test_pack_matches_oracle(case):
         for S, di in zip(lens, idx):
             x = siggen.signal(di, int(siggen.stream_seed(7, len(levels))), S)
             levels.append(_oracle_stream(x, doms[di])[2] if S else np.zeros(0, np.uint8))
+    elif case == "runs":
+        # runs of one level (3- or 5-bit codes: a packing block of 4096 such
+        # codewords does not end on a word boundary, so a block entered in
+        # another state than its reference never meets it) between runs of
+        # mixed lengths (where they do meet): blocks packed again from the
+        # true state, then entered as assumed once more
+        cl = np.full(256, 12, np.uint8)
+        cl[128], cl[127], cl[129], cl[126], cl[130], cl[:8] = 1, 3, 3, 5, 5, 11
+        d = oracle.Domain(32, 16, 2, 16, 50.0, 0.004, (1.0, 1.0, 0.0), 12, cl)
+        doms = [d]
+        lens = [32 * 4096 * 5 + 96, 32 * 777, 32 * 4096 * 2]
+        idx = [0] * len(lens)
+        levels = []
+        for si, S in enumerate(lens):
+            W = d.windows(S) * d.E
+            L = np.empty(W, np.uint8)
+            i = 0
+            while i < W:
+                k = min(int(rng.integers(1, 3 * 4096)), W - i)
+                if si == 2 or rng.random() < 0.5:
+                    L[i:i + k] = 126 if si == 2 else rng.choice([127, 126, 129])
+                else:
+                    L[i:i + k] = rng.choice([126, 127, 128, 129, 130, 5, 200], size=k,
+                                            p=[.1, .2, .4, .15, .1, .03, .02])
+                i += k
+            levels.append(L)
     else:
         cl = np.zeros(256, np.uint8)
         if case == "one_bit":   # levels 0 and 128 with one-bit codes: 64 codewords per word
