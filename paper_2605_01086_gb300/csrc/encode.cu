@@ -58,8 +58,17 @@ struct EncDomain {
   float A0f, A1f, muf, d1f, inv_A0f, inv_span1f, inv_log1pmuf;
   double d1;             // alpha1 A1 as the FP64 quantizer computes it
   float slack0, slack1;  // per zone: an input width that covers the FP32 evaluation error
-  uint32_t on0, on1;     // A0 > 1e-30, A1 > 1e-30 (as the FP64 quantizer tests them): the zone is in use
+  uint32_t on0, on1;     // A0 > 1e-30; A1 > 1e-30 and A1 > d1 (as the FP64 quantizer tests them): the zone is in use
   float d1_hi, d1_lo;    // d1 as a float pair: d1_hi + d1_lo = d1 to 2^-48 d1
+  // zone 1 in units of the unscaled sum (c N / 2), for the window kernel's
+  // branch-free first tier: d1, A1, slack1 scaled by N / 2 (exactly, N = 32),
+  // and 126 / (A1 - d1), 127 / (A1 - d1) scaled by 2 / N
+  float u1_d1, u1_A1, u1_slack, u1_kp, u1_kn;
+  // zone 1's linear map may be evaluated in FP32 (A1 - d1 >= 2^-12 A1): the
+  // FP32 roundings of A1 and d1 (2^-24 A1 each) then move the map's top by at
+  // most 126 2^-23 / 2^-12 = 0.06 of a level; otherwise FP64 decides every
+  // zone-1 bin outside the deadzone
+  uint32_t z1_f32;
 };
 
 struct EncSeg {
@@ -120,6 +129,7 @@ struct EncParams {
   BlockTrans *trans;     // per packing block: Alg. 1 over it from the state its predecessor's reference ends in
   const uint32_t *block_seg;  // per packing block: its segment
   const uint32_t *code_tab;   // per domain, 256 entries: codeword | length << 16
+  const uint32_t *lv_seg;     // k_enc_levels_w32: the segment of each warp's first window
   uint32_t *seg_bad;
   unsigned long long *fb_list;   // bins whose level the FP64 coefficient decides
   unsigned int *fb_count;
@@ -178,7 +188,7 @@ __device__ __forceinline__ uint32_t zone0_level32(float c, const EncDomain &d) {
 // FP64 coefficient has to decide.
 __device__ __forceinline__ bool zone1_decide(float c, double cd, double err_d, float m, const EncDomain &d,
                                              uint32_t &L) {
-  if (!(d.A1 > 1e-30) || isnan(c)) {
+  if (!d.on1 || isnan(c)) {
     L = 128u;
     return true;
   }
@@ -187,7 +197,7 @@ __device__ __forceinline__ bool zone1_decide(float c, double cd, double err_d, f
     L = 128u;
     return true;
   }
-  if (ac - err_d <= d.d1) return false;  // at the deadzone edge
+  if (ac - err_d <= d.d1 || !d.z1_f32) return false;  // at the deadzone edge, or FP32 cannot map it
   const float a = fabsf(c);
   const float k = c > 0.0f ? 126.0f : 127.0f;
   const float r0 = fmaxf((fminf(a - m, d.A1f) - d.d1f) * d.inv_span1f, 0.0f);
@@ -215,7 +225,7 @@ __device__ __forceinline__ bool zone1_decide32(float c, float m, const EncDomain
     L = 128u;
     return true;
   }
-  if (a - m <= d.d1f) return false;  // at the deadzone edge
+  if (a - m <= d.d1f || !d.z1_f32) return false;  // at the deadzone edge, or FP32 cannot map it
   const float k = c > 0.0f ? 126.0f : 127.0f;
   const float r0 = fmaxf((fminf(a - m, d.A1f) - d.d1f) * d.inv_span1f, 0.0f);
   const float r1 = fmaxf((fminf(a + m, d.A1f) - d.d1f) * d.inv_span1f, 0.0f);
@@ -248,7 +258,7 @@ __device__ __forceinline__ bool zone1_decide_pair(float hi, float lo, float e, f
     L = 128u;
     return true;
   }
-  if (t - margin <= 0.0f) return false;  // at the deadzone edge: FP64 decides
+  if (t - margin <= 0.0f || !d.z1_f32) return false;  // at the deadzone edge, or FP32 cannot map it: FP64 decides
   const float ac = fabsf(c);
   const float k = c > 0.0f ? 126.0f : 127.0f;
   const float r0 = fmaxf((fminf(ac - m, d.A1f) - d.d1f) * d.inv_span1f, 0.0f);
@@ -408,6 +418,43 @@ __device__ __forceinline__ void tier1_bins(const float (&a)[16], const float (&e
   }
 }
 
+// The window kernel's first tier for Table 1's zones (B1 = 2, B2 = 16) when
+// the window's samples are finite (so are its bins) and zone 1 is in use:
+// bins 0 and 1 as in tier1_bins, bins 2 .. 15 branch-free in units of the
+// unscaled sum a = c N / 2 (every constant scaled by the power of two N / 2
+// = 16, so each comparison and rounding is the one zone1_decide32 makes on c,
+// up to the level map's FP32 evaluation, whose error, a few ulp of a level
+// index, is far inside the slack 2^-18 A1 that the bracket carries).
+__device__ __forceinline__ void tier1_bins_fast(const float (&a)[16], const float (&eb)[16], float err64,
+                                                const EncDomain &d, uint32_t (&lv)[4], uint32_t &undecided) {
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const float sc = k == 0 ? 4.0f / 32.0f : 2.0f / 32.0f;
+    const float c = a[k] * sc;
+    const float m = eb[k] * sc + err64 + d.slack0 + fabsf(c) * 0x1p-21f;
+    const uint32_t l0 = zone0_level32(c - m, d), l1 = zone0_level32(c + m, d);
+    undecided |= l0 == l1 ? 0u : 1u << k;
+    lv[0] |= (l0 == l1 ? l0 : 0u) << (8 * k);
+  }
+  const float base = err64 * 16.0f + d.u1_slack;  // err64 and slack1 in units of a
+#pragma unroll
+  for (int k = 2; k < 16; ++k) {
+    const float ak = fabsf(a[k]);
+    const float m = eb[k] + base + ak * 0x1p-21f;
+    const float lo = ak - m, hi = ak + m;
+    const bool dz = hi < d.u1_d1;              // settled: inside the deadzone
+    const bool edge = lo <= d.u1_d1;           // else the deadzone edge is inside the bracket
+    const bool pos = a[k] > 0.0f;
+    const float kk = pos ? d.u1_kp : d.u1_kn;
+    const int v0 = __float2int_rd(fmaf(fminf(lo, d.u1_A1) - d.u1_d1, kk, 0.5f));
+    const int v1 = __float2int_rd(fmaf(fminf(hi, d.u1_A1) - d.u1_d1, kk, 0.5f));
+    const bool und = !dz && (edge || v0 != v1);
+    const uint32_t L = dz ? 128u : (und ? 0u : (uint32_t)(pos ? 129 + v0 : 127 - v0));
+    undecided |= und ? 1u << k : 0u;
+    lv[k >> 2] |= L << (8 * (k & 3));
+  }
+}
+
 // Inclusive warp scan.
 __device__ __forceinline__ uint32_t lane_prefix(uint32_t v, uint32_t lane) {
 #pragma unroll
@@ -420,7 +467,7 @@ __device__ __forceinline__ uint32_t lane_prefix(uint32_t v, uint32_t lane) {
 
 constexpr uint32_t kLvThreads = 128;  // threads per CTA of k_enc_levels_w32 (4 warps)
 constexpr uint32_t kTier2Inline = 8;  // a warp with more undecided bins settles them itself
-constexpr uint32_t kLvGroups = 4;     // groups of 32 windows per warp, each loaded while the previous is computed
+constexpr uint32_t kLvGroups = 8;     // groups of 32 windows per warp, each loaded while the previous is computed
 constexpr uint32_t kRowPitch = 36;    // floats per window row in shared memory (144 bytes: 16-byte reads conflict-free)
 
 __device__ __forceinline__ uint32_t lds_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -494,14 +541,12 @@ __global__ void __launch_bounds__(kLvThreads, 5) k_enc_levels_w32(EncParams p, u
   __shared__ uint32_t segs_s[kLvThreads / 32][32];
   __shared__ float s1s[kLvThreads / 32][32];
   const uint32_t lane = threadIdx.x & 31u, wid = threadIdx.x >> 5;
-  const uint64_t first_group = ((uint64_t)blockIdx.x * (kLvThreads / 32) + wid) * kLvGroups;
-  // the segment: one search per CTA (its first window), then a step forward
-  // per window (a CTA's windows span few segments)
-  __shared__ uint32_t s_first;
-  if (threadIdx.x == 0)
-    s_first = (uint32_t)last_leq(p.n_segs, (uint64_t)blockIdx.x * (kLvThreads / 32) * kLvGroups * 32u * 16u,
-                                 [&](uint64_t i) { return p.segs[i].level_offset; });
-  __syncthreads();
+  const uint64_t chunk = (uint64_t)blockIdx.x * (kLvThreads / 32) + wid;
+  if (chunk * kLvGroups * 32u >= n_windows) return;  // the whole warp
+  const uint64_t first_group = chunk * kLvGroups;
+  // the segment of the warp's first window from a table, then a step forward
+  // per window (a warp's windows span few segments)
+  const uint64_t s_first = p.lv_seg[chunk];
   LvWin cur = lv_window(p, first_group * 32u + lane, n_windows, s_first);
   lv_load_async(p, cur, rows[wid][0] + lane * kRowPitch);
   cp_async_commit_group();
@@ -541,7 +586,9 @@ __global__ void __launch_bounds__(kLvThreads, 5) k_enc_levels_w32(EncParams p, u
     const float err64 = s1 * (2.0f / 32.0f) * 0x1p-40f + 1e-30f;
     uint32_t lv[4] = {0u, 0u, 0u, 0u};
     uint32_t undecided = 0;  // bins the butterfly's bound cannot settle
-    if (d.B1 == 2u && d.B2 == 16u)  // Table 1's zones: the zone of every bin known at compile time
+    if (d.B1 == 2u && d.B2 == 16u && d.z1_f32 && s1 <= 3.0e38f)  // Table 1's zones, finite bins
+      tier1_bins_fast(a, eb, err64, d, lv, undecided);
+    else if (d.B1 == 2u && d.B2 == 16u)  // the zone of every bin known at compile time
       tier1_bins<true>(a, eb, err64, d, lv, undecided);
     else
       tier1_bins<false>(a, eb, err64, d, lv, undecided);
@@ -1150,6 +1197,7 @@ struct fptc_encoder {
   BlockTrans *d_trans = nullptr;            // [n_blocks]
   uint32_t *d_block_seg = nullptr;          // [n_blocks]
   uint32_t *d_code_tab = nullptr;           // [n_domains][256]
+  uint32_t *d_lv_seg = nullptr;             // [warps of k_enc_levels_w32]
   bool w32 = false;               // every domain N = 32, E = 16: the window-per-thread level kernel
   uint32_t *d_seg_bad = nullptr;
   unsigned long long *d_fb_list = nullptr;
@@ -1175,6 +1223,7 @@ void enc_free(fptc_encoder *e) {
   cudaFree(e->d_trans);
   cudaFree(e->d_block_seg);
   cudaFree(e->d_code_tab);
+  cudaFree(e->d_lv_seg);
   cudaFree(e->d_seg_bad);
   cudaFree(e->d_fb_list);
   cudaFree(e->d_fb_count);
@@ -1214,6 +1263,7 @@ EncParams enc_params(const fptc_encoder *e, uint64_t *d_words, uint8_t *d_symlen
   p.trans = e->d_trans;
   p.block_seg = e->d_block_seg;
   p.code_tab = e->d_code_tab;
+  p.lv_seg = e->d_lv_seg;
   p.seg_bad = e->d_seg_bad;
   p.fb_list = e->d_fb_list;
   p.fb_count = e->d_fb_count;
@@ -1283,7 +1333,18 @@ fptc_status fptc_encoder_create(fptc_encoder **enc, int device, const fptc_domai
       x.d1_hi = (float)x.d1;
       x.d1_lo = (float)(x.d1 - (double)x.d1_hi);
       x.on0 = dm.scale[0] > 1e-30 ? 1u : 0u;
-      x.on1 = dm.scale[1] > 1e-30 ? 1u : 0u;
+      // zone 1 is in use when A1 > 1e-30 and its linear part is not empty: with
+      // alpha1 = 1 every |c| <= min(|c|, A1) <= d1, all level 128
+      x.on1 = dm.scale[1] > 1e-30 && dm.scale[1] - x.d1 > 0.0 ? 1u : 0u;
+      {
+        const double h = dm.N / 2.0, span = dm.scale[1] - x.d1;
+        x.u1_d1 = (float)(x.d1 * h);
+        x.u1_A1 = (float)(dm.scale[1] * h);
+        x.u1_slack = (float)(std::fabs(dm.scale[1]) * 0x1p-18 * h);
+        x.u1_kp = span > 0.0 ? (float)(126.0 / span / h) : 0.0f;
+        x.u1_kn = span > 0.0 ? (float)(127.0 / span / h) : 0.0f;
+        x.z1_f32 = x.on1 && span >= dm.scale[1] * 0x1p-12 ? 1u : 0u;
+      }
       x.cos_off = (uint32_t)cosv.size();
       for (uint32_t k = 0; k < dm.E; ++k)
         for (uint32_t n = 0; n < dm.N; ++n) cosv.push_back(std::cos(M_PI * (2.0 * n + 1.0) * k / (2.0 * dm.N)));
@@ -1375,10 +1436,17 @@ fptc_status fptc_encoder_create(fptc_encoder **enc, int device, const fptc_domai
     if (err == cudaSuccess) err = enc_upload(&e->d_code_tab, code_tab.data(), code_tab.size());
     e->w32 = true;
     for (uint32_t d = 0; d < n_domains; ++d) e->w32 = e->w32 && domains[d].N == 32 && domains[d].E == 16;
-    // the window kernel's shared memory (two groups of rows per warp) fits five CTAs per SM
-    if (err == cudaSuccess && e->w32)
-      err = cudaFuncSetAttribute(k_enc_levels_w32, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                 (int)cudaSharedmemCarveoutMaxShared);
+    if (err == cudaSuccess && e->w32) {  // the segment of each window kernel warp's first window
+      const uint64_t per = 32u * kLvGroups, n = (win + per - 1) / per;
+      std::vector<uint32_t> lvs(n);
+      uint64_t sidx = 0;
+      for (uint64_t c = 0; c < n; ++c) {
+        const uint64_t g = c * per * 16u;  // its first level (E = 16)
+        while (sidx + 1 < n_segments && segs[sidx + 1].level_offset <= g) ++sidx;
+        lvs[c] = (uint32_t)sidx;
+      }
+      err = enc_upload(&e->d_lv_seg, lvs.data(), lvs.size());
+    }
     if (err == cudaSuccess) err = cudaMalloc(&e->d_seg_bad, std::max<uint64_t>(n_segments, 1) * sizeof(uint32_t));
     // room for the bins decided in FP64: 0.2 % of them on signals, a few percent when
     // decoded signals are encoded again (their levels 127 and 129 reconstruct on the

@@ -187,3 +187,35 @@ def test_room_and_code_flags():
     enc2.pack(torch.from_numpy(lv).to(enc2.device))
     st, flags, first = enc2.status()
     assert st == _lib.CORRUPT_STREAM and flags & _lib.ENC_FLAG_NO_CODE and first == 0
+
+
+@pytest.mark.parametrize("alpha1", [1.0, 1.0 - 2.0 ** -20, 0.999, 0.3])
+def test_encode_zone1_narrow_linear_part(alpha1):
+    """Zone 1 with a linear part from empty (alpha1 = 1: every bin level 128) to
+    far narrower than the FP32 roundings of A1 and d1 can resolve, and A1 small
+    enough that many bins lie beyond it (the map's top): levels equal the FP64
+    host encoder's in every bin."""
+    from paper_2605_01086_gb300 import Encoder, codec
+    base = oracle_domains()[0]
+    A = (base.A[0], base.A[1] * 0.05, 0.0)
+    d = oracle.Domain(base.N, base.E, base.B1, base.B2, base.mu, alpha1, A, base.lmax, base.code_len.copy())
+    pd = product_domain(d)
+    wl = siggen.mixed_10000_logu(n=8, lo=1000, hi=40000)
+    flat, offs = siggen.signals(np.zeros(8, np.int64), wl.seeds, wl.lengths)
+    enc = Encoder([pd], wl.lengths, np.zeros(8, np.int64))
+    lv = torch.empty(max(1, enc.n_levels), dtype=torch.uint8, device=enc.device)
+    enc.encode(torch.from_numpy(flat).to(enc.device), levels=lv)
+    assert enc.status()[0] == 0
+    lh = lv.cpu().numpy()
+    beyond = 0
+    for i in range(8):
+        S = int(wl.lengths[i])
+        _, _, l_h = codec.encode_stream(pd, flat[int(offs[i]):int(offs[i]) + S])
+        l_g = lh[int(enc.level_offsets[i]):int(enc.level_offsets[i]) + l_h.size]
+        np.testing.assert_array_equal(l_g, l_h, err_msg=f"levels of stream {i}")
+        beyond += int(np.sum((l_h == 255) | (l_h == 0)))
+    if alpha1 < 1.0:
+        assert beyond > 0   # the map's top is reached
+    else:
+        z1 = lh[:enc.n_levels].reshape(-1, d.E)[:, d.B1:d.B2]
+        assert np.all(z1 == 128)
