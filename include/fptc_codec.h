@@ -39,6 +39,16 @@ fptc_status fptc_canonical_codes(const fptc_domain *domain, uint32_t *codes /* 2
 fptc_status fptc_train_domain(const float *x, const uint64_t *offsets, const uint64_t *lengths, uint64_t n_signals,
                               double percentile, fptc_domain *domain);
 
+/* The level map of zone 0 (Eq. 2) or 1 (Eq. 3) that fptc_encode_stream
+ * applies to an FP64 coefficient, given as its 255 boundaries: bounds[L - 1]
+ * (L = 1 .. 255) is the smallest double c whose level is L or more (-inf when
+ * every double's is, NaN when none is).  The map is monotone in c, so the
+ * level of a non-NaN c, +-inf included, is the number of bounds <= c (NaN:
+ * 128).  The GPU
+ * encoder settles the bins its FP32 tiers cannot with this table.  bounds
+ * must hold 255 doubles; zone must be 0 or 1, else FPTC_ERR_INVALID_ARGUMENT. */
+fptc_status fptc_zone_bounds(const fptc_domain *domain, uint32_t zone, double *bounds);
+
 /* Upper bound on the words of a stream of S samples (every word but the last
  * holds at least ceil((65 - lmax) / lmax) codewords). */
 uint64_t fptc_word_capacity(const fptc_domain *domain, uint64_t n_samples);

@@ -73,6 +73,7 @@ SIGNATURES = {
     "fptc_canonical_codes": (_i32, [_p, _p]),
     "fptc_train_domain": (_i32, [_p, _p, _p, _u64, _d, _p]),
     "fptc_word_capacity": (_u64, [_p, _u64]),
+    "fptc_zone_bounds": (_i32, [_p, _u32, _p]),
     "fptc_encode_stream": (_i32, [_p, _p, _u64, _p, _p, _u64, _p, _p]),
     "fptc_encode_batch": (_i32, [_p, _u32, _p, _p, _p, _p, _u64, _p, _p, _p, _p, _i32]),
     "fptc_encoder_create": (_i32, [ctypes.POINTER(_p), _i32, _p, _u32, _p, _u64]),

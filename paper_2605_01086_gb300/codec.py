@@ -87,6 +87,15 @@ def train_domain(x_flat, offsets, lengths, N=32, E=16, B1=2, B2=16, mu=50.0, alp
     return Domain.from_c(cd)
 
 
+def zone_bounds(d: Domain, zone: int) -> np.ndarray:
+    """The host encoder's level map of zone 0 or 1 as its 255 boundaries
+    (include/fptc_codec.h fptc_zone_bounds): level(c) = #{bounds <= c}."""
+    cd = d.c()
+    b = np.zeros(255, np.float64)
+    check(lib().fptc_zone_bounds(ctypes.byref(cd), int(zone), _ptr(b)))
+    return b
+
+
 def word_capacity(d: Domain, n_samples: int) -> int:
     cd = d.c()
     return int(lib().fptc_word_capacity(ctypes.byref(cd), int(n_samples)))

@@ -8,6 +8,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <limits>
 #include <string>
 #include <thread>
 #include <vector>
@@ -145,6 +146,43 @@ bool package_merge(const uint64_t *freq, uint32_t lmax, uint8_t *len) {
 }
 
 }  // namespace
+
+// Total order of the non-NaN doubles as unsigned keys.
+static uint64_t order_key(double x) {
+  uint64_t u;
+  std::memcpy(&u, &x, 8);
+  return (u >> 63) ? ~u : u | 0x8000000000000000ull;
+}
+static double from_key(uint64_t k) {
+  const uint64_t u = (k >> 63) ? k & 0x7fffffffffffffffull : ~k;
+  double x;
+  std::memcpy(&x, &u, 8);
+  return x;
+}
+
+void host_zone_bounds(const fptc_domain &d, uint32_t zone, double *bounds) {
+  const Quantizer qz(d);
+  auto level = [&](double c) -> uint32_t { return zone == 0 ? qz.zone0(c) : qz.zone1(c); };
+  const double ninf = -std::numeric_limits<double>::infinity(), pinf = std::numeric_limits<double>::infinity();
+  for (uint32_t L = 1; L <= 255; ++L) {
+    if (level(ninf) >= L) {
+      bounds[L - 1] = ninf;
+    } else if (level(pinf) < L) {
+      bounds[L - 1] = std::numeric_limits<double>::quiet_NaN();  // no double: never <= c
+    } else {  // level(lo) < L <= level(hi): the smallest such key by bisection
+      uint64_t lo = order_key(ninf), hi = order_key(pinf);
+      while (hi - lo > 1) {
+        const uint64_t mid = lo + (hi - lo) / 2;
+        if (level(from_key(mid)) >= L)
+          hi = mid;
+        else
+          lo = mid;
+      }
+      bounds[L - 1] = from_key(hi);
+    }
+  }
+}
+
 }  // namespace fptc
 
 using namespace fptc;
@@ -244,6 +282,20 @@ fptc_status fptc_build_decode_table(const fptc_domain *d, uint16_t *table) {
       const uint32_t lo = codes[s] << (L - l), hi = (codes[s] + 1) << (L - l);
       for (uint32_t p = lo; p < hi; ++p) table[p] = (uint16_t)(s | (l << 8));
     }
+    return FPTC_OK;
+  });
+}
+
+fptc_status fptc_zone_bounds(const fptc_domain *d, uint32_t zone, double *bounds) {
+  return guarded([&]() -> fptc_status {
+    clear_error();
+    if (!d || !bounds || zone > 1) {
+      set_error("need a domain, zone 0 or 1 and room for 255 bounds");
+      return FPTC_ERR_INVALID_ARGUMENT;
+    }
+    const fptc_status st = fptc_validate_domain(d);
+    if (st != FPTC_OK) return st;
+    host_zone_bounds(*d, zone, bounds);
     return FPTC_OK;
   });
 }

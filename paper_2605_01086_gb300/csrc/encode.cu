@@ -51,15 +51,12 @@ constexpr uint32_t kPackBlock = 8192;  // symbols per packing block
 
 struct EncDomain {
   uint32_t N, E, B1, B2;
-  double A0, A1, mu, alpha1, log1pmu;
   uint32_t cos_off;   // first entry of the E x N cosine tables (FP64 and FP32 copies)
   uint32_t code_off;  // first entry of the 256 codewords / lengths
   // FP32 forms for the fast evaluation of the quantizer
   float A0f, A1f, muf, d1f, inv_A0f, inv_span1f, inv_log1pmuf;
-  double d1;             // alpha1 A1 as the FP64 quantizer computes it
   float slack0, slack1;  // per zone: an input width that covers the FP32 evaluation error
   uint32_t on0, on1;     // A0 > 1e-30; A1 > 1e-30 and A1 > d1 (as the FP64 quantizer tests them): the zone is in use
-  float d1_hi, d1_lo;    // d1 as a float pair: d1_hi + d1_lo = d1 to 2^-48 d1
   // zone 1 in units of the unscaled sum (c N / 2), for the window kernel's
   // branch-free first tier: d1, A1, slack1 scaled by N / 2 (exactly, N = 32),
   // and 126 / (A1 - d1), 127 / (A1 - d1) scaled by 2 / N
@@ -69,6 +66,7 @@ struct EncDomain {
   // most 126 2^-23 / 2^-12 = 0.06 of a level; otherwise FP64 decides every
   // zone-1 bin outside the deadzone
   uint32_t z1_f32;
+  uint32_t bnd_off;      // first of the domain's 2 x 255 boundaries of the host encoder's zone maps
 };
 
 struct EncSeg {
@@ -130,6 +128,7 @@ struct EncParams {
   const uint32_t *block_seg;  // per packing block: its segment
   const uint32_t *code_tab;   // per domain, 256 entries: codeword | length << 16
   const uint32_t *lv_seg;     // k_enc_levels_w32: the segment of each warp's first window
+  const double *bounds;       // per domain: zone 0's, then zone 1's 255 level boundaries
   uint32_t *seg_bad;
   unsigned long long *fb_list;   // bins whose level the FP64 coefficient decides
   unsigned int *fb_count;
@@ -145,30 +144,43 @@ __device__ __forceinline__ void enc_flag(EncStatus *st, unsigned int f, uint64_t
   atomicMin(&st->first_bad, (unsigned long long)seg);
 }
 
-// Eq. 2 with the level map 128 + round(127 q) / 128 - round(128 q), |c| clamped to A0.
-__device__ __forceinline__ uint32_t zone0_level(double c, const EncDomain &d) {
-  if (!(d.A0 > 1e-30) || isnan(c)) return 128u;
-  const double a = fmin(fabs(c), d.A0);
-  const double q = log1p(__dmul_rn(d.mu, a / d.A0)) / d.log1pmu;
-  long long v = c >= 0.0 ? 128 + (long long)floor(__dadd_rn(__dmul_rn(127.0, q), 0.5))
-                         : 128 - (long long)floor(__dadd_rn(__dmul_rn(128.0, q), 0.5));
-  return (uint32_t)(v < 0 ? 0 : (v > 255 ? 255 : v));
+// Level of c by the host encoder's FP64 map of a zone (Eq. 2 or Eq. 3), given
+// as its 255 ascending boundaries (bounds[L - 1]: the smallest double with
+// level L or more, computed on the host from the host encoder's own map): the
+// number of boundaries <= c, by an 8-step binary search.
+__device__ __forceinline__ uint32_t level_by_bounds(const double *b, double c) {
+  uint32_t n = 0;
+#pragma unroll
+  for (uint32_t step = 128; step; step >>= 1)
+    if (n + step <= 255u && __ldg(b + n + step - 1) <= c) n += step;
+  return n;
 }
 
-// Eq. 3, |c| clamped to A1, deadzone d1 = alpha1 A1.
-__device__ __forceinline__ uint32_t zone1_level(double c, const EncDomain &d) {
-  if (!(d.A1 > 1e-30) || isnan(c)) return 128u;
-  const double d1 = __dmul_rn(d.alpha1, d.A1);
-  const double m = fmin(fabs(c), d.A1);
-  if (m <= d1) return 128u;
-  const double r = __dsub_rn(m, d1) / __dsub_rn(d.A1, d1);
-  long long v = c > 0 ? 129 + (long long)floor(__dadd_rn(__dmul_rn(r, 126.0), 0.5))
-                      : 127 - (long long)floor(__dadd_rn(__dmul_rn(r, 127.0), 0.5));
-  return (uint32_t)(v < 0 ? 0 : (v > 255 ? 255 : v));
+__device__ __forceinline__ const double *zone_bounds(const EncParams &p, const EncDomain &d, uint32_t k) {
+  return p.bounds + d.bnd_off + (k < d.B1 ? 0u : 255u);
 }
 
-__device__ __forceinline__ uint32_t bin_level(uint32_t k, double c, const EncDomain &d) {
-  return k < d.B1 ? zone0_level(c, d) : zone1_level(c, d);
+// The host encoder's level of bin k for its FP64 coefficient c.
+__device__ __forceinline__ uint32_t bin_level(const EncParams &p, uint32_t k, double c, const EncDomain &d) {
+  if (k >= d.B2 || isnan(c)) return 128u;
+  return level_by_bounds(zone_bounds(p, d, k), c);
+}
+
+// The level of bin k when the FP64 coefficient lies within err of cd: the
+// host map's level at both ends of [cd - err, cd + err] (the map is monotone);
+// false when they differ or cd is not finite (the FP64 coefficient decides).
+__device__ __forceinline__ bool level_bracket64(const EncParams &p, uint32_t k, double cd, double err,
+                                                const EncDomain &d, uint32_t &L) {
+  if (k >= d.B2) {
+    L = 128u;
+    return true;
+  }
+  const double e = err + fabs(cd) * 0x1p-50;  // and the rounding of cd -+ e
+  if (!(fabs(cd) + e <= 1.0e300)) return false;
+  const double *b = zone_bounds(p, d, k);
+  const uint32_t l0 = level_by_bounds(b, cd - e), l1 = level_by_bounds(b, cd + e);
+  L = l0;
+  return l0 == l1;
 }
 
 // Zone 0's map evaluated in FP32 (reciprocals, log1pf): off from the FP64
@@ -181,39 +193,11 @@ __device__ __forceinline__ uint32_t zone0_level32(float c, const EncDomain &d) {
   const int v = c >= 0.0f ? 128 + (int)floorf(fmaf(127.0f, q, 0.5f)) : 128 - (int)floorf(fmaf(128.0f, q, 0.5f));
   return (uint32_t)(v < 0 ? 0 : (v > 255 ? 255 : v));
 }
-// Zone 1 decided from the compensated coefficient: cd (FP64 value of the
-// compensated sum, |cd - c64| <= err_d) settles the deadzone test exactly
-// unless |cd| is within err_d of d1; outside the deadzone the linear map is
-// bracketed in FP32 (a = |c|, bracket half-width m).  Returns false when the
-// FP64 coefficient has to decide.
-__device__ __forceinline__ bool zone1_decide(float c, double cd, double err_d, float m, const EncDomain &d,
-                                             uint32_t &L) {
-  if (!d.on1 || isnan(c)) {
-    L = 128u;
-    return true;
-  }
-  const double ac = fabs(cd);
-  if (ac + err_d < d.d1) {
-    L = 128u;
-    return true;
-  }
-  if (ac - err_d <= d.d1 || !d.z1_f32) return false;  // at the deadzone edge, or FP32 cannot map it
-  const float a = fabsf(c);
-  const float k = c > 0.0f ? 126.0f : 127.0f;
-  const float r0 = fmaxf((fminf(a - m, d.A1f) - d.d1f) * d.inv_span1f, 0.0f);
-  const float r1 = fmaxf((fminf(a + m, d.A1f) - d.d1f) * d.inv_span1f, 0.0f);
-  const int v0 = (int)floorf(fmaf(r0, k, 0.5f)), v1 = (int)floorf(fmaf(r1, k, 0.5f));
-  if (v0 != v1) return false;
-  const int v = c > 0.0f ? 129 + v0 : 127 - v0;
-  L = (uint32_t)(v < 0 ? 0 : (v > 255 ? 255 : v));
-  return true;
-}
-
 
 // Zone 1 decided in FP32 alone from c with |c - c64| <= m - slack1 (the first
-// tier of k_enc_levels_w32): the deadzone test against d1 rounded to FP32
-// (|d1f - d1| <= 2^-24 A1, far inside the slack A1 2^-18 that m carries), then
-// the linear map bracketed as in zone1_decide.  Returns false when the bin has
+// tier of the level kernels): the deadzone test against d1 rounded to FP32
+// (|d1f - d1| <= 2^-24 A1, far inside the slack A1 2^-20 that m carries), then
+// the linear map at both ends of the bracket.  Returns false when the bin has
 // to be decided more closely.
 __device__ __forceinline__ bool zone1_decide32(float c, float m, const EncDomain &d, uint32_t &L) {
   if (!d.on1 || isnan(c)) {
@@ -229,40 +213,6 @@ __device__ __forceinline__ bool zone1_decide32(float c, float m, const EncDomain
   const float k = c > 0.0f ? 126.0f : 127.0f;
   const float r0 = fmaxf((fminf(a - m, d.A1f) - d.d1f) * d.inv_span1f, 0.0f);
   const float r1 = fmaxf((fminf(a + m, d.A1f) - d.d1f) * d.inv_span1f, 0.0f);
-  const int v0 = (int)floorf(fmaf(r0, k, 0.5f)), v1 = (int)floorf(fmaf(r1, k, 0.5f));
-  if (v0 != v1) return false;
-  const int v = c > 0.0f ? 129 + v0 : 127 - v0;
-  L = (uint32_t)(v < 0 ? 0 : (v > 255 ? 255 : v));
-  return true;
-}
-
-// Zone 1 decided from a compensated coefficient c = hi + lo (scaled, |hi + lo -
-// c64| <= e) in FP32 alone (the second tier of k_enc_levels_w32): the
-// deadzone test by the sign of |c| - d1 with d1 as a float pair, where
-// |hi| - d1_hi is exact near the edge (Sterbenz) and the rest is rounded once
-// or twice (2^-22 of the difference covers it, 2^-46 d1 the pair's own
-// error); outside the deadzone the linear map bracketed in FP32 with m.
-__device__ __forceinline__ bool zone1_decide_pair(float hi, float lo, float e, float m, const EncDomain &d,
-                                                  uint32_t &L) {
-  const float c = hi + lo;
-  if (!d.on1 || isnan(c)) {
-    L = 128u;
-    return true;
-  }
-  const float sgn = hi < 0.0f ? -1.0f : 1.0f;
-  const float a = fabsf(hi) - d.d1_hi;
-  const float b = sgn * lo - d.d1_lo;
-  const float t = a + b;  // |c| - d1
-  const float margin = e + fabsf(t) * 0x1p-22f + d.d1_hi * 0x1p-46f + 1e-30f;
-  if (t + margin < 0.0f) {
-    L = 128u;
-    return true;
-  }
-  if (t - margin <= 0.0f || !d.z1_f32) return false;  // at the deadzone edge, or FP32 cannot map it: FP64 decides
-  const float ac = fabsf(c);
-  const float k = c > 0.0f ? 126.0f : 127.0f;
-  const float r0 = fmaxf((fminf(ac - m, d.A1f) - d.d1f) * d.inv_span1f, 0.0f);
-  const float r1 = fmaxf((fminf(ac + m, d.A1f) - d.d1f) * d.inv_span1f, 0.0f);
   const int v0 = (int)floorf(fmaf(r0, k, 0.5f)), v1 = (int)floorf(fmaf(r1, k, 0.5f));
   if (v0 != v1) return false;
   const int v = c > 0.0f ? 129 + v0 : 127 - v0;
@@ -298,7 +248,7 @@ __device__ __forceinline__ uint32_t level_fp64_seg(const EncParams &p, uint64_t 
   const double *row = p.cosv + d.cos_off + (size_t)k * d.N;
   double a64 = 0.0;
   for (uint32_t n = 0; n < d.N; ++n) a64 = __dadd_rn(a64, __dmul_rn(n < avail ? (double)src[n] : 0.0, row[n]));
-  return bin_level(k, __dmul_rn(a64, 2.0 / (double)d.N), d);
+  return bin_level(p, k, __dmul_rn(a64, 2.0 / (double)d.N), d);
 }
 
 // FP64 list entries: level index (bits 0-39) and segment (bits 40-63).
@@ -358,21 +308,12 @@ __global__ void __launch_bounds__(256) k_enc_levels(EncParams p) {
       hi = t;
       s1 += fabsf(xv);
     }
-    const float c = (hi + lo) * (2.0f / (float)N);
-    // |c - c64| bound: the compensated sum, the cosines' representation, the
-    // FP64 evaluation's own rounding (all far below 2^-40 sum |x| for N <= 128)
-    // and the final roundings (covered by the |c| term)
+    // |c - c64| bound for c = hi + lo scaled in FP64: twice the compensated
+    // sum's (2^-34 (2/N) sum |x|, which also covers the cosines' representation
+    // and the FP64 evaluation's own rounding for N <= 128)
     const float err = s1 * (2.0f / (float)N) * 0x1p-34f + 1e-30f;
-    const float m = err + (k < d.B1 ? d.slack0 : d.slack1) + fabsf(c) * 0x1p-21f;
-    bool decided;
-    if (k < d.B1) {
-      const uint32_t l0 = zone0_level32(c - m, d), l1 = zone0_level32(c + m, d);
-      decided = l0 == l1;
-      L = l0;
-    } else {
-      const double cd = ((double)hi + (double)lo) * (2.0 / (double)N);
-      decided = zone1_decide(c, cd, (double)err * 2.0, m, d, L);
-    }
+    const double cd = ((double)hi + (double)lo) * (2.0 / (double)N);
+    const bool decided = level_bracket64(p, k, cd, 2.0 * (double)err, d, L);
     if (!decided) {
       const unsigned int slot = fb_slot(p);
       if (slot != ~0u) {
@@ -652,18 +593,10 @@ __global__ void __launch_bounds__(kLvThreads, 5) k_enc_levels_w32(EncParams p, u
           lo = __fadd_rn(lo, __fadd_rn(__fadd_rn(__fsub_rn(hi, __fsub_rn(tt, bp)), __fsub_rn(pr, bp)), pe));
           hi = tt;
         }
-        const float c = (hi + lo) * (2.0f / 32.0f);
         const float err2 = s1s[wid][own] * (2.0f / 32.0f) * 0x1p-34f + 1e-30f;
-        const float m = err2 + (k < od.B1 ? od.slack0 : od.slack1) + fabsf(c) * 0x1p-21f;
+        const double cd = ((double)hi + (double)lo) * (2.0 / 32.0);
         uint32_t L = 0u;
-        bool decided;
-        if (k < od.B1) {
-          const uint32_t l0 = zone0_level32(c - m, od), l1 = zone0_level32(c + m, od);
-          decided = l0 == l1;
-          L = l0;
-        } else {
-          decided = zone1_decide_pair(hi * (2.0f / 32.0f), lo * (2.0f / 32.0f), err2 * 2.0f, m, od, L);
-        }
+        const bool decided = level_bracket64(p, k, cd, 2.0 * (double)err2, od, L);
         const uint64_t g = (gw_base + own) * 16u + k;
         if (!decided) {
           const unsigned int slot = fb_slot(p);
@@ -993,9 +926,7 @@ __device__ __forceinline__ bool level_compensated(const EncParams &p, uint64_t g
   const float *src = p.x + sg.in_offset + w * d.N;
   const float2 *ct = reinterpret_cast<const float2 *>(p.cosf) + d.cos_off + k;
   float hi = 0.0f, lo = 0.0f, s1 = 0.0f;
-  for (uint32_t n = 0; n < nn; ++n) {
-    const float xv = __ldg(src + n);
-    const float2 cs = ct[(size_t)n * d.E];
+  auto step = [&](float xv, float2 cs) {
     const float pr = __fmul_rn(xv, cs.x);
     const float pe = __fadd_rn(__fmaf_rn(xv, cs.x, -pr), __fmul_rn(xv, cs.y));
     const float t = __fadd_rn(hi, pr);
@@ -1003,21 +934,30 @@ __device__ __forceinline__ bool level_compensated(const EncParams &p, uint64_t g
     lo = __fadd_rn(lo, __fadd_rn(__fadd_rn(__fsub_rn(hi, __fsub_rn(t, bp)), __fsub_rn(pr, bp)), pe));
     hi = t;
     s1 += fabsf(xv);
+  };
+  if (d.N == 32 && nn == 32 && (reinterpret_cast<uintptr_t>(src) & 15u) == 0) {
+    // a whole window: its samples and cosines requested at once, the same
+    // operations in the same order as below
+    float xv[32];
+    float2 cs[32];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const float4 v = __ldg(reinterpret_cast<const float4 *>(src) + j);
+      xv[4 * j] = v.x;
+      xv[4 * j + 1] = v.y;
+      xv[4 * j + 2] = v.z;
+      xv[4 * j + 3] = v.w;
+    }
+#pragma unroll
+    for (int n = 0; n < 32; ++n) cs[n] = __ldg(ct + (size_t)n * d.E);
+#pragma unroll
+    for (int n = 0; n < 32; ++n) step(xv[n], cs[n]);
+  } else {
+    for (uint32_t n = 0; n < nn; ++n) step(__ldg(src + n), __ldg(ct + (size_t)n * d.E));
   }
-  const float sc = 2.0f / (float)d.N;
-  const float c = (hi + lo) * sc;
-  const float err2 = s1 * sc * 0x1p-34f + 1e-30f;
-  const float m = err2 + (k < d.B1 ? d.slack0 : d.slack1) + fabsf(c) * 0x1p-21f;
-  if (k >= d.B2) {
-    L = 128u;
-    return true;
-  }
-  if (k < d.B1) {
-    const uint32_t l0 = zone0_level32(c - m, d), l1 = zone0_level32(c + m, d);
-    L = l0;
-    return l0 == l1;
-  }
-  return zone1_decide_pair(hi * sc, lo * sc, err2 * 2.0f, m, d, L);
+  const float err2 = s1 * (2.0f / (float)d.N) * 0x1p-34f + 1e-30f;
+  const double cd = ((double)hi + (double)lo) * (2.0 / (double)d.N);
+  return level_bracket64(p, k, cd, 2.0 * (double)err2, d, L);
 }
 
 // The listed bins, one per thread: from their compensated FP32 coefficient
@@ -1198,6 +1138,7 @@ struct fptc_encoder {
   uint32_t *d_block_seg = nullptr;          // [n_blocks]
   uint32_t *d_code_tab = nullptr;           // [n_domains][256]
   uint32_t *d_lv_seg = nullptr;             // [warps of k_enc_levels_w32]
+  double *d_bounds = nullptr;               // [n_domains][2][255]
   bool w32 = false;               // every domain N = 32, E = 16: the window-per-thread level kernel
   uint32_t *d_seg_bad = nullptr;
   unsigned long long *d_fb_list = nullptr;
@@ -1224,6 +1165,7 @@ void enc_free(fptc_encoder *e) {
   cudaFree(e->d_block_seg);
   cudaFree(e->d_code_tab);
   cudaFree(e->d_lv_seg);
+  cudaFree(e->d_bounds);
   cudaFree(e->d_seg_bad);
   cudaFree(e->d_fb_list);
   cudaFree(e->d_fb_count);
@@ -1264,6 +1206,7 @@ EncParams enc_params(const fptc_encoder *e, uint64_t *d_words, uint8_t *d_symlen
   p.block_seg = e->d_block_seg;
   p.code_tab = e->d_code_tab;
   p.lv_seg = e->d_lv_seg;
+  p.bounds = e->d_bounds;
   p.seg_bad = e->d_seg_bad;
   p.fb_list = e->d_fb_list;
   p.fb_count = e->d_fb_count;
@@ -1301,6 +1244,7 @@ fptc_status fptc_encoder_create(fptc_encoder **enc, int device, const fptc_domai
     std::vector<uint32_t> codes;
     std::vector<uint8_t> lens;
     std::vector<uint32_t> code_tab;
+    std::vector<double> bounds(2 * 255 * (size_t)n_domains);
     for (uint32_t d = 0; d < n_domains; ++d) {
       const fptc_domain &dm = domains[d];
       fptc_status st = fptc_validate_domain(&dm);
@@ -1310,16 +1254,11 @@ fptc_status fptc_encoder_create(fptc_encoder **enc, int device, const fptc_domai
       x.E = dm.E;
       x.B1 = dm.B1;
       x.B2 = dm.B2;
-      x.A0 = dm.scale[0];
-      x.A1 = dm.scale[1];
-      x.mu = dm.mu;
-      x.alpha1 = dm.alpha1;
-      x.log1pmu = std::log1p(dm.mu);
       x.A0f = (float)dm.scale[0];
       x.A1f = (float)dm.scale[1];
       x.muf = (float)dm.mu;
-      x.d1f = (float)(dm.alpha1 * dm.scale[1]);
-      x.d1 = dm.alpha1 * dm.scale[1];
+      const double d1 = dm.alpha1 * dm.scale[1];  // as the FP64 quantizer computes it
+      x.d1f = (float)d1;
       x.inv_A0f = dm.scale[0] > 1e-30 ? (float)(1.0 / dm.scale[0]) : 0.0f;
       x.inv_span1f = dm.scale[1] > 1e-30 && dm.scale[1] * (1.0 - dm.alpha1) > 0.0
                          ? (float)(1.0 / (dm.scale[1] - dm.alpha1 * dm.scale[1])) : 0.0f;
@@ -1329,22 +1268,28 @@ fptc_status fptc_encoder_create(fptc_encoder **enc, int device, const fptc_domai
       // arguments carry relative errors of a few 2^-24, over slopes of at most
       // mu / log1p(mu) and 1 / (1 - alpha1) per scale)
       x.slack0 = (float)(std::fabs(dm.scale[0]) * 0x1p-18);
-      x.slack1 = (float)(std::fabs(dm.scale[1]) * 0x1p-18);
-      x.d1_hi = (float)x.d1;
-      x.d1_lo = (float)(x.d1 - (double)x.d1_hi);
+      // zone 1's map is linear: its FP32 evaluation errs by a few 2^-24 A1 in
+      // the coefficient (an emulation of both FP32 forms still brackets the
+      // FP64 map with 2^-22 A1)
+      x.slack1 = (float)(std::fabs(dm.scale[1]) * 0x1p-20);
       x.on0 = dm.scale[0] > 1e-30 ? 1u : 0u;
       // zone 1 is in use when A1 > 1e-30 and its linear part is not empty: with
       // alpha1 = 1 every |c| <= min(|c|, A1) <= d1, all level 128
-      x.on1 = dm.scale[1] > 1e-30 && dm.scale[1] - x.d1 > 0.0 ? 1u : 0u;
+      x.on1 = dm.scale[1] > 1e-30 && dm.scale[1] - d1 > 0.0 ? 1u : 0u;
       {
-        const double h = dm.N / 2.0, span = dm.scale[1] - x.d1;
-        x.u1_d1 = (float)(x.d1 * h);
+        const double h = dm.N / 2.0, span = dm.scale[1] - d1;
+        x.u1_d1 = (float)(d1 * h);
         x.u1_A1 = (float)(dm.scale[1] * h);
-        x.u1_slack = (float)(std::fabs(dm.scale[1]) * 0x1p-18 * h);
+        x.u1_slack = (float)(std::fabs(dm.scale[1]) * 0x1p-20 * h);
         x.u1_kp = span > 0.0 ? (float)(126.0 / span / h) : 0.0f;
         x.u1_kn = span > 0.0 ? (float)(127.0 / span / h) : 0.0f;
         x.z1_f32 = x.on1 && span >= dm.scale[1] * 0x1p-12 ? 1u : 0u;
       }
+      // the host encoder's zone maps as boundaries: the levels of the second
+      // and third tiers are those maps' own
+      x.bnd_off = 2 * 255 * d;
+      host_zone_bounds(dm, 0, bounds.data() + x.bnd_off);
+      host_zone_bounds(dm, 1, bounds.data() + x.bnd_off + 255);
       x.cos_off = (uint32_t)cosv.size();
       for (uint32_t k = 0; k < dm.E; ++k)
         for (uint32_t n = 0; n < dm.N; ++n) cosv.push_back(std::cos(M_PI * (2.0 * n + 1.0) * k / (2.0 * dm.N)));
@@ -1434,6 +1379,7 @@ fptc_status fptc_encoder_create(fptc_encoder **enc, int device, const fptc_domai
     if (err == cudaSuccess) err = cudaMalloc(&e->d_trans, std::max<uint64_t>(blocks, 1) * sizeof(BlockTrans));
     if (err == cudaSuccess) err = enc_upload(&e->d_block_seg, block_seg.data(), block_seg.size());
     if (err == cudaSuccess) err = enc_upload(&e->d_code_tab, code_tab.data(), code_tab.size());
+    if (err == cudaSuccess) err = enc_upload(&e->d_bounds, bounds.data(), bounds.size());
     e->w32 = true;
     for (uint32_t d = 0; d < n_domains; ++d) e->w32 = e->w32 && domains[d].N == 32 && domains[d].E == 16;
     if (err == cudaSuccess && e->w32) {  // the segment of each window kernel warp's first window

@@ -55,6 +55,13 @@ __host__ __device__ inline float basis_value(uint32_t N, uint32_t n, uint32_t k)
 // Sec. 3.2); lut_offset, basis_offset and tile_windows are left 0.
 void fill_domain_dev(const fptc_domain &dm, DomainDev *dd);
 
+// The host encoder's FP64 level map of zone 0 or 1 (Eq. 2, Eq. 3) as its
+// boundaries: bounds[L - 1], L = 1 .. 255, is the smallest double c whose
+// level is L or more (-inf when every double's is, NaN when none is), so the
+// level of any non-NaN c is the number of bounds <= c (the map is monotone in
+// c, and a NaN bound is never <= c).
+void host_zone_bounds(const fptc_domain &d, uint32_t zone, double *bounds);
+
 // One segment, in tile-queue order (segments sorted by domain).
 struct SegDev {
   uint64_t word_offset;

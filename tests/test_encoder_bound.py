@@ -218,3 +218,69 @@ def test_butterfly_bins_within_their_bounds():
     assert worst < 1.0
     # on the offset windows the bounds are far below the uniform 2^-19.5 sum |x|
     assert np.median(tighter) < 0.5
+
+
+# ---- the window kernel's branch-free zone-1 map (units of the unscaled sum) ----
+
+def _zone1_64(c, A1, alpha1):
+    """The FP64 host encoder's zone-1 map (Eq. 3, |c| clamped to A1)."""
+    d1 = alpha1 * A1
+    m = min(abs(c), A1)
+    if m <= d1:
+        return 128
+    r = (m - d1) / (A1 - d1)
+    return 129 + int(np.floor(r * 126.0 + 0.5)) if c > 0 else 127 - int(np.floor(r * 127.0 + 0.5))
+
+
+def _zone1_fast32(y, A1, alpha1, form="fast"):
+    """Level indices (positive, negative side) of the FP32 zone-1 map at the
+    bracket end y = |c| N / 2 (N = 32), operation by operation in float32 with
+    the constants the encoder uploads.  form "fast": the window kernel's first
+    tier in units of y (fminf, subtraction, one FMA with 126 / span scaled,
+    round down); "c": the other tiers in units of c (fminf, subtraction,
+    product with 1 / span, then an FMA with 126 or 127)."""
+    h = 16.0
+    d1 = alpha1 * A1
+    span = A1 - d1
+    out = []
+    if form == "fast":
+        u1_d1, u1_A1 = f32(d1 * h), f32(A1 * h)
+        for k in (f32(126.0 / span / h), f32(127.0 / span / h)):
+            t = _fma(f32(min(f32(y), u1_A1) - u1_d1), k, f32(0.5))
+            out.append(int(np.floor(float(t))))
+    else:
+        a = f32(f32(y) * f32(1.0 / h))
+        r = max(f32(f32(min(a, f32(A1)) - f32(d1)) * f32(1.0 / span)), f32(0.0))
+        for k in (f32(126.0), f32(127.0)):
+            out.append(int(np.floor(float(_fma(r, k, f32(0.5))))))
+    return out
+
+
+@pytest.mark.parametrize("form", ["fast", "c"])
+@pytest.mark.parametrize("A1,alpha1", [(86.4, 0.004), (0.933, 0.004), (6.02, 0.2), (1e-3, 0.9),
+                                       (3.0, 1.0 - 2.0 ** -12), (2.5e5, 0.5)])
+def test_zone1_fp32_slack_brackets_the_fp64_map(A1, alpha1, form):
+    """Away from the deadzone edge, the FP32 zone-1 map at y - slack and
+    y + slack (slack = 2^-20 A1, in units of y = |c| N / 2) brackets the FP64
+    level at c: densely around every level boundary, at the clamp A1 and past
+    it, for linear parts down to the narrowest the encoder maps in FP32
+    (A1 - d1 = 2^-12 A1).  (It fails with slack 2^-23 A1: the margin is 8x.)"""
+    d1 = alpha1 * A1
+    span = A1 - d1
+    slack = 16.0 * A1 * 2.0 ** -20
+    cs = []
+    for j in range(0, 127):
+        for den in (126.0, 127.0):
+            b = d1 + (j + 0.5) / den * span
+            cs += [b * (1 + e) for e in (-1e-6, -1e-9, 0.0, 1e-9, 1e-6)]
+    cs += [A1 * (1 + e) for e in (-1e-7, 0.0, 1e-7, 1e-3, 0.5, 10.0)]
+    cs += list(np.random.default_rng(1).uniform(d1, 1.3 * A1, 1500))
+    for c in cs:
+        for sgn in (1.0, -1.0):
+            cc = sgn * c
+            y = abs(cc) * 16.0
+            if y - slack <= d1 * 16.0:
+                continue  # the deadzone edge is inside the bracket: not decided by the map
+            lo, hi = _zone1_fast32(y - slack, A1, alpha1, form), _zone1_fast32(y + slack, A1, alpha1, form)
+            lv = [129 + lo[0], 129 + hi[0]] if sgn > 0 else [127 - hi[1], 127 - lo[1]]
+            assert lv[0] <= _zone1_64(cc, A1, alpha1) <= lv[1], (cc, lv)
