@@ -34,6 +34,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <limits>
 #include <memory>
 #include <vector>
 
@@ -128,7 +129,7 @@ struct EncParams {
   const uint32_t *block_seg;  // per packing block: its segment
   const uint32_t *code_tab;   // per domain, 256 entries: codeword | length << 16
   const uint32_t *lv_seg;     // k_enc_levels_w32: the segment of each warp's first window
-  const double *bounds;       // per domain: zone 0's, then zone 1's 255 level boundaries
+  const long long *bound_keys;  // per domain: zone 0's, then zone 1's 255 level boundaries (order keys)
   uint32_t *seg_bad;
   unsigned long long *fb_list;   // bins whose level the FP64 coefficient decides
   unsigned int *fb_count;
@@ -144,41 +145,56 @@ __device__ __forceinline__ void enc_flag(EncStatus *st, unsigned int f, uint64_t
   atomicMin(&st->first_bad, (unsigned long long)seg);
 }
 
-// Level of c by the host encoder's FP64 map of a zone (Eq. 2 or Eq. 3), given
-// as its 255 ascending boundaries (bounds[L - 1]: the smallest double with
-// level L or more, computed on the host from the host encoder's own map): the
-// number of boundaries <= c, by an 8-step binary search.
-__device__ __forceinline__ uint32_t level_by_bounds(const double *b, double c) {
+// The host encoder's FP64 map of a zone (Eq. 2 or Eq. 3) is given as its 255
+// ascending boundaries (the smallest double with level L or more, L = 1 ..
+// 255, computed on the host from the host encoder's own map), stored as
+// order keys: signed 64-bit integers that order like the doubles (the
+// magnitude bits of a negative double flipped; a level no double reaches has
+// the largest key), so that comparisons run on the integer pipe.  The level
+// of a non-NaN c is the number of keys <= key(c).
+__device__ __forceinline__ long long order_key(double c) {
+  const long long b = __double_as_longlong(c);
+  return b < 0 ? b ^ 0x7fffffffffffffffll : b;
+}
+
+__device__ __forceinline__ uint32_t level_by_keys(const long long *kb, long long kc) {
   uint32_t n = 0;
 #pragma unroll
   for (uint32_t step = 128; step; step >>= 1)
-    if (n + step <= 255u && __ldg(b + n + step - 1) <= c) n += step;
+    if (n + step <= 255u && __ldg(kb + n + step - 1) <= kc) n += step;
   return n;
 }
 
-__device__ __forceinline__ const double *zone_bounds(const EncParams &p, const EncDomain &d, uint32_t k) {
-  return p.bounds + d.bnd_off + (k < d.B1 ? 0u : 255u);
+__device__ __forceinline__ const long long *zone_keys(const EncParams &p, const EncDomain &d, uint32_t k) {
+  return p.bound_keys + d.bnd_off + (k < d.B1 ? 0u : 255u);
 }
 
 // The host encoder's level of bin k for its FP64 coefficient c.
 __device__ __forceinline__ uint32_t bin_level(const EncParams &p, uint32_t k, double c, const EncDomain &d) {
   if (k >= d.B2 || isnan(c)) return 128u;
-  return level_by_bounds(zone_bounds(p, d, k), c);
+  return level_by_keys(zone_keys(p, d, k), order_key(c));
 }
 
-// The level of bin k when the FP64 coefficient lies within err of cd: the
-// host map's level at both ends of [cd - err, cd + err] (the map is monotone);
-// false when they differ or cd is not finite (the FP64 coefficient decides).
+// The level of bin k when the FP64 coefficient lies within err of cd: level
+// L0 (an estimate) when both ends of [cd - err, cd + err] lie between
+// boundaries L0 - 1 and L0 (two loads), else the map's level at both ends (the
+// map is monotone); false when those differ or cd is not finite (the FP64
+// coefficient decides).
 __device__ __forceinline__ bool level_bracket64(const EncParams &p, uint32_t k, double cd, double err,
-                                                const EncDomain &d, uint32_t &L) {
+                                                uint32_t L0, const EncDomain &d, uint32_t &L) {
   if (k >= d.B2) {
     L = 128u;
     return true;
   }
   const double e = err + fabs(cd) * 0x1p-50;  // and the rounding of cd -+ e
   if (!(fabs(cd) + e <= 1.0e300)) return false;
-  const double *b = zone_bounds(p, d, k);
-  const uint32_t l0 = level_by_bounds(b, cd - e), l1 = level_by_bounds(b, cd + e);
+  const long long *kb = zone_keys(p, d, k);
+  const long long lo = order_key(cd - e), hi = order_key(cd + e);
+  if ((L0 == 0u || __ldg(kb + L0 - 1) <= lo) && (L0 == 255u || hi < __ldg(kb + L0))) {
+    L = L0;
+    return true;
+  }
+  const uint32_t l0 = level_by_keys(kb, lo), l1 = level_by_keys(kb, hi);
   L = l0;
   return l0 == l1;
 }
@@ -191,6 +207,18 @@ __device__ __forceinline__ uint32_t zone0_level32(float c, const EncDomain &d) {
   const float a = fminf(fabsf(c), d.A0f);
   const float q = log1pf(d.muf * (a * d.inv_A0f)) * d.inv_log1pmuf;
   const int v = c >= 0.0f ? 128 + (int)floorf(fmaf(127.0f, q, 0.5f)) : 128 - (int)floorf(fmaf(128.0f, q, 0.5f));
+  return (uint32_t)(v < 0 ? 0 : (v > 255 ? 255 : v));
+}
+
+// A level near the FP32 coefficient c (the FP32 map at c; a start for
+// level_bracket64, which checks it).
+__device__ __forceinline__ uint32_t level_estimate(uint32_t k, float c, const EncDomain &d) {
+  if (k >= d.B2) return 128u;
+  if (k < d.B1) return zone0_level32(c, d);
+  const float a = fabsf(c);
+  if (!d.on1 || isnan(c) || a <= d.d1f) return 128u;
+  const float r = fminf((fminf(a, d.A1f) - d.d1f) * d.inv_span1f, 1.0f);
+  const int v = c > 0.0f ? 129 + (int)floorf(fmaf(r, 126.0f, 0.5f)) : 127 - (int)floorf(fmaf(r, 127.0f, 0.5f));
   return (uint32_t)(v < 0 ? 0 : (v > 255 ? 255 : v));
 }
 
@@ -313,7 +341,7 @@ __global__ void __launch_bounds__(256) k_enc_levels(EncParams p) {
     // and the FP64 evaluation's own rounding for N <= 128)
     const float err = s1 * (2.0f / (float)N) * 0x1p-34f + 1e-30f;
     const double cd = ((double)hi + (double)lo) * (2.0 / (double)N);
-    const bool decided = level_bracket64(p, k, cd, 2.0 * (double)err, d, L);
+    const bool decided = level_bracket64(p, k, cd, 2.0 * (double)err, level_estimate(k, (float)cd, d), d, L);
     if (!decided) {
       const unsigned int slot = fb_slot(p);
       if (slot != ~0u) {
@@ -596,7 +624,8 @@ __global__ void __launch_bounds__(kLvThreads, 5) k_enc_levels_w32(EncParams p, u
         const float err2 = s1s[wid][own] * (2.0f / 32.0f) * 0x1p-34f + 1e-30f;
         const double cd = ((double)hi + (double)lo) * (2.0 / 32.0);
         uint32_t L = 0u;
-        const bool decided = level_bracket64(p, k, cd, 2.0 * (double)err2, od, L);
+        const bool decided =
+            level_bracket64(p, k, cd, 2.0 * (double)err2, level_estimate(k, (float)cd, od), od, L);
         const uint64_t g = (gw_base + own) * 16u + k;
         if (!decided) {
           const unsigned int slot = fb_slot(p);
@@ -957,7 +986,7 @@ __device__ __forceinline__ bool level_compensated(const EncParams &p, uint64_t g
   }
   const float err2 = s1 * (2.0f / (float)d.N) * 0x1p-34f + 1e-30f;
   const double cd = ((double)hi + (double)lo) * (2.0 / (double)d.N);
-  return level_bracket64(p, k, cd, 2.0 * (double)err2, d, L);
+  return level_bracket64(p, k, cd, 2.0 * (double)err2, level_estimate(k, (float)cd, d), d, L);
 }
 
 // The listed bins, one per thread: from their compensated FP32 coefficient
@@ -1138,7 +1167,7 @@ struct fptc_encoder {
   uint32_t *d_block_seg = nullptr;          // [n_blocks]
   uint32_t *d_code_tab = nullptr;           // [n_domains][256]
   uint32_t *d_lv_seg = nullptr;             // [warps of k_enc_levels_w32]
-  double *d_bounds = nullptr;               // [n_domains][2][255]
+  long long *d_bound_keys = nullptr;        // [n_domains][2][255]
   bool w32 = false;               // every domain N = 32, E = 16: the window-per-thread level kernel
   uint32_t *d_seg_bad = nullptr;
   unsigned long long *d_fb_list = nullptr;
@@ -1165,7 +1194,7 @@ void enc_free(fptc_encoder *e) {
   cudaFree(e->d_block_seg);
   cudaFree(e->d_code_tab);
   cudaFree(e->d_lv_seg);
-  cudaFree(e->d_bounds);
+  cudaFree(e->d_bound_keys);
   cudaFree(e->d_seg_bad);
   cudaFree(e->d_fb_list);
   cudaFree(e->d_fb_count);
@@ -1206,7 +1235,7 @@ EncParams enc_params(const fptc_encoder *e, uint64_t *d_words, uint8_t *d_symlen
   p.block_seg = e->d_block_seg;
   p.code_tab = e->d_code_tab;
   p.lv_seg = e->d_lv_seg;
-  p.bounds = e->d_bounds;
+  p.bound_keys = e->d_bound_keys;
   p.seg_bad = e->d_seg_bad;
   p.fb_list = e->d_fb_list;
   p.fb_count = e->d_fb_count;
@@ -1245,6 +1274,7 @@ fptc_status fptc_encoder_create(fptc_encoder **enc, int device, const fptc_domai
     std::vector<uint8_t> lens;
     std::vector<uint32_t> code_tab;
     std::vector<double> bounds(2 * 255 * (size_t)n_domains);
+    std::vector<long long> bound_keys(bounds.size());
     for (uint32_t d = 0; d < n_domains; ++d) {
       const fptc_domain &dm = domains[d];
       fptc_status st = fptc_validate_domain(&dm);
@@ -1379,7 +1409,13 @@ fptc_status fptc_encoder_create(fptc_encoder **enc, int device, const fptc_domai
     if (err == cudaSuccess) err = cudaMalloc(&e->d_trans, std::max<uint64_t>(blocks, 1) * sizeof(BlockTrans));
     if (err == cudaSuccess) err = enc_upload(&e->d_block_seg, block_seg.data(), block_seg.size());
     if (err == cudaSuccess) err = enc_upload(&e->d_code_tab, code_tab.data(), code_tab.size());
-    if (err == cudaSuccess) err = enc_upload(&e->d_bounds, bounds.data(), bounds.size());
+    for (size_t i = 0; i < bounds.size(); ++i) {  // order keys (see order_key); a NaN bound: no level reached
+      long long b;
+      std::memcpy(&b, &bounds[i], 8);
+      bound_keys[i] = std::isnan(bounds[i]) ? std::numeric_limits<long long>::max()
+                                            : (b < 0 ? b ^ 0x7fffffffffffffffll : b);
+    }
+    if (err == cudaSuccess) err = enc_upload(&e->d_bound_keys, bound_keys.data(), bound_keys.size());
     e->w32 = true;
     for (uint32_t d = 0; d < n_domains; ++d) e->w32 = e->w32 && domains[d].N == 32 && domains[d].E == 16;
     if (err == cudaSuccess && e->w32) {  // the segment of each window kernel warp's first window
