@@ -186,9 +186,9 @@ def measured_peaks():
 
 
 KERNEL_SOURCES = {1: ["decode.cu"], 2: ["decode_fixed.cu"],
-                  3: ["decode_warp.cu", "warp_tile.cuh", "symlen_chunks.cuh"],
-                  4: ["decode_tc.cu", "warp_tile.cuh", "symlen_chunks.cuh"],
-                  5: ["backward_warp.cu", "warp_tile.cuh", "symlen_chunks.cuh"]}
+                  3: ["decode_warp.cu", "warp_tile.cuh", "symlen_chunks.cuh", "device_util.cuh"],
+                  4: ["decode_tc.cu", "tc_ops.cuh", "warp_tile.cuh", "symlen_chunks.cuh", "device_util.cuh"],
+                  5: ["backward_warp.cu", "dct32.cuh", "warp_tile.cuh", "symlen_chunks.cuh", "device_util.cuh"]}
 
 
 def _kernel_source_hash(kind: int):

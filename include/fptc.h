@@ -287,6 +287,18 @@ fptc_status fptc_plan_autotune(fptc_plan *plan, const uint64_t *d_words, const u
 fptc_status fptc_decode_stream_noalloc(const fptc_domain *domain, const uint64_t *d_words, const uint8_t *d_symlen,
                                        uint64_t n_words, uint64_t n_samples, float *d_out, fptc_stream stream);
 
+/* Runs, on its own, the bounded wait that every tensor-core and TMA
+ * completion wait of the decode kernels uses: one CTA on `device` waits on an
+ * mbarrier in its shared memory, sleeping between tests; the wait gives up
+ * after 1 s of GPU global time, and the kernel then sets FPTC_FLAG_TIMEOUT in
+ * a status word, as the decode kernels do in their plan status.  arrive != 0:
+ * one thread arrives on the barrier first (the wait completes, *flags = 0);
+ * arrive == 0: nothing arrives (*flags = FPTC_FLAG_TIMEOUT after about 1 s).
+ * Either way the kernel returns and the context stays usable.  Synchronous;
+ * allocates and frees 4 bytes of device memory.  Errors: NULL flags
+ * (FPTC_ERR_INVALID_ARGUMENT), CUDA errors (FPTC_ERR_CUDA). */
+fptc_status fptc_check_bounded_wait(int device, int arrive, uint32_t *flags);
+
 /* Kernel launches of one fptc_decode_batch call with the plan's current settings. */
 uint32_t fptc_plan_launches_per_decode(const fptc_plan *plan);
 

@@ -11,6 +11,6 @@ from ._lib import STAGE_DECODE, STAGE_INDEX, STAGE_LOSSLESS, STAGE_LOSSY, FptcEr
 from .build import build  # noqa: F401
 from .codec import (Batch, Domain, canonical_codes, decode_table, encode_batch, encode_stream,  # noqa: F401
                     packed_out_offsets, segments_array, train_domain, validate_domain, word_capacity)
-from .decoder import FPTCDecode, Plan, decode_differentiable  # noqa: F401
+from .decoder import FPTCDecode, Plan, check_bounded_wait, decode_differentiable  # noqa: F401
 from .encoder import Encoder  # noqa: F401
 from .tuning import fit_zone_scales  # noqa: F401

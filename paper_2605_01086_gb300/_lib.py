@@ -64,6 +64,7 @@ SIGNATURES = {
     "fptc_plan_device_status": (_i32, [_p, ctypes.POINTER(_u32), ctypes.POINTER(_u64)]),
     "fptc_plan_autotune": (_i32, [_p, _p, _p, _p, _u32, _p, _p, ctypes.POINTER(_f)]),
     "fptc_plan_launches_per_decode": (_u32, [_p]),
+    "fptc_check_bounded_wait": (_i32, [_i32, _i32, ctypes.POINTER(_u32)]),
     "fptc_struct_size": (_u64, [_u32]),
     "fptc_status_string": (ctypes.c_char_p, [_i32]),
     "fptc_last_error_message": (ctypes.c_char_p, []),

@@ -224,3 +224,12 @@ def decode_differentiable(plan: Plan, words, symlen, scale, coeff_probe=None):
     if coeff_probe is None:
         coeff_probe = torch.zeros(1, device=plan.device)
     return FPTCDecode.apply(scale, coeff_probe, plan, words, symlen)
+
+
+def check_bounded_wait(device: int = 0, arrive: bool = False) -> int:
+    """Runs the decode kernels' bounded completion wait on its own
+    (include/fptc.h fptc_check_bounded_wait); returns the status flags it set:
+    FLAG_TIMEOUT when nothing arrived (after about 1 s), 0 when it did."""
+    flags = ctypes.c_uint32(0)
+    check(lib().fptc_check_bounded_wait(int(device), 1 if arrive else 0, ctypes.byref(flags)))
+    return int(flags.value)
