@@ -686,7 +686,8 @@ def run_sweep(args):
     trend): 512 EEG-like signals of 65,536 samples per shape, tables trained per shape, encoded
     once and decoded as `--sweep-copies` copies of the batch (each copy its own words and output,
     4.3 GB of output per shape at 32 copies: far beyond L2, so every row is a fraction of the HBM
-    roofline), index + decode per step on the plan's default kernel."""
+    roofline), index + decode per step on the plan's default kernel; for E >= 32 also the
+    tensor-core forms of the transform."""
     import torch
 
     from paper_2605_01086_gb300 import Plan, codec
@@ -714,32 +715,45 @@ def run_sweep(args):
         segs = np.concatenate([codec.segments_array(sg["word_offset"] + np.uint64(r * n_w), sg["n_words"],
                                                     sg["n_samples"], sg["out_offset"] + np.uint64(r * out_one),
                                                     sg["domain"]) for r in range(R)])
-        plan = Plan([d], segs, device=0)
         w1 = torch.from_numpy(np.ascontiguousarray(b.words, np.uint64).view(np.int64)).to(dev)
         s1 = torch.from_numpy(np.ascontiguousarray(b.symlen, np.uint8)).to(dev)
         w, s = w1.repeat(R), s1.repeat(R)  # copy r of the streams at words r * n_w
         del w1, s1
-        out = plan.empty_out()
-        with torch.cuda.stream(stream):
-            plan.decode(w, s, out=out, stream=stream)
-            for _ in range(args.warmup):
-                plan.decode(w, s, out=out, stream=stream)
-            ms = time_steps(lambda: plan.decode(w, s, out=out, stream=stream), args.steps, stream, torch)
-        torch.cuda.synchronize()
-        x = flat.astype(np.float64)
-        xh = out[:n * S].double().cpu().numpy()
-        prd = 100.0 * float(np.sqrt(np.sum((x - xh) ** 2) / np.sum(x ** 2)))
-        same = bool(torch.equal(out[:out_one], out[(R - 1) * out_one:R * out_one]))
         out_b = 4 * n * S * R
         alg = out_b + 9 * int(sg["n_words"].sum()) * R
-        med = statistics.median(ms)
-        rows.append({"N": N, "E": E, "kernel": plan.info["kernel"], "ms": med,
-                     "GBps": out_b / (med / 1e3) / 1e9,
-                     "roofline_frac": alg / (med / 1e3) / 1e9 / peak,
-                     "compression_ratio": 4 * n * S / (9.0 * int(sg["n_words"].sum())), "prd_percent": prd,
-                     "copies_identical": same})
-        plan.close()
-        del w, s, out
+        ref = None
+        # the FP32 transform, and for E >= 32 the tensor-core forms
+        for idct in (["fp32"] + (["tf32x3", "bf16x3", "tf32"] if E >= 32 else [])):
+            try:
+                plan = Plan([d], segs, device=0, idct=idct)
+            except Exception:  # a shape the tensor-core kernel does not serve
+                continue
+            out = plan.empty_out()
+            with torch.cuda.stream(stream):
+                plan.decode(w, s, out=out, stream=stream)
+                for _ in range(args.warmup):
+                    plan.decode(w, s, out=out, stream=stream)
+                ms = time_steps(lambda: plan.decode(w, s, out=out, stream=stream), args.steps, stream, torch)
+            torch.cuda.synchronize()
+            x = flat.astype(np.float64)
+            xh = out[:n * S].double().cpu().numpy()
+            prd = 100.0 * float(np.sqrt(np.sum((x - xh) ** 2) / np.sum(x ** 2)))
+            same = bool(torch.equal(out[:out_one], out[(R - 1) * out_one:R * out_one]))
+            if ref is None:
+                ref = out[:out_one].clone()
+                rel = 0.0
+            else:
+                rel = float(torch.linalg.vector_norm((out[:out_one] - ref).double()) /
+                            torch.linalg.vector_norm(ref.double()))
+            med = statistics.median(ms)
+            rows.append({"N": N, "E": E, "idct": idct, "kernel": plan.info["kernel"], "threads": plan.info["threads"],
+                         "ms": med, "GBps": out_b / (med / 1e3) / 1e9,
+                         "roofline_frac": alg / (med / 1e3) / 1e9 / peak,
+                         "compression_ratio": 4 * n * S / (9.0 * int(sg["n_words"].sum())), "prd_percent": prd,
+                         "rel_l2_vs_fp32": rel, "copies_identical": same})
+            plan.close()
+            del out
+        del w, s, ref
     print(json.dumps({"sweep": f"N x E, {R} copies of 512 EEG-like signals x 65536 samples "
                                f"({4 * n * S * R / 1e9:.1f} GB out per shape), index + decode per step",
                       "unit": UNIT, "peak": peak, "peak_kind": peak_kind, "rows": rows}), flush=True)

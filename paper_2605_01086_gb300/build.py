@@ -15,7 +15,7 @@ LIB = os.path.join(PKG, "libfptc.so")
 
 CUDA_HOME = os.environ.get("CUDA_HOME", "/usr/local/cuda")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CU_SOURCES = ["index.cu", "decode.cu", "decode_fixed.cu", "decode_warp.cu", "decode_shape.cu", "decode_tc.cu", "backward.cu",
+CU_SOURCES = ["index.cu", "decode.cu", "decode_fixed.cu", "decode_warp.cu", "decode_shape.cu", "decode_tc.cu", "decode_tcs.cu", "backward.cu",
               "backward_warp.cu", "decode_paper.cu",
               "noalloc.cu", "encode.cu", "wait_check.cu"]
 CPP_SOURCES = ["plan.cpp", "codec_host.cpp"]

@@ -201,6 +201,19 @@ cudaError_t tc_occupancy(uint32_t mode, uint32_t threads, size_t smem, int *ctas
 cudaError_t tc_attributes(uint32_t mode, uint32_t threads, cudaFuncAttributes *attr);
 cudaError_t launch_tc(const DecodeParams &p, const WarpParams &wp, const TcParams &tp, const CUtensorMap &out_map,
                       uint32_t mode, uint32_t threads, uint32_t grid, size_t smem, cudaStream_t stream);
+// The tensor-core transform for shapes with E >= 32 (decode_tcs.cu): every domain the same
+// (N, E) in {(32, 32), (64, 32), (128, 32), (128, 64)}; tiles of kTS / E windows; threads
+// fixed per form and shape (tensor memory).
+bool tcs_supported(uint32_t N, uint32_t E);
+uint32_t tcs_tile_windows(uint32_t E);
+uint32_t tcs_threads(uint32_t mode, uint32_t N, uint32_t E);
+size_t tcs_smem_layout(uint32_t mode, uint32_t N, uint32_t E, const uint32_t *lmax, uint32_t n_domains,
+                       WarpParams *wp, TcParams *tp);
+cudaError_t tcs_smem_config(uint32_t mode, uint32_t N, uint32_t E, size_t smem);
+cudaError_t tcs_occupancy(uint32_t mode, uint32_t N, uint32_t E, size_t smem, int *ctas_per_sm);
+bool encode_out_map3(CUtensorMap *map, float *out, uint64_t extent, uint32_t N);
+cudaError_t launch_tcs(const DecodeParams &p, const WarpParams &wp, const TcParams &tp, const CUtensorMap &out_map,
+                       uint32_t mode, uint32_t N, uint32_t E, uint32_t grid, size_t smem, cudaStream_t stream);
 
 // warp-tile kernel for other shapes: a power-of-two N in [4, 128] for every
 // domain (several N in one plan), any E <= N (decode_shape.cu); tiles of

@@ -50,6 +50,7 @@ struct fptc_plan {
   int kind = FPTC_KERNEL_GENERIC;   // fptc_kernel in use
   bool shape = false;     // every domain has a power-of-two N in [4, 128] and the warp-tile kernel of
                           // decode_shape.cu serves the plan (N = 32, E = 16 plans use decode_warp.cu)
+  uint32_t tcs_N = 0, tcs_E = 0;  // the tensor-core kernel of decode_tcs.cu serves this shape (0: decode_tc.cu)
   WarpParams wp{};
   TcParams tp{};
   uint32_t threads = 256, grid = 0, ctas_per_sm = 0;
@@ -225,7 +226,9 @@ fptc_status configure_launch(fptc_plan *p) {
         }
     }
   }
-  const bool t_ok = shape ? (threads == 256 || threads == 512 || threads == 768)
+  if (p->kind == FPTC_KERNEL_TENSOR && p->tcs_N) threads = tcs_threads(p->opts.idct, p->tcs_N, p->tcs_E);
+  const bool t_ok = (p->kind == FPTC_KERNEL_TENSOR && p->tcs_N) ? threads > 0
+                    : shape ? (threads == 256 || threads == 512 || threads == 768)
                           : (threads == 128 || threads == 256 || threads == 512 ||
                              ((threads == 768 || threads == 1024) && p->kind == FPTC_KERNEL_WARP_TILE) ||
                              ((threads == 384 || threads == 640 || threads == 768) && p->kind == FPTC_KERNEL_TENSOR));
@@ -243,6 +246,20 @@ fptc_status configure_launch(fptc_plan *p) {
     e = fixed_smem_config(threads, p->smem);
     if (e != cudaSuccess) return cuda_fail(e, "decode shared-memory size");
     e = fixed_occupancy(threads, p->smem, &occ);
+  } else if (p->kind == FPTC_KERNEL_TENSOR && p->tcs_N) {
+    // the shape kernel: threads fixed by its form and shape (tensor memory), one CTA per SM
+    p->smem = tcs_smem_layout(p->opts.idct, p->tcs_N, p->tcs_E, lm.data(), (uint32_t)lm.size(), &p->wp, &p->tp);
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (p->smem > (size_t)optin) {
+      set_error("tensor-core kernel of shape N = %u, E = %u does not fit shared memory", p->tcs_N, p->tcs_E);
+      return FPTC_ERR_UNSUPPORTED;
+    }
+    e = tcs_smem_config(p->opts.idct, p->tcs_N, p->tcs_E, p->smem);
+    if (e != cudaSuccess) return cuda_fail(e, "decode shared-memory size");
+    e = tcs_occupancy(p->opts.idct, p->tcs_N, p->tcs_E, p->smem, &occ);
+    if (e == cudaSuccess) occ = std::min<int>(occ, 1);
   } else if (p->kind == FPTC_KERNEL_TENSOR) {
     if (p->opts.threads == 0) {
       // as many warpgroups as one CTA's shared memory allows (6 at most)
@@ -296,7 +313,7 @@ fptc_status configure_launch(fptc_plan *p) {
   const uint64_t full = (uint64_t)p->sm_count * p->ctas_per_sm;
   p->grid = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(full, p->n_tiles));
   // backward (the warp-tile adjoint serves N = 32, E = 16 plans)
-  if ((p->kind == FPTC_KERNEL_WARP_TILE && !shape) || p->kind == FPTC_KERNEL_TENSOR) {
+  if ((p->kind == FPTC_KERNEL_WARP_TILE && !shape) || (p->kind == FPTC_KERNEL_TENSOR && !p->tcs_N)) {
     // the warp-tile adjoint: 16 warps if their buffers fit, else 8
     int dev = 0, optin = 0;
     cudaGetDevice(&dev);
@@ -441,6 +458,13 @@ cudaError_t run_range(const fptc_plan *p, const IndexParams &ip0, const DecodePa
     if (p->shape) return launch_shape(dp, wp, map, p->threads, grid, p->smem, st);
     return launch_warp(dp, wp, map, p->threads, grid, p->smem, st);
   }
+  if (p->kind == FPTC_KERNEL_TENSOR && p->tcs_N) {
+    WarpParams wp = p->wp;
+    CUtensorMap map;
+    std::memset(&map, 0, sizeof(map));
+    wp.out_tma = encode_out_map3(&map, dp.out, p->out_extent, p->tcs_N) ? 1u : 0u;
+    return launch_tcs(dp, wp, p->tp, map, p->opts.idct, p->tcs_N, p->tcs_E, grid, p->smem, st);
+  }
   if (p->kind == FPTC_KERNEL_TENSOR) {
     WarpParams wp = p->wp;
     CUtensorMap map;
@@ -547,14 +571,22 @@ fptc_status fptc_plan_create(fptc_plan **out, int device, const fptc_domain *dom
                 "power-of-two N in [4, 128] in every domain (at most %u domains)", kWarpMaxDomains);
       return FPTC_ERR_UNSUPPORTED;
     }
+    // the tensor-core transform: N = 32, E = 16 in every domain (decode_tc.cu), or one
+    // shape with E >= 32 shared by every domain (decode_tcs.cu)
+    bool tcs_ok = !all_fixed && n_domains > 0 && n_domains <= kWarpMaxDomains &&
+                  tcs_supported(domains[0].N, domains[0].E);
+    for (uint32_t d = 1; d < n_domains && tcs_ok; ++d)
+      tcs_ok = domains[d].N == domains[0].N && domains[d].E == domains[0].E;
     if (o.idct != FPTC_IDCT_FP32 || o.kernel == FPTC_KERNEL_TENSOR) {
-      if (!fixed_ok || o.idct == FPTC_IDCT_FP32) {
-        set_error("the tensor-core transform needs N = 32, E = 16 in every domain (at most %u domains) and "
+      if (!(fixed_ok || tcs_ok) || o.idct == FPTC_IDCT_FP32) {
+        set_error("the tensor-core transform needs N = 32, E = 16 in every domain, or one shape (N, E) in "
+                  "{(32, 32), (64, 32), (128, 32), (128, 64)} shared by every domain (at most %u domains), and "
                   "idct = TF32, BF16X3 or TF32X3", kWarpMaxDomains);
         return FPTC_ERR_UNSUPPORTED;
       }
       o.kernel = FPTC_KERNEL_TENSOR;
     }
+    if (o.kernel != FPTC_KERNEL_TENSOR) tcs_ok = false;
     if (o.kernel == FPTC_KERNEL_AUTO) {
       // the warp-tile kernel keeps every domain's tables in shared memory: it is
       // the default when they fit beside at least four warps' buffers
@@ -579,7 +611,8 @@ fptc_status fptc_plan_create(fptc_plan **out, int device, const fptc_domain *dom
       o.kernel = fits ? FPTC_KERNEL_WARP_TILE : (all_fixed ? FPTC_KERNEL_BLOCK_TILE : FPTC_KERNEL_GENERIC);
     }
     if (o.kernel == FPTC_KERNEL_WARP_TILE) o.tile_samples = shape_ok ? 0 : warp_tile_windows() * 32;
-    if (o.kernel == FPTC_KERNEL_TENSOR) o.tile_samples = tc_tile_windows() * 32;
+    if (o.kernel == FPTC_KERNEL_TENSOR)
+      o.tile_samples = tcs_ok ? tcs_tile_windows(domains[0].E) * domains[0].N : tc_tile_windows() * 32;
     if (o.tile_samples == 0) o.tile_samples = o.kernel == FPTC_KERNEL_BLOCK_TILE ? 8192 : 4096;
     if (o.tile_samples > 65536) {
       set_error("tile_samples must be <= 65536");
@@ -664,6 +697,8 @@ fptc_status fptc_plan_create(fptc_plan **out, int device, const fptc_domain *dom
     p->lut_cap = 1u << max_lmax;
     p->kind = (int)o.kernel;
     p->shape = shape_ok;
+    p->tcs_N = tcs_ok ? domains[0].N : 0u;
+    p->tcs_E = tcs_ok ? domains[0].E : 0u;
 
     // ---- tile queue: segments ordered by output offset
     p->queue.resize(n_segments);
@@ -1049,7 +1084,9 @@ fptc_status fptc_plan_autotune(fptc_plan *p, const uint64_t *d_words, const uint
       uint32_t kernel, tile_samples, threads;
     };
     std::vector<Cand> cands;
-    if (keep.idct != FPTC_IDCT_FP32)
+    if (keep.idct != FPTC_IDCT_FP32 && p->tcs_N)  // the shape kernel: one configuration
+      cands.push_back({FPTC_KERNEL_TENSOR, tcs_tile_windows(p->tcs_E) * p->tcs_N, 0u});
+    else if (keep.idct != FPTC_IDCT_FP32)
       for (uint32_t th : {256u, 384u, 512u, 640u, 768u})
         cands.push_back({FPTC_KERNEL_TENSOR, tc_tile_windows() * 32, th});
     for (uint32_t th : {128u, 256u, 512u, 768u, 1024u}) {

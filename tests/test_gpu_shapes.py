@@ -141,3 +141,54 @@ def test_shape_chain_across_rejected_segment():
     st, flags, first = plan.device_status()
     assert st == _lib.CORRUPT_STREAM and flags & _lib.FLAG_SYMBOL_COUNT and first == bad
     compare_with_oracle(plan, b, out, lv, idx=[i for i in range(b.n_streams) if i != bad])
+
+
+TC_TOL = {"tf32": 1e-3, "bf16x3": 2e-5, "tf32x3": 1e-5}  # as for N = 32, E = 16 (tests/test_gpu_tc.py)
+
+
+@pytest.mark.parametrize("mode", ["tf32", "bf16x3", "tf32x3"])
+@pytest.mark.parametrize("N,E", [(32, 32), (64, 32), (128, 32), (128, 64)])
+@pytest.mark.parametrize("align", ["window", "odd"])
+def test_tensor_core_shapes(N, E, mode, align):
+    """The tensor-core transform for shapes with E >= 32 (decode_tcs.cu): two
+    domains of the same (N, E) with different scales and zone bounds (one with a
+    zone-2 bin), ragged lengths; outputs on window boundaries (3-D TMA stores of
+    whole steps) and at odd offsets (lane stores); levels bit-exact, samples
+    within the form's bound, nothing written outside the segments."""
+    b = _random_batch(N, [E, E], seed=N * 7 + E + len(mode))
+    plan = make_plan(b, out_align=N if align == "window" else 1, out_base=0 if align == "window" else 3, idct=mode)
+    assert plan.info["kernel"] == 4
+    _, _, out, lv = gpu_decode(plan, b, out_fill=float("nan"))
+    # TF32 bounds each sample's error by ~2^-10 sum_k |C_k B_kn|, not by the sample: a
+    # stream of a few samples whose sums cancel can exceed the stream-level bound
+    short = np.flatnonzero(b.lengths < 1024)
+    longer = np.flatnonzero(b.lengths >= 1024)
+    worst = compare_with_oracle(plan, b, out, lv, idx=longer, tol=TC_TOL[mode])
+    compare_with_oracle(plan, b, out, lv, idx=short, tol=TC_TOL[mode] * (50 if mode == "tf32" else 1))
+    h = out.cpu().numpy()
+    mask = np.ones(h.size, bool)
+    for sg in plan.segments:
+        mask[int(sg["out_offset"]):int(sg["out_offset"]) + int(sg["n_samples"])] = False
+    assert np.all(np.isnan(h[mask]))
+    assert plan.device_status()[0] == 0
+    print(N, E, mode, align, "worst rel L2", worst)
+
+
+def test_tensor_core_shape_trained_signals():
+    """(64, 32) on trained tables and EEG-like signals, against the FP32 kernel's output too."""
+    wl = siggen.Workload("tcs", 11, np.zeros(6, np.int32),
+                         np.array([siggen.stream_seed(11, i) for i in range(6)], np.uint64),
+                         np.array([64 * 1000 + 3, 65536, 1, 200000, 64 * 64, 12345], np.uint64))
+    ts = siggen.training_set(0)
+    flat, offs = siggen.signals(ts.domains, ts.seeds, ts.lengths)
+    dom = oracle.train_domain(flat, offs, ts.lengths, oracle.Domain(64, 32, 2, 32, 50.0, 0.004, (0.0, 0.0, 0.0), 12),
+                              99.9)
+    b = encode_workload(wl, domains=[dom])
+    plan = make_plan(b, out_align=64, idct="tf32x3")
+    assert plan.info["kernel"] == 4
+    _, _, out, lv = gpu_decode(plan, b)
+    compare_with_oracle(plan, b, out, lv, tol=TC_TOL["tf32x3"])
+    ref = make_plan(b, out_align=64, kernel="warp_tile")
+    _, _, out32, _ = gpu_decode(ref, b)
+    rel = float(torch.linalg.vector_norm((out - out32).double()) / torch.linalg.vector_norm(out32.double()))
+    assert rel < 1e-6
