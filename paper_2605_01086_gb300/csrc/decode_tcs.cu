@@ -12,7 +12,8 @@
 // M = 128, N samples, K = E, in the precision form's split) into the
 // warpgroup's D, and the lanes read their window's N samples back 32 at a
 // time (tcgen05.ld) and store them.  Two A sets per warpgroup (the next step's
-// rows are written while the product runs).  A window's 32-sample chunk c
+// rows are written while the product runs) where four warpgroups still fit the
+// 512 tensor-memory columns, else one (for more warpgroups).  A window's 32-sample chunk c
 // leaves by a 3-D TMA tensor store (the output viewed as [windows][N / 32][32]
 // floats: box 32 windows x 1 chunk x 32 floats, the staging tile's 128-byte
 // swizzle) when the segment's output starts on a window boundary of that view
@@ -33,14 +34,28 @@ template <int MODE, int E>
 __host__ __device__ constexpr uint32_t tcs_a_cols() {
   return MODE == FPTC_IDCT_TF32X3 ? 2u * E : (uint32_t)E;
 }
+// A sets per warpgroup: two (the next step's rows are written while the
+// product runs) unless one set lets more warpgroups fit the 512 tensor-memory
+// columns (then the rows are written after the previous product has
+// finished); at most 5 warpgroups (registers and shared memory per warp).
+constexpr uint32_t kTcsMaxWg = 5;
+template <int MODE, int N, int E>
+__host__ __device__ constexpr uint32_t tcs_nwg_for(uint32_t sets) {
+  return 512u / ((uint32_t)N + sets * tcs_a_cols<MODE, E>()) < kTcsMaxWg
+             ? 512u / ((uint32_t)N + sets * tcs_a_cols<MODE, E>())
+             : kTcsMaxWg;
+}
+template <int MODE, int N, int E>
+__host__ __device__ constexpr uint32_t tcs_asets() {
+  return tcs_nwg_for<MODE, N, E>(2u) >= tcs_nwg_for<MODE, N, E>(1u) ? 2u : 1u;
+}
 template <int MODE, int N, int E>
 __host__ __device__ constexpr uint32_t tcs_wg_cols() {
-  return (uint32_t)N + 2u * tcs_a_cols<MODE, E>();
+  return (uint32_t)N + tcs_asets<MODE, N, E>() * tcs_a_cols<MODE, E>();
 }
-// Warpgroups per CTA: as many as tensor memory holds, at most 4.
 template <int MODE, int N, int E>
 __host__ __device__ constexpr uint32_t tcs_nwg() {
-  return 512u / tcs_wg_cols<MODE, N, E>() >= 4u ? 4u : 512u / tcs_wg_cols<MODE, N, E>();
+  return tcs_nwg_for<MODE, N, E>(tcs_asets<MODE, N, E>());
 }
 // B operand bytes (the small / lo part follows the big / hi one).
 template <int MODE, int N, int E>
@@ -71,41 +86,36 @@ __device__ __forceinline__ void tcs_fill_b(unsigned char *b_base, const float *b
   }
 }
 
-// This lane's row of the A operand(s) from its window's E coefficients.
+// Bins 16 q .. 16 q + 15 of this lane's row of the A operand(s): TF32 (and
+// TF32X3's big part) at columns 16 q, TF32X3's small part at E + 16 q; BF16X3
+// hi pairs at columns 8 q, lo pairs at E / 2 + 8 q.
 template <int MODE, int E>
-__device__ __forceinline__ void tcs_put_a_row(uint32_t a, const float (&c)[E]) {
+__device__ __forceinline__ void tcs_put_a16(uint32_t a, uint32_t q, const float (&c)[16]) {
   if (MODE == FPTC_IDCT_BF16X3) {
+    uint32_t h[8], l[8];
 #pragma unroll
-    for (int g = 0; g < E / 32; ++g) {  // 16 columns of hi and of lo per 32 bins
-      uint32_t h[16], l[16];
-#pragma unroll
-      for (int j = 0; j < 16; ++j) {
-        const float x0 = c[32 * g + 2 * j], x1 = c[32 * g + 2 * j + 1];
-        h[j] = pack_bf16(x0, x1);
-        const float h0 = __uint_as_float(h[j] << 16), h1 = __uint_as_float(h[j] & 0xffff0000u);
-        l[j] = pack_bf16(x0 - h0, x1 - h1);
-      }
-      tmem_st16(a + 16u * g, h);
-      tmem_st16(a + E / 2 + 16u * g, l);
+    for (int j = 0; j < 8; ++j) {
+      const float x0 = c[2 * j], x1 = c[2 * j + 1];
+      h[j] = pack_bf16(x0, x1);
+      const float h0 = __uint_as_float(h[j] << 16), h1 = __uint_as_float(h[j] & 0xffff0000u);
+      l[j] = pack_bf16(x0 - h0, x1 - h1);
     }
+    tmem_st8(a + 8u * q, h);
+    tmem_st8(a + E / 2 + 8u * q, l);
   } else {
+    uint32_t big[16], sm[16];
 #pragma unroll
-    for (int g = 0; g < E / 16; ++g) {
-      uint32_t big[16], sm[16];
-#pragma unroll
-      for (int j = 0; j < 16; ++j) {
-        const float x = c[16 * g + j];
-        if (MODE == FPTC_IDCT_TF32X3) {
-          // big = x with its 13 low mantissa bits cleared (a TF32 value), small = x - big exactly
-          big[j] = __float_as_uint(x) & 0xFFFFE000u;
-          sm[j] = __float_as_uint(x - __uint_as_float(big[j]));
-        } else {
-          big[j] = __float_as_uint(tf32_round(x));
-        }
+    for (int j = 0; j < 16; ++j) {
+      if (MODE == FPTC_IDCT_TF32X3) {
+        // big = c with its 13 low mantissa bits cleared (a TF32 value), small = c - big exactly
+        big[j] = __float_as_uint(c[j]) & 0xFFFFE000u;
+        sm[j] = __float_as_uint(c[j] - __uint_as_float(big[j]));
+      } else {
+        big[j] = __float_as_uint(tf32_round(c[j]));
       }
-      tmem_st16(a + 16u * g, big);
-      if (MODE == FPTC_IDCT_TF32X3) tmem_st16(a + E + 16u * g, sm);
     }
+    tmem_st16(a + 16u * q, big);
+    if (MODE == FPTC_IDCT_TF32X3) tmem_st16(a + E + 16u * q, sm);
   }
 }
 
@@ -327,38 +337,47 @@ __global__ void __launch_bounds__(tcs_nwg<MODE, N, E>() * 128, 1)
     // window index of the tile's first window in the output view [windows][N / 32][32]
     const int64_t vwin = (wp.out_tma && sg.out_offset % N == 0) ? (int64_t)(sg.out_offset / N + win0) : -1;
     for (uint32_t w0 = 0; w0 < T; w0 += 32) {
-      const uint32_t a_set = a_tmem + (uint32_t)(k & 1) * tcs_a_cols<MODE, E>();
+      constexpr uint32_t AS = tcs_asets<MODE, N, E>();
+      const uint32_t a_set = a_tmem + (AS == 2u ? (uint32_t)(k & 1) * tcs_a_cols<MODE, E>() : 0u);
       const uint32_t wi = w0 + lane;
-      float c[E];
-      if (wi < nwin) {
-        const uint4 *sv = reinterpret_cast<const uint4 *>(stage + wi * E);
+      // this lane's window: E coefficients dequantized and written 16 at a time
+      auto put_row = [&]() {
 #pragma unroll
-        for (int q = 0; q < E / 16; ++q) {
-          const uint4 u = sv[q];
-          const uint32_t sw[4] = {u.x, u.y, u.z, u.w};
+        for (uint32_t q = 0; q < (uint32_t)E / 16; ++q) {
+          float c[16];
+          if (wi < nwin) {
+            const uint4 u = reinterpret_cast<const uint4 *>(stage + wi * E)[q];
+            const uint32_t sw[4] = {u.x, u.y, u.z, u.w};
 #pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            const uint32_t kb = 16u * q + j;
-            const uint32_t z = kb < B1 ? 0u : (kb < B2 ? 1u : 2u);
-            c[kb] = deq[z * kZStride + ((sw[j >> 2] >> (8 * (j & 3))) & 0xffu)];
-          }
-          if (lev) {
-            uint8_t *dl = lev + wi * E + 16 * q;
-            if ((reinterpret_cast<uintptr_t>(dl) & 15u) == 0) {
-              *reinterpret_cast<uint4 *>(dl) = u;
-            } else {
-#pragma unroll
-              for (int j = 0; j < 16; ++j) dl[j] = (uint8_t)(sw[j >> 2] >> (8 * (j & 3)));
+            for (int j = 0; j < 16; ++j) {
+              const uint32_t kb = 16u * q + j;
+              const uint32_t z = kb < B1 ? 0u : (kb < B2 ? 1u : 2u);
+              c[j] = deq[z * kZStride + ((sw[j >> 2] >> (8 * (j & 3))) & 0xffu)];
             }
-          }
-        }
-      } else {
+            if (lev) {
+              uint8_t *dl = lev + wi * E + 16 * q;
+              if ((reinterpret_cast<uintptr_t>(dl) & 15u) == 0) {
+                *reinterpret_cast<uint4 *>(dl) = u;
+              } else {
 #pragma unroll
-        for (int j = 0; j < E; ++j) c[j] = 0.0f;
+                for (int j = 0; j < 16; ++j) dl[j] = (uint8_t)(sw[j >> 2] >> (8 * (j & 3)));
+              }
+            }
+          } else {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) c[j] = 0.0f;
+          }
+          tcs_put_a16<MODE, E>(a_set + lane_off, q, c);
+        }
+        tmem_wait_st();
+      };
+      if (AS == 2u) {
+        put_row();                  // product k - 1 reads the other A set
+        if (k > 0) drain(prev);     // D is free for product k once every warp has read it
+      } else {
+        if (k > 0) drain(prev);     // product k - 1 has read A and D is read back
+        put_row();
       }
-      tcs_put_a_row<MODE, E>(a_set + lane_off, c);  // product k - 1 reads the other A set
-      tmem_wait_st();
-      if (k > 0) drain(prev);                      // D is free for product k once every warp has read it
       tc_fence_before();
       if (wg_barrier_any(wg, timeout)) {
         stop = true;
