@@ -109,14 +109,17 @@ typedef enum fptc_schedule {
 } fptc_schedule;
 
 typedef enum fptc_kernel {
-  FPTC_KERNEL_AUTO = 0,        /* warp-tile if every domain has N = 32, E = 16, or a power-of-two N in
-                                  [4, 128] (and their tables fit), else generic */
+  FPTC_KERNEL_AUTO = 0,        /* warp-tile if every domain has N in [4, 128] (and their tables fit),
+                                  else generic */
   FPTC_KERNEL_GENERIC = 1,     /* any N, E: one block per tile, basis through L1 */
   FPTC_KERNEL_BLOCK_TILE = 2,  /* N = 32, E = 16: one block per tile, pipelined */
   FPTC_KERNEL_WARP_TILE = 3,   /* one warp per tile, no block barriers: N = 32, E = 16 (128-window tiles),
-                                  or a power-of-two N in [4, 128] in every domain (several N in one
-                                  batch), any E <= N (tiles of about 2048 symbols); at most 8 domains */
-  FPTC_KERNEL_TENSOR = 4       /* N = 32, E = 16, tensor-core transform; chosen by idct != FPTC_IDCT_FP32 */
+                                  or any N in [4, 128] in every domain (several N in one batch; N not a
+                                  power of two stores with the lanes instead of TMA), any E <= N (tiles
+                                  of about 2048 symbols); at most 8 domains */
+  FPTC_KERNEL_TENSOR = 4       /* tensor-core transform, chosen by idct != FPTC_IDCT_FP32: N = 32, E = 16
+                                  in every domain, or one (N, E) in {(32, 32), (64, 32), (128, 32),
+                                  (128, 64)} shared by every domain */
 } fptc_kernel;
 
 typedef struct fptc_plan_options {

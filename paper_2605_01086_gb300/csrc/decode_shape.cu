@@ -1,8 +1,9 @@
 // Fused decode for window shapes other than the Table 1 default: every domain of
-// the plan has a power-of-two window size N in [4, 128] and any kept-bin count
-// E <= N, domains of different N in one batch (Table 1 gives the ranges; Fig. 14
+// the plan has a window size N in [4, 128] and any kept-bin count E <= N,
+// domains of different N in one batch (Table 1 gives the ranges; Fig. 14
 // measures how the throughput moves with them).  The transform is compiled per
-// N and chosen per tile from the tile's domain (a warp-uniform switch).
+// power-of-two N and chosen per tile from the tile's domain (a warp-uniform
+// switch); other N take a run-time-N version (shape_transform_any).
 //
 // The SymLen decode, tile chaining, level staging and TMA output path are those
 // of the warp-tile kernel (warp_tile.cuh), with tiles of T windows per domain
@@ -52,15 +53,24 @@ struct ShapeK {
   static_assert(M * P == 16, "16 pairs per lane");
 };
 
+__host__ __device__ constexpr bool shape_pow2(uint32_t N) { return (N & (N - 1)) == 0; }
+// Other N: the ceil(N / 2) sample pairs of a window in groups of 16, one lane per group.
+__host__ __device__ constexpr uint32_t shape_any_pairs(uint32_t N) { return (N + 1) / 2; }
+__host__ __device__ constexpr uint32_t shape_any_lanes(uint32_t N) { return (shape_any_pairs(N) + 15) / 16; }
+// Windows per output step for other N: one lane group each, at most 1024 samples.
+__host__ __device__ constexpr uint32_t shape_any_step(uint32_t N) {
+  return 32 / shape_any_lanes(N) < 1024 / N ? 32 / shape_any_lanes(N) : 1024 / N;
+}
+
 __host__ __device__ constexpr uint32_t shape_brow(uint32_t N) {
-  return N >= 32 ? N / 32 * 20 : (N / 2 + 3) / 4 * 4;
+  return !shape_pow2(N) ? shape_any_lanes(N) * 20 : N >= 32 ? N / 32 * 20 : (N / 2 + 3) / 4 * 4;
 }
 
 // Windows per tile for a domain of the shape kernel: whole steps of 1024
 // samples, at most 2048 symbols (the level staging buffer) and at most 8 steps
 // (8192 samples: the dL/dx tile of the block adjoint fits shared memory).
 __host__ __device__ constexpr uint32_t shape_tile_windows(uint32_t N, uint32_t E) {
-  const uint32_t r = 1024 / N;
+  const uint32_t r = shape_pow2(N) ? 1024 / N : shape_any_step(N);
   uint32_t t = (uint32_t)kTS / E / r * r;
   if (t > 8 * r) t = 8 * r;
   return t ? t : r;
@@ -110,13 +120,16 @@ __device__ __forceinline__ uint32_t load_shape_tables(const DecodeParams &p, uin
       const uint32_t z = i / kZStride, L = i - z * kZStride;
       deq[i] = (L < 256u && z < 2u) ? (z == 0 ? a0 : a1) * dm.unit[z][L] : 0.0f;
     }
-    // the half basis B[k][n], n < N / 2: rows of brow floats, N >= 32 in groups of 16 (+ 4 pad)
+    // the half basis B[k][n], n < ceil(N / 2): rows of brow floats, in groups of 16 (+ 4
+    // pad) for N >= 32 and for N not a power of two
     float *bas = reinterpret_cast<float *>(smem + basis_off);
     const float *g_bas = p.basis + dm.basis_offset;
+    const bool grouped = N >= 32 || !shape_pow2(N);
+    const uint32_t pairs = shape_any_pairs(N);
     for (uint32_t i = threadIdx.x; i < dm.E * brow; i += THREADS) {
       const uint32_t k = i / brow, r = i - k * brow;
-      const uint32_t n = N >= 32 ? 16 * (r / 20) + r % 20 : r;
-      const bool in = N >= 32 ? r % 20 < 16 : r < half;
+      const uint32_t n = grouped ? 16 * (r / 20) + r % 20 : r;
+      const bool in = grouped ? r % 20 < 16 && n < pairs : r < half;
       bas[i] = in ? __ldg(g_bas + (size_t)k * N + n) : 0.0f;
     }
   }
@@ -276,7 +289,101 @@ __device__ __forceinline__ void shape_transform(const DecodeParams &p, const Seg
   }
 }
 
-template <int WARPS>
+// The same for a window size N that is not a power of two (run-time N): a
+// window's ceil(N / 2) sample pairs (n, N - 1 - n) in groups of 16, one lane per
+// group; a step holds R = min(32 / groups, 1024 / N) windows, R N samples of the
+// tile from the staging tile's start, which the lanes store row by row (vector
+// stores where a row's address allows).
+__device__ __forceinline__ void shape_transform_any(const DecodeParams &p, const SegDev &sg, const DomS &dd,
+                                                    const unsigned char *smem, const uint8_t *stage, uint64_t win0,
+                                                    uint32_t nwin, const ShapeOut &o, bool &tma_pending) {
+  const uint32_t N = dd.N, P = shape_any_pairs(N), L = shape_any_lanes(N), R = shape_any_step(N);
+  const uint32_t brow = L * 20u;
+  const uint32_t lane = o.lane;
+  const float *deq0 = reinterpret_cast<const float *>(smem + dd.deq_off);
+  const float *bas = reinterpret_cast<const float *>(smem + dd.basis_off);
+  const uint64_t S = sg.n_samples;
+  if (tma_pending) {  // a previous tile's TMA store may still read the staging tile
+    if (lane == 0) tma_wait_read();
+    __syncwarp();
+    tma_pending = false;
+  }
+  const uint32_t wr = lane / L, q = lane % L;  // window of the step, pair group
+#pragma unroll 1
+  for (uint32_t w0 = 0; w0 < nwin; w0 += R) {
+    const uint32_t wl = w0 + wr;
+    const bool mine = wr < R && wl < nwin;
+    float ev[16], od[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) ev[i] = od[i] = 0.0f;
+    if (mine) {
+      const uint8_t *lv = stage + wl * dd.E;
+      const float *bq = bas + q * 20;
+      uint32_t k = 0;
+#pragma unroll 1
+      for (; k + 2 <= dd.kz; k += 2) {
+        const float c0 = deq0[(k < dd.B1 ? 0 : kZStride) + lv[k]];
+        const float c1 = deq0[(k + 1 < dd.B1 ? 0 : kZStride) + lv[k + 1]];
+        const float4 *b0 = reinterpret_cast<const float4 *>(bq + k * brow);
+        const float4 *b1 = reinterpret_cast<const float4 *>(bq + (k + 1) * brow);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const float4 u = b0[j], v = b1[j];
+          ev[4 * j] = fmaf(c0, u.x, ev[4 * j]);
+          ev[4 * j + 1] = fmaf(c0, u.y, ev[4 * j + 1]);
+          ev[4 * j + 2] = fmaf(c0, u.z, ev[4 * j + 2]);
+          ev[4 * j + 3] = fmaf(c0, u.w, ev[4 * j + 3]);
+          od[4 * j] = fmaf(c1, v.x, od[4 * j]);
+          od[4 * j + 1] = fmaf(c1, v.y, od[4 * j + 1]);
+          od[4 * j + 2] = fmaf(c1, v.z, od[4 * j + 2]);
+          od[4 * j + 3] = fmaf(c1, v.w, od[4 * j + 3]);
+        }
+      }
+      if (k < dd.kz) {  // a last even bin
+        const float c0 = deq0[(k < dd.B1 ? 0 : kZStride) + lv[k]];
+        const float4 *b0 = reinterpret_cast<const float4 *>(bq + k * brow);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const float4 u = b0[j];
+          ev[4 * j] = fmaf(c0, u.x, ev[4 * j]);
+          ev[4 * j + 1] = fmaf(c0, u.y, ev[4 * j + 1]);
+          ev[4 * j + 2] = fmaf(c0, u.z, ev[4 * j + 2]);
+          ev[4 * j + 3] = fmaf(c0, u.w, ev[4 * j + 3]);
+        }
+      }
+      // samples n = 16 q + i and N - 1 - n of window wr at step positions wr N + ...
+      // (the middle sample of an odd N once: its odd-bin basis values are zero)
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        const uint32_t n = 16 * q + i;
+        if (n < P) {
+          const uint32_t tf = wr * N + n, tm = wr * N + (N - 1 - n);
+          *reinterpret_cast<float *>(o.otile + (tf >> 5) * 128 + ((((tf & 31u) >> 2) ^ ((tf >> 5) & 7u)) << 4) +
+                                     ((tf & 3u) << 2)) = ev[i] + od[i];
+          if (tm != tf)
+            *reinterpret_cast<float *>(o.otile + (tm >> 5) * 128 + ((((tm & 31u) >> 2) ^ ((tm >> 5) & 7u)) << 4) +
+                                       ((tm & 3u) << 2)) = ev[i] - od[i];
+        }
+      }
+    }
+    __syncwarp();  // rows are written by other lanes
+    const uint64_t s0 = (win0 + w0) * N;  // first sample of the step in the segment
+    const uint32_t nw = nwin - w0 < R ? nwin - w0 : R;
+    const uint64_t lim = (uint64_t)nw * N < S - s0 ? (uint64_t)nw * N : S - s0;
+    const uint64_t r0 = (uint64_t)lane * 32;
+    if (r0 < lim) {
+      const uint32_t m = lim - r0 < 32 ? (uint32_t)(lim - r0) : 32u;
+      float *const dst = p.out + sg.out_offset + s0 + r0;
+      const uintptr_t a = reinterpret_cast<uintptr_t>(dst);
+      store_row(o.row, o.sx, dst, m, (a & 31u) == 0, (a & 15u) == 0);
+    }
+    __syncwarp();  // before the next step rewrites the tile
+  }
+}
+
+// ANY: a domain of the plan has a window size that is not a power of two (its
+// transform is compiled only into this instance, whose registers it costs).
+template <int WARPS, bool ANY>
 __global__ void __launch_bounds__(WARPS * 32, 1) k_decode_shape(const DecodeParams p, const WarpParams wp,
                                                                 const __grid_constant__ CUtensorMap out_map) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -359,25 +466,29 @@ __global__ void __launch_bounds__(WARPS * 32, 1) k_decode_shape(const DecodePara
       case 32: shape_transform<32>(p, sg, dd, smem_raw, stage, win0, nwin, o, tma_pending); break;
       case 64: shape_transform<64>(p, sg, dd, smem_raw, stage, win0, nwin, o, tma_pending); break;
       case 128: shape_transform<128>(p, sg, dd, smem_raw, stage, win0, nwin, o, tma_pending); break;
-      default: break;  // not a shape of this kernel (the plan never sends one)
+      default:
+        if (ANY) shape_transform_any(p, sg, dd, smem_raw, stage, win0, nwin, o, tma_pending);
+        break;
     }
     __syncwarp();  // the level bytes are rewritten by the next tile
   }
   if (tma_pending && lane == 0) tma_wait_all();
 }
 
-void *spick(uint32_t threads) {
+void *spick(uint32_t threads, bool any) {
   switch (threads) {
-    case 256: return reinterpret_cast<void *>(&k_decode_shape<8>);
-    case 512: return reinterpret_cast<void *>(&k_decode_shape<16>);
-    case 768: return reinterpret_cast<void *>(&k_decode_shape<24>);
+    case 256: return any ? reinterpret_cast<void *>(&k_decode_shape<8, true>) : reinterpret_cast<void *>(&k_decode_shape<8, false>);
+    case 512: return any ? reinterpret_cast<void *>(&k_decode_shape<16, true>) : reinterpret_cast<void *>(&k_decode_shape<16, false>);
+    case 768: return any ? reinterpret_cast<void *>(&k_decode_shape<24, true>) : reinterpret_cast<void *>(&k_decode_shape<24, false>);
     default: return nullptr;
   }
 }
 
 }  // namespace
 
-bool shape_supported(uint32_t N) { return N >= 4 && N <= 128 && (N & (N - 1)) == 0; }
+bool shape_supported(uint32_t N) { return N >= 4 && N <= 128; }
+
+bool shape_pow2_only(uint32_t N) { return shape_pow2(N); }
 
 uint32_t shape_windows_per_tile(uint32_t N, uint32_t E) { return shape_tile_windows(N, E); }
 
@@ -398,8 +509,8 @@ size_t shape_smem_layout(uint32_t threads, const uint32_t *lmax, const uint32_t 
   return o + warps * kMiscBytes + 1023 + warps * kOutTile;  // + alignment of the staging tiles
 }
 
-cudaError_t shape_smem_config(uint32_t threads, size_t smem) {
-  void *k = spick(threads);
+cudaError_t shape_smem_config(uint32_t threads, bool any, size_t smem) {
+  void *k = spick(threads, any);
   if (!k) return cudaErrorInvalidValue;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout,
                                        (int)cudaSharedmemCarveoutMaxShared);
@@ -407,16 +518,16 @@ cudaError_t shape_smem_config(uint32_t threads, size_t smem) {
   return set_dynamic_smem_limit(k, smem);
 }
 
-cudaError_t shape_occupancy(uint32_t threads, size_t smem, int *ctas_per_sm) {
-  void *k = spick(threads);
+cudaError_t shape_occupancy(uint32_t threads, bool any, size_t smem, int *ctas_per_sm) {
+  void *k = spick(threads, any);
   if (!k) return cudaErrorInvalidValue;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, k, (int)threads, smem);
 }
 
 cudaError_t launch_shape(const DecodeParams &p, const WarpParams &wp, const CUtensorMap &out_map, uint32_t threads,
-                         uint32_t grid, size_t smem, cudaStream_t stream) {
+                         bool any, uint32_t grid, size_t smem, cudaStream_t stream) {
   if (p.tile_end <= p.tile_begin || grid == 0) return cudaSuccess;
-  void *k = spick(threads);
+  void *k = spick(threads, any);
   if (!k) return cudaErrorInvalidValue;
   DecodeParams pp = p;
   WarpParams ww = wp;

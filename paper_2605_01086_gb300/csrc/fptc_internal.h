@@ -215,17 +215,19 @@ bool encode_out_map3(CUtensorMap *map, float *out, uint64_t extent, uint32_t N);
 cudaError_t launch_tcs(const DecodeParams &p, const WarpParams &wp, const TcParams &tp, const CUtensorMap &out_map,
                        uint32_t mode, uint32_t N, uint32_t E, uint32_t grid, size_t smem, cudaStream_t stream);
 
-// warp-tile kernel for other shapes: a power-of-two N in [4, 128] for every
-// domain (several N in one plan), any E <= N (decode_shape.cu); tiles of
-// shape_windows_per_tile(N, E) windows
+// warp-tile kernel for other shapes: N in [4, 128] for every domain (several N
+// in one plan), any E <= N (decode_shape.cu); tiles of shape_windows_per_tile(N,
+// E) windows; `any`: some domain's N is not a power of two (shape_pow2_only
+// false), served by the kernel instance that holds that transform
 bool shape_supported(uint32_t N);
+bool shape_pow2_only(uint32_t N);
 uint32_t shape_windows_per_tile(uint32_t N, uint32_t E);
 size_t shape_smem_layout(uint32_t threads, const uint32_t *lmax, const uint32_t *N, const uint32_t *E,
                          uint32_t n_domains, WarpParams *wp);
-cudaError_t shape_smem_config(uint32_t threads, size_t smem);
-cudaError_t shape_occupancy(uint32_t threads, size_t smem, int *ctas_per_sm);
+cudaError_t shape_smem_config(uint32_t threads, bool any, size_t smem);
+cudaError_t shape_occupancy(uint32_t threads, bool any, size_t smem, int *ctas_per_sm);
 cudaError_t launch_shape(const DecodeParams &p, const WarpParams &wp, const CUtensorMap &out_map, uint32_t threads,
-                         uint32_t grid, size_t smem, cudaStream_t stream);
+                         bool any, uint32_t grid, size_t smem, cudaStream_t stream);
 
 // adjoint for N = 32, E = 16 plans on the warp-tile machinery (backward_warp.cu)
 size_t backward_warp_smem_layout(uint32_t threads, const uint32_t *lmax, uint32_t n_domains, WarpParams *wp);

@@ -48,9 +48,10 @@ struct fptc_plan {
   size_t device_bytes = 0;
   // launch settings
   int kind = FPTC_KERNEL_GENERIC;   // fptc_kernel in use
-  bool shape = false;     // every domain has a power-of-two N in [4, 128] and the warp-tile kernel of
+  bool shape = false;     // every domain has N in [4, 128] and the warp-tile kernel of
                           // decode_shape.cu serves the plan (N = 32, E = 16 plans use decode_warp.cu)
   uint32_t tcs_N = 0, tcs_E = 0;  // the tensor-core kernel of decode_tcs.cu serves this shape (0: decode_tc.cu)
+  bool shape_any = false; // a domain's N is not a power of two (the shape kernel instance with that transform)
   WarpParams wp{};
   TcParams tp{};
   uint32_t threads = 256, grid = 0, ctas_per_sm = 0;
@@ -290,9 +291,9 @@ fptc_status configure_launch(fptc_plan *p) {
     if (e == cudaSuccess) occ = std::min<int>(occ, 1);
   } else if (shape) {
     p->smem = shape_smem_layout(threads, lm.data(), ns.data(), es.data(), (uint32_t)lm.size(), &p->wp);
-    e = shape_smem_config(threads, p->smem);
+    e = shape_smem_config(threads, p->shape_any, p->smem);
     if (e != cudaSuccess) return cuda_fail(e, "decode shared-memory size");
-    e = shape_occupancy(threads, p->smem, &occ);
+    e = shape_occupancy(threads, p->shape_any, p->smem, &occ);
   } else if (p->kind == FPTC_KERNEL_WARP_TILE) {
     p->smem = warp_smem_layout(threads, lm.data(), (uint32_t)lm.size(), &p->wp);
     e = warp_smem_config(threads, p->smem);
@@ -455,7 +456,7 @@ cudaError_t run_range(const fptc_plan *p, const IndexParams &ip0, const DecodePa
     CUtensorMap map;
     std::memset(&map, 0, sizeof(map));
     wp.out_tma = encode_out_map(&map, dp.out, p->out_extent) ? 1u : 0u;
-    if (p->shape) return launch_shape(dp, wp, map, p->threads, grid, p->smem, st);
+    if (p->shape) return launch_shape(dp, wp, map, p->threads, p->shape_any, grid, p->smem, st);
     return launch_warp(dp, wp, map, p->threads, grid, p->smem, st);
   }
   if (p->kind == FPTC_KERNEL_TENSOR && p->tcs_N) {
@@ -557,18 +558,18 @@ fptc_status fptc_plan_create(fptc_plan **out, int device, const fptc_domain *dom
       set_error("unknown kernel %u", o.kernel);
       return FPTC_ERR_INVALID_ARGUMENT;
     }
-    bool all_fixed = true, all_pow2 = n_domains > 0;
+    bool all_fixed = true, all_shape = n_domains > 0;
     for (uint32_t d = 0; d < n_domains; ++d) {
       all_fixed = all_fixed && domains[d].N == 32 && domains[d].E == 16;
-      all_pow2 = all_pow2 && shape_supported(domains[d].N);
+      all_shape = all_shape && shape_supported(domains[d].N);
     }
     const bool fixed_ok = all_fixed && n_domains <= kWarpMaxDomains;
-    // other shapes: a power-of-two N in [4, 128] for every domain
-    const bool shape_ok = !all_fixed && all_pow2 && n_domains <= kWarpMaxDomains;
+    // other shapes: N in [4, 128] for every domain
+    const bool shape_ok = !all_fixed && all_shape && n_domains <= kWarpMaxDomains;
     const bool warp_ok = fixed_ok || shape_ok;
     if ((o.kernel == FPTC_KERNEL_BLOCK_TILE && !all_fixed) || (o.kernel == FPTC_KERNEL_WARP_TILE && !warp_ok)) {
-      set_error("the block-tile kernel needs N = 32, E = 16 in every domain; the warp-tile kernel that, or a "
-                "power-of-two N in [4, 128] in every domain (at most %u domains)", kWarpMaxDomains);
+      set_error("the block-tile kernel needs N = 32, E = 16 in every domain; the warp-tile kernel that, or "
+                "N in [4, 128] in every domain (at most %u domains)", kWarpMaxDomains);
       return FPTC_ERR_UNSUPPORTED;
     }
     // the tensor-core transform: N = 32, E = 16 in every domain (decode_tc.cu), or one
@@ -697,6 +698,8 @@ fptc_status fptc_plan_create(fptc_plan **out, int device, const fptc_domain *dom
     p->lut_cap = 1u << max_lmax;
     p->kind = (int)o.kernel;
     p->shape = shape_ok;
+    p->shape_any = false;
+    for (uint32_t d = 0; d < n_domains; ++d) p->shape_any = p->shape_any || !shape_pow2_only(domains[d].N);
     p->tcs_N = tcs_ok ? domains[0].N : 0u;
     p->tcs_E = tcs_ok ? domains[0].E : 0u;
 
