@@ -678,7 +678,8 @@ def run(args):
     return 0
 
 
-SWEEP_SHAPES = [(16, 8), (32, 8), (32, 16), (32, 32), (64, 16), (64, 32), (128, 32), (128, 64)]
+SWEEP_SHAPES = [(16, 8), (32, 8), (32, 16), (32, 32), (64, 16), (64, 32), (128, 32), (128, 64),
+                (24, 12), (48, 24), (100, 50)]  # the last three: N not a power of two
 
 
 def run_sweep(args):
@@ -723,9 +724,12 @@ def run_sweep(args):
         alg = out_b + 9 * int(sg["n_words"].sum()) * R
         ref = None
         # the FP32 transform, and for E >= 32 the tensor-core forms
-        for idct in (["fp32"] + (["tf32x3", "bf16x3", "tf32"] if E >= 32 else [])):
+        pow2 = N & (N - 1) == 0
+        forms = ["fp32"] + (["tf32x3", "bf16x3", "tf32"] if E >= 32 and pow2 else []) + ([] if pow2 else ["generic"])
+        for idct in forms:
             try:
-                plan = Plan([d], segs, device=0, idct=idct)
+                plan = (Plan([d], segs, device=0, kernel="generic") if idct == "generic"
+                        else Plan([d], segs, device=0, idct=idct))
             except Exception:  # a shape the tensor-core kernel does not serve
                 continue
             out = plan.empty_out()
