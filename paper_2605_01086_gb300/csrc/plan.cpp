@@ -313,7 +313,9 @@ fptc_status configure_launch(fptc_plan *p) {
   p->ctas_per_sm = p->opts.ctas_per_sm ? std::min<uint32_t>(p->opts.ctas_per_sm, (uint32_t)occ) : (uint32_t)occ;
   const uint64_t full = (uint64_t)p->sm_count * p->ctas_per_sm;
   p->grid = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(full, p->n_tiles));
-  // backward (the warp-tile adjoint serves N = 32, E = 16 plans)
+  // backward (the warp-tile adjoint serves N = 32, E = 16 plans); decided afresh on every
+  // configuration: the autotuner configures one candidate after another
+  p->b_warp = false;
   if ((p->kind == FPTC_KERNEL_WARP_TILE && !shape) || (p->kind == FPTC_KERNEL_TENSOR && !p->tcs_N)) {
     // the warp-tile adjoint: 16 warps if their buffers fit, else 8
     int dev = 0, optin = 0;

@@ -181,3 +181,31 @@ def test_backward_other_shapes_matches_oracle(mode):
     for i, c in enumerate(gC):
         a = int(plan.level_offsets[i])
         assert np.linalg.norm(h[a:a + c.size] - c) <= GRAD_COEFF_REL_L2 * max(np.linalg.norm(c), 1e-30), i
+
+
+def test_backward_after_autotune():
+    """The adjoint of a plan whose autotuner tried warp-tile candidates and may
+    have settled on a block kernel (a single stream of 65,536 samples, where the
+    block-tile kernel tends to win): the adjoint serves the configuration the
+    autotuner left, and agrees with a plan configured once."""
+    wl = siggen.Workload("one", 3, np.zeros(1, np.int32), np.array([siggen.stream_seed(3, 0)], np.uint64),
+                         np.array([65536], np.uint64))
+    b = encode_workload(wl)
+    outs = []
+    for tune in (True, False):
+        plan = make_plan(b, out_align=32)
+        w, s = plan.to_device(b.words, b.symlen)
+        out = plan.empty_out().zero_()
+        if tune:
+            plan.autotune(w, s, out, trials=2)
+        n_lev = plan.info["n_levels_total"]
+        lv = torch.empty(n_lev, dtype=torch.uint8, device=plan.device)
+        gco = torch.empty(n_lev, dtype=torch.float32, device=plan.device)
+        plan.decode(w, s, out=out, levels=lv)
+        gsc, _ = plan.backward(out, levels=lv, grad_coeffs=gco)
+        torch.cuda.synchronize()
+        assert plan.device_status()[0] == 0
+        outs.append((gsc.cpu().numpy(), gco.cpu().numpy().astype(np.float64)))
+    (g1, c1), (g2, c2) = outs
+    np.testing.assert_allclose(g1, g2, rtol=1e-6, atol=1e-9)
+    assert np.linalg.norm(c1 - c2) <= 1e-6 * np.linalg.norm(c2)
