@@ -1,5 +1,5 @@
 // tcgen05 building blocks shared by the tensor-core decode kernels
-// (decode_tc.cu, decode_ws.cu): barriers, fences, shared-memory and instruction
+// (decode_tc.cu, decode_tcs.cu): barriers, fences, shared-memory and instruction
 // descriptors, the MMA / tensor-memory load and store wrappers, the operand
 // split of each precision form, the products of one 128-window step, and the B
 // operand (the inverse-transform basis) in shared memory.
