@@ -284,7 +284,7 @@ size_t backward_warp_smem_layout(uint32_t threads, const uint32_t *lmax, uint32_
     wp->lut_off[d] = (uint32_t)o;
     o += align16((size_t)2 << lmax[d]);
     wp->tab_off[d] = (uint32_t)o;
-    o += align16(3u * kZStride * 4);
+    o += kDeqBytes;
   }
   o = align16(o);
   wp->warp_off = (uint32_t)o;

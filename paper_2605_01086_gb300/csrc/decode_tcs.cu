@@ -352,7 +352,7 @@ __global__ void __launch_bounds__(tcs_nwg<MODE, N, E>() * 128, 1)
             for (int j = 0; j < 16; ++j) {
               const uint32_t kb = 16u * q + j;
               const uint32_t z = kb < B1 ? 0u : (kb < B2 ? 1u : 2u);
-              c[j] = deq[z * kZStride + ((sw[j >> 2] >> (8 * (j & 3))) & 0xffu)];
+              c[j] = z < 2u ? deq[z * kZStride + ((sw[j >> 2] >> (8 * (j & 3))) & 0xffu)] : 0.0f;
             }
             if (lev) {
               uint8_t *dl = lev + wi * E + 16 * q;
@@ -490,7 +490,7 @@ size_t tcs_smem_layout(uint32_t mode, uint32_t N, uint32_t E, const uint32_t *lm
     wp->lut_off[d] = (uint32_t)o;
     o += align16((size_t)2 << lmax[d]);
     wp->tab_off[d] = (uint32_t)o;
-    o += align16(3u * kZStride * 4);
+    o += kDeqBytes;
   }
   o = align16(o);
   wp->warp_off = (uint32_t)o;

@@ -245,6 +245,7 @@ void *wpick(uint32_t threads) {
     case 256: return wptr<8>();
     case 512: return wptr<16>();
     case 768: return wptr<24>();
+    case 896: return wptr<28>();
     case 1024: return wptr<32>();
     default: return nullptr;
   }
@@ -262,7 +263,7 @@ size_t warp_smem_layout(uint32_t threads, const uint32_t *lmax, uint32_t n_domai
     wp->lut_off[d] = (uint32_t)o;
     o += align16((size_t)2 << lmax[d]);
     wp->tab_off[d] = (uint32_t)o;
-    o += align16(3u * kZStride * 4);
+    o += kDeqBytes;
   }
   o = align16(o);
   wp->warp_off = (uint32_t)o;

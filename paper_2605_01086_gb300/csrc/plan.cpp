@@ -220,7 +220,7 @@ fptc_status configure_launch(fptc_plan *p) {
           break;
         }
     } else {
-      for (uint32_t t : {1024u, 768u, 512u, 256u})
+      for (uint32_t t : {1024u, 896u, 768u, 512u, 256u})
         if (warp_smem_layout(t, lm.data(), (uint32_t)lm.size(), &probe) <= (size_t)optin) {
           threads = t;
           break;
@@ -231,10 +231,11 @@ fptc_status configure_launch(fptc_plan *p) {
   const bool t_ok = (p->kind == FPTC_KERNEL_TENSOR && p->tcs_N) ? threads > 0
                     : shape ? (threads == 256 || threads == 512 || threads == 768)
                           : (threads == 128 || threads == 256 || threads == 512 ||
-                             ((threads == 768 || threads == 1024) && p->kind == FPTC_KERNEL_WARP_TILE) ||
+                             ((threads == 768 || threads == 896 || threads == 1024) &&
+                              p->kind == FPTC_KERNEL_WARP_TILE) ||
                              ((threads == 384 || threads == 640 || threads == 768) && p->kind == FPTC_KERNEL_TENSOR));
   if (!t_ok) {
-    set_error("threads must be 128, 256 or 512 (768 and 1024 also for the warp-tile kernel, 384, 640 and 768 "
+    set_error("threads must be 128, 256 or 512 (768, 896 and 1024 also for the warp-tile kernel, 384, 640 and 768 "
               "for the tensor-core kernel; 256, 512 or 768 for the warp-tile kernel of other shapes; got %u)",
               threads);
     return FPTC_ERR_INVALID_ARGUMENT;
@@ -1094,7 +1095,7 @@ fptc_status fptc_plan_autotune(fptc_plan *p, const uint64_t *d_words, const uint
     else if (keep.idct != FPTC_IDCT_FP32)
       for (uint32_t th : {256u, 384u, 512u, 640u, 768u})
         cands.push_back({FPTC_KERNEL_TENSOR, tc_tile_windows() * 32, th});
-    for (uint32_t th : {128u, 256u, 512u, 768u, 1024u}) {
+    for (uint32_t th : {128u, 256u, 512u, 768u, 896u, 1024u}) {
       if (keep.idct != FPTC_IDCT_FP32) continue;
       if (th > 512) {
         if (fixed && p->domains.size() <= kWarpMaxDomains)

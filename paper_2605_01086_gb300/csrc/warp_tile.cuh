@@ -25,6 +25,8 @@ constexpr int kTS = kT * kE;               // symbols per tile
 constexpr int kGuard = 64;                 // entries before and after the tile (a word holds <= 64 codewords)
 constexpr int kStage = kTS + 2 * kGuard;   // level bytes per warp
 constexpr int kZStride = 257;              // floats per zone row (zero levels of the zones in different banks)
+constexpr int kZRows = 2;                  // zone rows in shared memory: zone 2 reconstructs 0 without a row
+constexpr uint32_t kDeqBytes = (kZRows * kZStride * 4 + 15) / 16 * 16;  // a domain's dequantization rows
 constexpr int kWPL = 2;                    // consecutive words per lane per decode pass
 constexpr int kPassWords = 32 * kWPL;
 constexpr int kStepWin = 32;               // windows per transform step (one per lane)
@@ -87,7 +89,7 @@ __device__ __forceinline__ void fence_async_shared() { asm volatile("fence.proxy
 
 struct DomW {
   uint32_t lut_off;   // bytes from the start of shared memory: 16-bit entries len | level << 8
-  uint32_t deq_off;   // bytes: zone rows [3][kZStride] floats (row 2 zero)
+  uint32_t deq_off;   // bytes: zone rows [kZRows][kZStride] floats (zones 0 and 1)
   uint32_t shift;     // 32 - lmax
   uint32_t zmask;     // zone of bin k at bits 2k..2k+1
   uint32_t complete;  // every prefix decodes (no zero entry)
@@ -242,7 +244,7 @@ __device__ __forceinline__ uint32_t load_domain_tables(const DecodeParams &p, ui
     const DomainDev &dm = p.domains[d];
     const uint32_t lut_off = off;
     const uint32_t deq_off = lut_off + (uint32_t)align16((size_t)2 << dm.lmax);
-    off = deq_off + (uint32_t)align16(3u * kZStride * 4);
+    off = deq_off + kDeqBytes;
     if (threadIdx.x == 0) {
       DomW x;
       x.lut_off = lut_off;
@@ -267,9 +269,9 @@ __device__ __forceinline__ uint32_t load_domain_tables(const DecodeParams &p, ui
     a0 = a0 > 1e-30f ? a0 : 0.0f;
     a1 = a1 > 1e-30f ? a1 : 0.0f;
     float *deq = reinterpret_cast<float *>(smem + deq_off);
-    for (uint32_t i = threadIdx.x; i < 3u * kZStride; i += THREADS) {
+    for (uint32_t i = threadIdx.x; i < (uint32_t)(kZRows * kZStride); i += THREADS) {
       const uint32_t z = i / kZStride, L = i - z * kZStride;
-      deq[i] = (L < 256u && z < 2u) ? (z == 0 ? a0 : a1) * dm.unit[z][L] : 0.0f;
+      deq[i] = L < 256u ? (z == 0 ? a0 : a1) * dm.unit[z][L] : 0.0f;
     }
   }
   return off;
@@ -375,8 +377,10 @@ __device__ __forceinline__ void window_coefs(const uint4 &sv, const float *deq, 
     for (int k = 0; k < 16; ++k) c[k] = deq[(k < 2 ? 0 : kZStride) + ((sw[k >> 2] >> (8 * (k & 3))) & 0xffu)];
   } else {
 #pragma unroll
-    for (int k = 0; k < 16; ++k)
-      c[k] = deq[((zmask >> (2 * k)) & 3u) * kZStride + ((sw[k >> 2] >> (8 * (k & 3))) & 0xffu)];
+    for (int k = 0; k < 16; ++k) {
+      const uint32_t z = (zmask >> (2 * k)) & 3u;
+      c[k] = z < 2u ? deq[z * kZStride + ((sw[k >> 2] >> (8 * (k & 3))) & 0xffu)] : 0.0f;  // zone 2: 0
+    }
   }
 }
 
