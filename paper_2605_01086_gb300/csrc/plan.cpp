@@ -196,6 +196,19 @@ void layout_tiles(fptc_plan *p, uint32_t tile_samples) {
   p->n_tiles = t;
 }
 
+// FPTC_ERR_UNSUPPORTED with the sizes when a kernel's shared memory at `threads`
+// exceeds what one CTA may opt in to on the current device.
+fptc_status smem_fits(const char *kernel, uint32_t threads, size_t smem) {
+  int dev = 0, optin = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (smem <= (size_t)optin) return FPTC_OK;
+  set_error("the %s kernel at %u threads needs %zu bytes of shared memory with these domains' tables; a CTA may "
+            "use %d (fewer threads, or 0 to choose)",
+            kernel, threads, smem, optin);
+  return FPTC_ERR_UNSUPPORTED;
+}
+
 fptc_status configure_launch(fptc_plan *p) {
   uint32_t threads = p->opts.threads ? p->opts.threads : (p->kind == FPTC_KERNEL_TENSOR ? 512u : 256u);
   const bool shape = p->kind == FPTC_KERNEL_WARP_TILE && p->shape;
@@ -220,7 +233,8 @@ fptc_status configure_launch(fptc_plan *p) {
           break;
         }
     } else {
-      for (uint32_t t : {1024u, 896u, 768u, 512u, 256u})
+      // 896 before 1024: 28 warps run without spills (72 registers), 32 would spill at 64
+      for (uint32_t t : {896u, 1024u, 768u, 512u, 256u})
         if (warp_smem_layout(t, lm.data(), (uint32_t)lm.size(), &probe) <= (size_t)optin) {
           threads = t;
           break;
@@ -279,6 +293,7 @@ fptc_status configure_launch(fptc_plan *p) {
       p->threads = threads;
     }
     p->smem = tc_smem_layout(p->opts.idct, threads, lm.data(), (uint32_t)lm.size(), &p->wp, &p->tp);
+    if (const fptc_status fs = smem_fits("tensor-core", threads, p->smem); fs != FPTC_OK) return fs;
     e = tc_smem_config(p->opts.idct, threads, p->smem);
     if (e != cudaSuccess) return cuda_fail(e, "decode shared-memory size");
     e = tc_occupancy(p->opts.idct, threads, p->smem, &occ);
@@ -292,11 +307,13 @@ fptc_status configure_launch(fptc_plan *p) {
     if (e == cudaSuccess) occ = std::min<int>(occ, 1);
   } else if (shape) {
     p->smem = shape_smem_layout(threads, lm.data(), ns.data(), es.data(), (uint32_t)lm.size(), &p->wp);
+    if (const fptc_status fs = smem_fits("warp-tile", threads, p->smem); fs != FPTC_OK) return fs;
     e = shape_smem_config(threads, p->shape_any, p->smem);
     if (e != cudaSuccess) return cuda_fail(e, "decode shared-memory size");
     e = shape_occupancy(threads, p->shape_any, p->smem, &occ);
   } else if (p->kind == FPTC_KERNEL_WARP_TILE) {
     p->smem = warp_smem_layout(threads, lm.data(), (uint32_t)lm.size(), &p->wp);
+    if (const fptc_status fs = smem_fits("warp-tile", threads, p->smem); fs != FPTC_OK) return fs;
     e = warp_smem_config(threads, p->smem);
     if (e != cudaSuccess) return cuda_fail(e, "decode shared-memory size");
     e = warp_occupancy(threads, p->smem, &occ);

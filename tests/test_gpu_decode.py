@@ -54,6 +54,25 @@ def test_mixed_batch_ragged(kernel, schedule):
     assert plan.device_status()[0] == 0
 
 
+def test_warp_tile_28_warps_and_shared_memory_limit():
+    """896 threads (28 warps per CTA) fit the tables of four Table 1 domains and decode them; 1024
+    threads do not fit and are refused at plan creation with the sizes named (no launch)."""
+    from paper_2605_01086_gb300 import _lib
+    wl = siggen.mixed_10000_logu(n=24, lo=100, hi=100000)
+    b = encode_workload(wl)
+    assert len(b.domains) == 4
+    assert make_plan(b).info["threads"] == 896  # the default: the most warps that fit without spills
+    plan = make_plan(b, kernel="warp_tile", threads=896)
+    assert plan.info["threads"] == 896 and plan.info["kernel"] == KERNEL_IDS["warp_tile"]
+    _, _, out, lv = gpu_decode(plan, b, out_fill=float("nan"))
+    compare_with_oracle(plan, b, out, lv)
+    assert plan.device_status()[0] == 0
+    with pytest.raises(_lib.FptcError) as ei:
+        make_plan(b, kernel="warp_tile", threads=1024)
+    assert ei.value.status == _lib.UNSUPPORTED
+    assert "shared memory" in str(ei.value) and "1024 threads" in str(ei.value)
+
+
 @pytest.mark.parametrize("tile_samples,threads", [(32, 128), (512, 256), (2048, 512), (4096, 256), (16384, 256),
                                                   (8192, 128)])
 def test_tile_and_cta_sizes(tile_samples, threads):
