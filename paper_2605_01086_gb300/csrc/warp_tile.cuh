@@ -101,14 +101,16 @@ struct DomW {
 // length (the entry's low 5 bits: the funnel shifts use the amount mod 32).
 // The marker leaves the buffer iff the codewords used more than 64 bits.
 // CHECKED (incomplete code): an entry of length 0 marks a prefix with no
-// codeword.  Returns error flags.
-template <bool CHECKED>
+// codeword.  SHIFT: 32 - lmax when the caller knows it at compile time (the
+// table index is then one shift-and-add), else 0 and `shift` holds it.
+// Returns error flags.
+template <bool CHECKED, uint32_t SHIFT = 0>
 __device__ __forceinline__ uint32_t decode_word(uint64_t w, uint32_t n, uint8_t *__restrict__ dst,
                                                 const uint16_t *__restrict__ lut, uint32_t shift) {
   uint32_t hi = (uint32_t)(w >> 32), lo = (uint32_t)w, mk = 0x80000000u;
   uint32_t low = 31u;
   auto step = [&]() -> uint32_t {
-    const uint32_t e = lut[hi >> shift];
+    const uint32_t e = lut[hi >> (SHIFT ? SHIFT : shift)];
     hi = __funnelshift_l(lo, hi, e);
     lo = __funnelshift_l(mk, lo, e);
     mk = __funnelshift_l(0u, mk, e);
@@ -121,10 +123,19 @@ __device__ __forceinline__ uint32_t decode_word(uint64_t w, uint32_t n, uint8_t 
     dst[0] = (uint8_t)(step() >> 8);
     j = 1;
   }
-  for (; j + 2 <= n; j += 2) {
+  for (; j + 4 <= n; j += 4) {  // four codewords an iteration (less loop overhead per codeword)
+    const uint32_t e0 = step();
+    const uint32_t e1 = step();
+    const uint32_t e2 = step();
+    const uint32_t e3 = step();
+    *reinterpret_cast<uint16_t *>(dst + j) = (uint16_t)__byte_perm(e0, e1, 0x0051);
+    *reinterpret_cast<uint16_t *>(dst + j + 2) = (uint16_t)__byte_perm(e2, e3, 0x0051);
+  }
+  if (j + 2 <= n) {
     const uint32_t e0 = step();
     const uint32_t e1 = step();
     *reinterpret_cast<uint16_t *>(dst + j) = (uint16_t)__byte_perm(e0, e1, 0x0051);
+    j += 2;
   }
   if (j < n) dst[j] = (uint8_t)(step() >> 8);
   return ((hi | lo | mk) == 0u ? kFlagBitOverrun : 0u) | ((CHECKED && low == 0u) ? kFlagInvalidCode : 0u);
@@ -343,7 +354,13 @@ __device__ __forceinline__ TileEnd decode_tile(const DecodeParams &p, const Ctx 
       }
     }
     uint8_t *dst = stage + p0;
-    if (dd.complete) {
+    if (dd.complete && dd.shift == 20u) {  // L_max = 12, the trained tables' limit
+#pragma unroll
+      for (int u = 0; u < kWPL; ++u) {
+        bad |= decode_word<false, 20u>(w[u], n[u], dst, lut, 20u);
+        dst += n[u];
+      }
+    } else if (dd.complete) {
 #pragma unroll
       for (int u = 0; u < kWPL; ++u) {
         bad |= decode_word<false>(w[u], n[u], dst, lut, dd.shift);
