@@ -62,7 +62,7 @@ __global__ void __launch_bounds__(WARPS * 32, 1) k_backward_warp(const BackwardP
 
   unsigned char *const wbase = smem_raw + wp.warp_off + warp * kMiscBytes;
   uint64_t *const wbuf = reinterpret_cast<uint64_t *>(wbase);
-  uint8_t *const stage = wbase + kPassWords * 8 + kGuard;
+  uint8_t *const stage = wbase + kStageOff;
   uint64_t *const mbar = reinterpret_cast<uint64_t *>(smem_raw + wp.warp_off + WARPS * kMiscBytes) + 2 * warp;
   const uintptr_t tiles0 =
       (reinterpret_cast<uintptr_t>(smem_raw + wp.warp_off + WARPS * kMiscBytes + WARPS * 16) + 1023) &

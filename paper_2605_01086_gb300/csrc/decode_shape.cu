@@ -395,7 +395,7 @@ __global__ void __launch_bounds__(WARPS * 32, 1) k_decode_shape(const DecodePara
 
   unsigned char *const wbase = smem_raw + wp.warp_off + warp * kMiscBytes;
   uint64_t *const wbuf = reinterpret_cast<uint64_t *>(wbase);  // first-pass words
-  uint8_t *const stage = wbase + kPassWords * 8 + kGuard;      // tile position 0
+  uint8_t *const stage = wbase + kStageOff;      // tile position 0
   const uintptr_t tiles0 = (reinterpret_cast<uintptr_t>(smem_raw + wp.warp_off + WARPS * kMiscBytes) + 1023) &
                            ~uintptr_t(1023);
   unsigned char *const otile = reinterpret_cast<unsigned char *>(tiles0) + warp * kOutTile;

@@ -10,7 +10,7 @@
 // transform step of a warpgroup: its four warps each contribute 32 windows
 // (one step of their own current tile) as rows 32 q .. 32 q + 31 of the A
 // operand, which lane i of warp q writes straight into tensor-memory lane
-// 32 q + i (tcgen05.st: no shared-memory operand, so 24 warps fit); one thread
+// 32 q + i (tcgen05.st: no shared-memory operand, so 28 warps fit); one thread
 // issues tcgen05.mma (M = 128, N = 32) with A and D in tensor memory and B in
 // shared memory, tcgen05.commit signals an mbarrier, and warp q reads rows
 // 32 q .. 32 q + 31 of D with tcgen05.ld 32x32b (lane i = one window: the
@@ -82,7 +82,7 @@ __global__ void __launch_bounds__(NWG * 128, 1) k_decode_tc(const DecodeParams p
 
   unsigned char *const wbase = smem_raw + wp.warp_off + warp * kMiscBytes;
   uint64_t *const wbuf = reinterpret_cast<uint64_t *>(wbase);
-  uint8_t *const stage = wbase + kPassWords * 8 + kGuard;
+  uint8_t *const stage = wbase + kStageOff;
   const uintptr_t tiles0 = (reinterpret_cast<uintptr_t>(smem_raw + tp.tiles_off) + 1023) & ~uintptr_t(1023);
   unsigned char *const otile = reinterpret_cast<unsigned char *>(tiles0) + warp * kOutTile;
   const bool want_lev = p.levels != nullptr;
@@ -125,48 +125,54 @@ __global__ void __launch_bounds__(NWG * 128, 1) k_decode_tc(const DecodeParams p
     }
     if (timeout) return;
     tc_fence_after();
-    uint32_t v[32];
-    tmem_ld32(d_tmem + lane_off, v);
-    if (o.nwin == 0) return;
+    if (o.nwin == 0) return;  // nothing of this product is stored (D is not read)
     const bool tma = (o.flags & 4u) && o.nwin == kStepWin && (uint64_t)kStepWin * kN <= o.left;
-    if (tma) {
-      if (tma_pending) {
-        if (lane == 0) tma_wait_read();
-        __syncwarp();
-      }
-      unsigned char *const row = otile + lane * (kN * 4);
-      const uint32_t sx = lane & 7u;
+    if (tma && tma_pending) {
+      if (lane == 0) tma_wait_read();
+      __syncwarp();
+    }
+    unsigned char *const row = otile + lane * (kN * 4);
+    const uint32_t sx = lane & 7u;
+    const uint64_t s0 = (uint64_t)lane * kN;
+    float *const dst = o.dst + s0;
+    // the 32 samples of this lane's window, read back 16 at a time (fewer live registers)
 #pragma unroll
-      for (int cidx = 0; cidx < 8; ++cidx)
-        *reinterpret_cast<uint4 *>(row + ((cidx ^ sx) << 4)) =
-            make_uint4(v[4 * cidx], v[4 * cidx + 1], v[4 * cidx + 2], v[4 * cidx + 3]);
+    for (uint32_t h = 0; h < 2; ++h) {
+      uint32_t v[16];
+      tmem_ld16(d_tmem + lane_off + 16u * h, v);
+      if (tma) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          *reinterpret_cast<uint4 *>(row + (((4u * h + q) ^ sx) << 4)) =
+              make_uint4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+      } else if (lane < o.nwin) {
+        if (s0 + kN <= o.left && (o.flags & 2u)) {
+#pragma unroll
+          for (int b = 0; b < 2; ++b) {
+            const float vv[8] = {__uint_as_float(v[8 * b]),     __uint_as_float(v[8 * b + 1]),
+                                 __uint_as_float(v[8 * b + 2]), __uint_as_float(v[8 * b + 3]),
+                                 __uint_as_float(v[8 * b + 4]), __uint_as_float(v[8 * b + 5]),
+                                 __uint_as_float(v[8 * b + 6]), __uint_as_float(v[8 * b + 7])};
+            st_cs_v8(dst + 16 * h + 8 * b, vv);
+          }
+        } else if (s0 + kN <= o.left && (o.flags & 1u)) {
+#pragma unroll
+          for (int j = 0; j < 4; ++j)
+            __stcs(reinterpret_cast<float4 *>(dst + 16 * h) + j,
+                   make_float4(__uint_as_float(v[4 * j]), __uint_as_float(v[4 * j + 1]),
+                               __uint_as_float(v[4 * j + 2]), __uint_as_float(v[4 * j + 3])));
+        } else {
+#pragma unroll
+          for (int n = 0; n < 16; ++n)
+            if (s0 + 16 * h + n < o.left) dst[16 * h + n] = __uint_as_float(v[n]);
+        }
+      }
+    }
+    if (tma) {
       fence_async_shared();
       __syncwarp();
       if (lane == 0) tma_store_rows(&out_map, otile, (int32_t)o.out_row);
       tma_pending = true;
-    } else if (lane < o.nwin) {
-      const uint64_t s0 = (uint64_t)lane * kN;
-      float *const dst = o.dst + s0;
-      if (s0 + kN <= o.left && (o.flags & 2u)) {
-#pragma unroll
-        for (int b = 0; b < 4; ++b) {
-          const float vv[8] = {__uint_as_float(v[8 * b]),     __uint_as_float(v[8 * b + 1]),
-                               __uint_as_float(v[8 * b + 2]), __uint_as_float(v[8 * b + 3]),
-                               __uint_as_float(v[8 * b + 4]), __uint_as_float(v[8 * b + 5]),
-                               __uint_as_float(v[8 * b + 6]), __uint_as_float(v[8 * b + 7])};
-          st_cs_v8(dst + 8 * b, vv);
-        }
-      } else if (s0 + kN <= o.left && (o.flags & 1u)) {
-#pragma unroll
-        for (int j = 0; j < 8; ++j)
-          __stcs(reinterpret_cast<float4 *>(dst) + j,
-                 make_float4(__uint_as_float(v[4 * j]), __uint_as_float(v[4 * j + 1]), __uint_as_float(v[4 * j + 2]),
-                             __uint_as_float(v[4 * j + 3])));
-      } else {
-#pragma unroll
-        for (int n = 0; n < kN; ++n)
-          if (s0 + n < o.left) dst[n] = __uint_as_float(v[n]);
-      }
     }
   };
 
@@ -284,6 +290,7 @@ void *tcpick_mode(uint32_t nwg) {
     case 4: return tcptr<MODE, 4>();
     case 5: return tcptr<MODE, 5>();
     case 6: return MODE == FPTC_IDCT_TF32X3 ? nullptr : tcptr<MODE, 6>();
+    case 7: return MODE == FPTC_IDCT_TF32X3 ? nullptr : tcptr<MODE, 7>();
     default: return nullptr;
   }
 }
@@ -321,7 +328,7 @@ size_t tc_smem_layout(uint32_t mode, uint32_t threads, const uint32_t *lmax, uin
   wp->out_tma = 0;
   o += (size_t)warps * kMiscBytes;
   tp->b_off = (uint32_t)align16(o);
-  o = tp->b_off + 4096;  // up to two 32 x 64-byte B operands
+  o = tp->b_off + (mode == FPTC_IDCT_TF32X3 ? 4096u : 2048u);  // B: TF32, BF16 hi + lo, or TF32 big + small
   tp->a_off = 0;         // A lives in tensor memory
   tp->a_buf = 0;
   tp->misc_off = (uint32_t)align16(o);
@@ -329,7 +336,8 @@ size_t tc_smem_layout(uint32_t mode, uint32_t threads, const uint32_t *lmax, uin
   tp->tiles_off = (uint32_t)align16(o);
   const uint32_t cols = (mode == FPTC_IDCT_TF32X3 ? 96u : 64u) * nwg;  // wg_cols per warpgroup
   if (cols > 512u) return ~size_t(0);                                   // does not fit tensor memory
-  return tp->tiles_off + 1023 + (size_t)warps * kOutTile;
+  // staging tiles aligned up to 1024 bytes from a 16-byte aligned offset: at most 1008 bytes skipped
+  return tp->tiles_off + 1008 + (size_t)warps * kOutTile;
 }
 
 cudaError_t tc_smem_config(uint32_t mode, uint32_t threads, size_t smem) {

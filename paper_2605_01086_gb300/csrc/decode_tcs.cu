@@ -206,7 +206,7 @@ __global__ void __launch_bounds__(tcs_nwg<MODE, N, E>() * 128, 1)
 
   unsigned char *const wbase = smem_raw + wp.warp_off + warp * kMiscBytes;
   uint64_t *const wbuf = reinterpret_cast<uint64_t *>(wbase);
-  uint8_t *const stage = wbase + kPassWords * 8 + kGuard;
+  uint8_t *const stage = wbase + kStageOff;
   const uintptr_t tiles0 = (reinterpret_cast<uintptr_t>(smem_raw + tp.tiles_off) + 1023) & ~uintptr_t(1023);
   unsigned char *const otile = reinterpret_cast<unsigned char *>(tiles0) + warp * kOutTile;
   unsigned char *const orow = otile + lane * 128u;

@@ -134,7 +134,7 @@ __global__ void __launch_bounds__(WARPS * 32, WARPS > 16 ? 1 : 32 / WARPS) k_dec
 
   unsigned char *const wbase = smem_raw + wp.warp_off + warp * kMiscBytes;
   uint64_t *const wbuf = reinterpret_cast<uint64_t *>(wbase);                       // first-pass words
-  uint8_t *const stage = wbase + kPassWords * 8 + kGuard;                           // tile position 0
+  uint8_t *const stage = wbase + kStageOff;                           // tile position 0
   // output staging tile: 1024-byte aligned (the period of the 128-byte swizzle)
   const uintptr_t tiles0 = (reinterpret_cast<uintptr_t>(smem_raw + wp.warp_off + WARPS * kMiscBytes) + 1023) &
                            ~uintptr_t(1023);

@@ -247,10 +247,11 @@ fptc_status configure_launch(fptc_plan *p) {
                           : (threads == 128 || threads == 256 || threads == 512 ||
                              ((threads == 768 || threads == 896 || threads == 1024) &&
                               p->kind == FPTC_KERNEL_WARP_TILE) ||
-                             ((threads == 384 || threads == 640 || threads == 768) && p->kind == FPTC_KERNEL_TENSOR));
+                             ((threads == 384 || threads == 640 || threads == 768 || threads == 896) &&
+                              p->kind == FPTC_KERNEL_TENSOR));
   if (!t_ok) {
-    set_error("threads must be 128, 256 or 512 (768, 896 and 1024 also for the warp-tile kernel, 384, 640 and 768 "
-              "for the tensor-core kernel; 256, 512 or 768 for the warp-tile kernel of other shapes; got %u)",
+    set_error("threads must be 128, 256 or 512 (768, 896 and 1024 also for the warp-tile kernel, 384, 640, 768 and "
+              "896 for the tensor-core kernel; 256, 512 or 768 for the warp-tile kernel of other shapes; got %u)",
               threads);
     return FPTC_ERR_INVALID_ARGUMENT;
   }
@@ -278,14 +279,14 @@ fptc_status configure_launch(fptc_plan *p) {
     if (e == cudaSuccess) occ = std::min<int>(occ, 1);
   } else if (p->kind == FPTC_KERNEL_TENSOR) {
     if (p->opts.threads == 0) {
-      // as many warpgroups as one CTA's shared memory allows (6 at most)
+      // as many warpgroups as one CTA's shared memory and tensor memory allow (7 at most)
       int dev = 0, optin = 0;
       cudaGetDevice(&dev);
       cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
       WarpParams pw{};
       TcParams pt{};
       threads = 128;
-      for (uint32_t t : {768u, 640u, 512u, 384u, 256u})
+      for (uint32_t t : {896u, 768u, 640u, 512u, 384u, 256u})
         if (tc_smem_layout(p->opts.idct, t, lm.data(), (uint32_t)lm.size(), &pw, &pt) <= (size_t)optin) {
           threads = t;
           break;
@@ -1110,7 +1111,7 @@ fptc_status fptc_plan_autotune(fptc_plan *p, const uint64_t *d_words, const uint
     if (keep.idct != FPTC_IDCT_FP32 && p->tcs_N)  // the shape kernel: one configuration
       cands.push_back({FPTC_KERNEL_TENSOR, tcs_tile_windows(p->tcs_E) * p->tcs_N, 0u});
     else if (keep.idct != FPTC_IDCT_FP32)
-      for (uint32_t th : {256u, 384u, 512u, 640u, 768u})
+      for (uint32_t th : {256u, 384u, 512u, 640u, 768u, 896u})
         cands.push_back({FPTC_KERNEL_TENSOR, tc_tile_windows() * 32, th});
     for (uint32_t th : {128u, 256u, 512u, 768u, 896u, 1024u}) {
       if (keep.idct != FPTC_IDCT_FP32) continue;

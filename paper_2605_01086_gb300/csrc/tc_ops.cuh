@@ -45,7 +45,7 @@ __device__ __forceinline__ bool bar_any_c(bool v) {
   return r != 0;
 }
 
-// Barrier over the 128 threads of warpgroup wg (ids 1..6), returning the OR of v.
+// Barrier over the 128 threads of warpgroup wg (ids 1..7), returning the OR of v.
 __device__ __forceinline__ bool wg_barrier_any(uint32_t wg, bool v) {
   switch (wg) {
     case 0: return bar_any_c<1>(v);
@@ -53,7 +53,8 @@ __device__ __forceinline__ bool wg_barrier_any(uint32_t wg, bool v) {
     case 2: return bar_any_c<3>(v);
     case 3: return bar_any_c<4>(v);
     case 4: return bar_any_c<5>(v);
-    default: return bar_any_c<6>(v);
+    case 5: return bar_any_c<6>(v);
+    default: return bar_any_c<7>(v);
   }
 }
 
@@ -121,6 +122,18 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
         "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
         "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
         "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr)
+      : "memory");
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Thread i of the warp reads 16 consecutive 32-bit columns of lane (taddr lane) + i.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
       : "r"(taddr)
       : "memory");
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");

@@ -23,7 +23,7 @@ constexpr int kE = 16;
 constexpr int kT = 128;                    // windows per tile
 constexpr int kTS = kT * kE;               // symbols per tile
 constexpr int kGuard = 64;                 // entries before and after the tile (a word holds <= 64 codewords)
-constexpr int kStage = kTS + 2 * kGuard;   // level bytes per warp
+constexpr int kStage = kTS + kGuard;       // level bytes per warp after the first-pass words (see kStageOff)
 constexpr int kZStride = 257;              // floats per zone row (zero levels of the zones in different banks)
 constexpr int kZRows = 2;                  // zone rows in shared memory: zone 2 reconstructs 0 without a row
 constexpr uint32_t kDeqBytes = (kZRows * kZStride * 4 + 15) / 16 * 16;  // a domain's dequantization rows
@@ -31,7 +31,14 @@ constexpr int kWPL = 2;                    // consecutive words per lane per dec
 constexpr int kPassWords = 32 * kWPL;
 constexpr int kStepWin = 32;               // windows per transform step (one per lane)
 constexpr int kOutTile = kStepWin * kN * 4;  // bytes of a step's output (TMA box 32 x 32 floats)
-constexpr int kMiscBytes = kPassWords * 8 + kStage;  // per warp: first-pass words, level bytes
+// Per warp: the first-pass words, then the level bytes.  The guard before tile
+// position 0 is the last kGuard bytes of the first-pass words: those words are
+// in registers before the decode writes there, and the next tile's words are
+// requested only after it (decode_tile ends with a warp barrier).
+constexpr int kMiscBytes = kPassWords * 8 + kStage;
+constexpr int kStageOff = kPassWords * 8;  // tile position 0 from the start of the warp's area
+static_assert(kGuard <= kPassWords * 8, "the guard before the tile lies inside the first-pass words");
+static_assert(kStageOff % 16 == 0 && kMiscBytes % 16 == 0, "level rows are read as 16-byte vectors");
 // zone mask of Table 1 (B1 = 2, B2 = 16): bins 0, 1 in zone 0, the rest in zone 1
 constexpr uint32_t kZmaskTable1 = 0x55555550u;
 
@@ -382,6 +389,7 @@ __device__ __forceinline__ TileEnd decode_tile(const DecodeParams &p, const Ctx 
     }
   }
   r.bad = __reduce_or_sync(0xffffffffu, bad);
+  __syncwarp();  // the guard before the tile is the first-pass words' area, refilled after this
   return r;
 }
 
