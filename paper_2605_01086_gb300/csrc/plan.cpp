@@ -294,6 +294,12 @@ fptc_status configure_launch(fptc_plan *p) {
       p->threads = threads;
     }
     p->smem = tc_smem_layout(p->opts.idct, threads, lm.data(), (uint32_t)lm.size(), &p->wp, &p->tp);
+    if (p->smem == ~size_t(0)) {
+      set_error("the tensor-core kernel at %u threads (%u warpgroups) needs more than the 512 tensor-memory "
+                "columns of an SM in this form (at most 640 threads for 3xTF32, 896 for the others)",
+                threads, threads / 128);
+      return FPTC_ERR_UNSUPPORTED;
+    }
     if (const fptc_status fs = smem_fits("tensor-core", threads, p->smem); fs != FPTC_OK) return fs;
     e = tc_smem_config(p->opts.idct, threads, p->smem);
     if (e != cudaSuccess) return cuda_fail(e, "decode shared-memory size");
