@@ -132,10 +132,11 @@ typedef struct fptc_plan_options {
   uint32_t threads;       /* threads per CTA: 128, 256 or 512 (also 768, 896, 1024 for the warp-tile kernel
                              at N = 32, E = 16; 256, 512 or 768 for it at other shapes; 384, 640, 768 or
                              896 for the tensor-core kernel at N = 32, E = 16, whose other shapes fix their
-                             own); 0 = 256, or for the warp-tile and tensor-core kernels the most that fit
-                             shared and tensor memory (at most 512 at other shapes, 896 for the
-                             tensor-core kernel, 640 for its 3xTF32 form); a count whose shared memory does
-                             not fit is refused with FPTC_ERR_UNSUPPORTED */
+                             own); 0 = 256, or for the warp-tile kernel 896 where its shared memory fits
+                             (28 warps, no register spills), else the most that fit (at most 512 at other
+                             shapes), and for the tensor-core kernel the most that fit shared and tensor
+                             memory (896; 640 for its 3xTF32 form); a count that does not fit is refused
+                             with FPTC_ERR_UNSUPPORTED */
   uint32_t ctas_per_sm;   /* persistent CTAs per SM; 0 = as many as fit */
   uint32_t kernel;        /* fptc_kernel: which decode kernel; 0 = choose */
   uint32_t reserved[2];   /* must be 0 */
